@@ -1,0 +1,413 @@
+"""Plain FP64 CPU oracle for the FDAS hot path -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this module.  The CUDA library never calls it and it
+imports nothing from the product package; the two share only the seeded input
+generators in ``synthetic``.
+
+What it computes, in the order of the method (paper §2.1 "FDAS": a matched
+filter over a grid of constant-acceleration templates; §2.2: the filter is a
+convolution evaluated in the Fourier domain; the rest of the pipeline -- the
+normalisation, the harmonic sum and the threshold -- is not spelled out in the
+paper and follows the stated readings):
+
+1. ``spectrum``      X_k = sum_n x_n exp(-2 pi i k n / N), k in [0, N/2),
+                     with X_0 set to 0 (numpy's FFT is the library step).
+2. ``normalise``     per block of B bins, X'_k = X_k sqrt(ln 2 / median|X|^2)
+                     (block 0 skips k = 0; even counts take the mean of the two
+                     middle values): white noise then has |X'|^2 ~ Exp(1).
+3. ``rho``           the response of an accelerated sinusoid,
+                     rho(q, z) = int_0^1 exp(2 pi i [(q - z/2) u + z u^2/2]) du,
+                     by Gauss-Legendre quadrature (deliberately not the Fresnel
+                     closed form the CUDA path uses).
+   ``template_bank`` g_z[e] = conj(rho(e, z)) / sqrt(E_z), |e| <= m(z),
+                     E_z = sum |rho(e, z)|^2, m(z) = 8 + ceil(|z|/2).
+4. ``power_plane``   the DIRECT correlation F(r, z) = sum_e X'_{r-e} g_z[e],
+                     P = |F|^2 (C loop in fdas_oracle.c).  Overlap-save is an
+                     exact re-arrangement of this sum, which is why the oracle
+                     does not use it.
+5. ``plane_stats``   mean and population standard deviation of P over the
+                     whole n_z x N_r plane.
+6. ``harmonic_*``    top-harmonic-indexed sums S_h, h = 1, 2, 4, ..., H
+                     (C loop in fdas_oracle.c).
+7. ``thresholds``    S_h > T_h with T_h = mean * Q^-1(h, Phibar(sigma))
+                     (Gamma(h,1) tail at the Gaussian-equivalent false-alarm
+                     probability of `sigma`), or T_h = h*mean + sigma*sqrt(h)*std.
+8. ``candidates``    every cell above threshold, sorted by (trial, h, iz, ir).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.special as sps
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_SRC = os.path.join(_HERE, "fdas_oracle.c")
+
+GAMMA_TAIL = 0
+MEAN_PLUS_KSIGMA = 1
+
+
+# --------------------------------------------------------------------------
+# C part
+# --------------------------------------------------------------------------
+def build(force: bool = False) -> str:
+    """Compile fdas_oracle.c into oracle/_build/liboracle.so (gcc, OpenMP)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared",
+                           "-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+_lib = None
+
+
+def _c():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        i64, i32 = ctypes.c_int64, ctypes.c_int32
+        lib.oracle_plane.argtypes = [P, P, i64, i32, P, P, P, P, P]
+        lib.oracle_plane.restype = None
+        lib.oracle_cells.argtypes = [P, P, i64, P, P, P, P, i64, P, P, P]
+        lib.oracle_cells.restype = None
+        lib.oracle_harmonic_planes.argtypes = [P, i64, i32, i32, i32, P]
+        lib.oracle_harmonic_planes.restype = None
+        lib.oracle_harmonic_cells.argtypes = [P, i64, i32, i32, i32, P, i64,
+                                              P, P, P, P]
+        lib.oracle_harmonic_cells.restype = i64
+        lib.oracle_harmonic_at.argtypes = [P, i64, i32, i32, i64, P, P, P, P]
+        lib.oracle_harmonic_at.restype = None
+        lib.oracle_threads.argtypes = []
+        lib.oracle_threads.restype = i32
+        _lib = lib
+    return _lib
+
+
+def threads() -> int:
+    """OpenMP threads used by the C loops."""
+    return int(_c().oracle_threads())
+
+
+def _ptr(a: np.ndarray) -> ctypes.c_void_p:
+    assert a.flags["C_CONTIGUOUS"]
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+# --------------------------------------------------------------------------
+# geometry of the search grid
+# --------------------------------------------------------------------------
+@dataclass
+class Geometry:
+    n_samples: int
+    z_max: float
+    z_step: float
+    n_harm: int
+    n_r: int = field(init=False)
+    K: int = field(init=False)          # index of z = 0 (iz0)
+    n_z: int = field(init=False)
+    z: np.ndarray = field(init=False)
+    m: np.ndarray = field(init=False)
+    stages: list = field(init=False)
+
+    def __post_init__(self):
+        self.n_r = self.n_samples // 2
+        ratio = self.z_max / self.z_step
+        self.K = int(round(ratio))
+        if abs(ratio - self.K) > 1e-9 * max(1.0, ratio):
+            raise ValueError("z_max / z_step must be an integer")
+        self.n_z = 2 * self.K + 1
+        idx = np.arange(self.n_z) - self.K
+        self.z = idx * float(self.z_step)
+        # m(z) = 8 + ceil(|z|/2), evaluated on the exact grid offset
+        self.m = np.array([8 + math.ceil(abs(i) * self.z_step / 2.0 - 1e-9)
+                           for i in idx], dtype=np.int32)
+        self.stages = [1 << s for s in range(int(math.log2(self.n_harm)) + 1)]
+
+    @property
+    def iz0(self) -> int:
+        return self.K
+
+    @property
+    def m_max(self) -> int:
+        return int(self.m.max())
+
+
+def geometry(n_samples: int, z_max: float, z_step: float, n_harm: int) -> Geometry:
+    return Geometry(n_samples, z_max, z_step, n_harm)
+
+
+# --------------------------------------------------------------------------
+# 1-2: spectrum and normalisation
+# --------------------------------------------------------------------------
+def spectrum(x: np.ndarray) -> np.ndarray:
+    """X_k for k in [0, N/2) in FP64; DC removed (X_0 = 0), Nyquist dropped."""
+    x = np.asarray(x, dtype=np.float64)
+    n = x.shape[0]
+    X = np.fft.rfft(x)[: n // 2].astype(np.complex128)
+    X[0] = 0.0
+    return X
+
+
+def block_medians(X: np.ndarray, block: int = 2048) -> np.ndarray:
+    """median(|X_k|^2) per block of `block` bins (block 0 without k = 0)."""
+    p = np.abs(X) ** 2
+    b = min(block, p.shape[0])
+    nb = p.shape[0] // b
+    meds = np.empty(nb)
+    for i in range(nb):
+        seg = p[i * b:(i + 1) * b]
+        if i == 0:
+            seg = seg[1:]
+        meds[i] = np.median(seg)
+    return meds
+
+
+def normalise(X: np.ndarray, block: int = 2048, mode: str = "median"):
+    """Return (X', medians).  Exp(1) noise has median ln 2, hence sqrt(ln2/med).
+
+    A block whose median is 0 (no power at all) gets the factor 0.
+    """
+    if mode == "none":
+        return X.copy(), None
+    meds = block_medians(X, block)
+    b = min(block, X.shape[0])
+    with np.errstate(divide="ignore"):
+        f = np.where(meds > 0, np.sqrt(math.log(2.0) / np.where(meds > 0, meds, 1.0)), 0.0)
+    return X * np.repeat(f, b), meds
+
+
+# --------------------------------------------------------------------------
+# 3: templates
+# --------------------------------------------------------------------------
+def rho(q, z: float, n_nodes: int | None = None) -> np.ndarray:
+    """rho(q, z) = int_0^1 exp(2 pi i [(q - z/2) u + z u^2 / 2]) du (quadrature).
+
+    Gauss-Legendre on [0, 1] with n >= 4 (|q| + |z|) + 64 nodes: the
+    integrand turns through at most |q| + |z|/2 cycles, so this is far past
+    convergence in FP64.
+    """
+    q = np.atleast_1d(np.asarray(q, dtype=np.float64))
+    if n_nodes is None:
+        n_nodes = int(4 * (np.max(np.abs(q)) + abs(z))) + 64
+    t, w = np.polynomial.legendre.leggauss(n_nodes)
+    u = 0.5 * (t + 1.0)
+    w = 0.5 * w
+    ph = 2.0 * np.pi * ((q[:, None] - z / 2.0) * u[None, :] + z * u[None, :] ** 2 / 2.0)
+    return (np.exp(1j * ph) * w[None, :]).sum(axis=1)
+
+
+@dataclass
+class Bank:
+    geom: Geometry
+    taps: list          # taps[iz][e + m] = g_z[e], complex128
+    energy: np.ndarray  # E_z
+
+
+def template_bank(geom: Geometry) -> Bank:
+    taps, energy = [], np.empty(geom.n_z)
+    for iz in range(geom.n_z):
+        m = int(geom.m[iz])
+        e = np.arange(-m, m + 1, dtype=np.float64)
+        r = rho(e, float(geom.z[iz]))
+        E = float(np.sum(np.abs(r) ** 2))
+        energy[iz] = E
+        taps.append(np.conj(r) / math.sqrt(E))
+    return Bank(geom, taps, energy)
+
+
+def _flat_taps(bank: Bank):
+    offs = np.zeros(bank.geom.n_z, dtype=np.int64)
+    acc = 0
+    for i, t in enumerate(bank.taps):
+        offs[i] = acc
+        acc += t.shape[0]
+    flat = np.concatenate(bank.taps)
+    return (np.ascontiguousarray(flat.real), np.ascontiguousarray(flat.imag),
+            offs, np.ascontiguousarray(bank.geom.m.astype(np.int32)))
+
+
+# --------------------------------------------------------------------------
+# 4: direct correlation
+# --------------------------------------------------------------------------
+def power_plane(Xn: np.ndarray, bank: Bank) -> np.ndarray:
+    """P[iz][r] = |sum_e X'_{r-e} g_z[e]|^2 over the whole plane (FP64)."""
+    n_r = Xn.shape[0]
+    xr = np.ascontiguousarray(Xn.real)
+    xi = np.ascontiguousarray(Xn.imag)
+    gr, gi, offs, m = _flat_taps(bank)
+    P = np.empty((bank.geom.n_z, n_r), dtype=np.float64)
+    _c().oracle_plane(_ptr(xr), _ptr(xi), n_r, bank.geom.n_z, _ptr(m),
+                      _ptr(offs), _ptr(gr), _ptr(gi), _ptr(P))
+    return P
+
+
+def cell_powers(Xn: np.ndarray, bank: Bank, iz, r) -> np.ndarray:
+    """P at the cells (iz[c], r[c]) by the same direct sum."""
+    iz = np.ascontiguousarray(np.asarray(iz, dtype=np.int32))
+    r = np.ascontiguousarray(np.asarray(r, dtype=np.int64))
+    xr = np.ascontiguousarray(Xn.real)
+    xi = np.ascontiguousarray(Xn.imag)
+    gr, gi, offs, m = _flat_taps(bank)
+    out = np.empty(iz.shape[0], dtype=np.float64)
+    _c().oracle_cells(_ptr(xr), _ptr(xi), Xn.shape[0], _ptr(m), _ptr(offs),
+                      _ptr(gr), _ptr(gi), iz.shape[0], _ptr(iz), _ptr(r),
+                      _ptr(out))
+    return out
+
+
+def plane_stats(P: np.ndarray):
+    """(mean, population std) of the plane in FP64."""
+    return float(P.mean(dtype=np.float64)), float(P.std(dtype=np.float64))
+
+
+# --------------------------------------------------------------------------
+# 6: harmonic sum
+# --------------------------------------------------------------------------
+def harmonic_indices(ir: int, iz: int, iz0: int, H: int, j: int):
+    """(source iz, source ir) that harmonic j of H reads for the cell (ir, iz)."""
+    o = iz - iz0
+    a = abs(o)
+    oj = (a * j + H // 2) // H
+    return iz0 + (-oj if o < 0 else oj), (ir * j + H // 2) // H
+
+
+def harmonic_planes(P: np.ndarray, geom: Geometry) -> np.ndarray:
+    """S[st][iz][ir] for every stage h = 2^st <= H."""
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    S = np.empty((len(geom.stages),) + P.shape, dtype=np.float64)
+    _c().oracle_harmonic_planes(_ptr(P), P.shape[1], P.shape[0], geom.iz0,
+                                geom.n_harm, _ptr(S))
+    return S
+
+
+def harmonic_at(P: np.ndarray, geom: Geometry, st, iz, ir) -> np.ndarray:
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    st = np.ascontiguousarray(np.asarray(st, dtype=np.int32))
+    iz = np.ascontiguousarray(np.asarray(iz, dtype=np.int32))
+    ir = np.ascontiguousarray(np.asarray(ir, dtype=np.int64))
+    out = np.empty(st.shape[0])
+    _c().oracle_harmonic_at(_ptr(P), P.shape[1], geom.iz0, geom.n_harm,
+                            st.shape[0], _ptr(st), _ptr(iz), _ptr(ir), _ptr(out))
+    return out
+
+
+# --------------------------------------------------------------------------
+# 7: thresholds
+# --------------------------------------------------------------------------
+def false_alarm_prob(sigma: float) -> float:
+    """Gaussian upper tail Phibar(sigma)."""
+    return float(0.5 * sps.erfc(sigma / math.sqrt(2.0)))
+
+
+def gamma_tail_factors(H: int, sigma: float) -> np.ndarray:
+    """G_h = Q^-1(h, Phibar(sigma)) for h = 1, 2, 4, ..., H (scipy)."""
+    p = false_alarm_prob(sigma)
+    return np.array([sps.gammainccinv(h, p) for h in _stages(H)])
+
+
+def _stages(H: int):
+    return [1 << s for s in range(int(math.log2(H)) + 1)]
+
+
+def thresholds(H: int, sigma: float, mode: int, mean: float, std: float) -> np.ndarray:
+    hs = np.array(_stages(H), dtype=np.float64)
+    if mode == GAMMA_TAIL:
+        return mean * gamma_tail_factors(H, sigma)
+    return hs * mean + sigma * np.sqrt(hs) * std
+
+
+def log_gamma_tail(h: int, x: float) -> float:
+    """log Q(h, x) for integer h: Q = exp(-x) sum_{k<h} x^k / k! (Poisson)."""
+    if x <= 0:
+        return 0.0
+    k = np.arange(h, dtype=np.float64)
+    lt = k * math.log(x) - sps.gammaln(k + 1.0)
+    mx = lt.max()
+    return -x + mx + math.log(np.exp(lt - mx).sum())
+
+
+def sigma_equiv(S: float, h: int, mean: float, std: float, mode: int) -> float:
+    """Gaussian-equivalent significance of a harmonic sum S at stage h."""
+    if mode == GAMMA_TAIL:
+        return float(-sps.ndtri_exp(log_gamma_tail(h, S / mean)))
+    return float((S - h * mean) / (math.sqrt(h) * std))
+
+
+# --------------------------------------------------------------------------
+# 8: candidates
+# --------------------------------------------------------------------------
+CAND_DTYPE = np.dtype([("trial", np.uint32), ("harm", np.int32), ("iz", np.int32),
+                       ("ir", np.int64), ("power", np.float64), ("sigma", np.float64)])
+
+
+def candidates(P: np.ndarray, geom: Geometry, mean: float, std: float,
+               sigma: float = 6.0, mode: int = GAMMA_TAIL, trial: int = 0,
+               guard: float = 0.0, cap: int = 1 << 22):
+    """(candidates, guard_cells).
+
+    candidates: every (h, iz, ir) with S_h > T_h, sorted by (trial, h, iz, ir).
+    guard_cells: the cells with |S_h - T_h| <= guard * T_h (same dtype),
+    where a rounding difference may flip the decision.
+    """
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    T = thresholds(geom.n_harm, sigma, mode, mean, std)
+    lo = np.ascontiguousarray(T * (1.0 - guard))
+    out_st = np.empty(cap, dtype=np.int32)
+    out_iz = np.empty(cap, dtype=np.int32)
+    out_ir = np.empty(cap, dtype=np.int64)
+    out_s = np.empty(cap, dtype=np.float64)
+    n = _c().oracle_harmonic_cells(_ptr(P), P.shape[1], P.shape[0], geom.iz0,
+                                   geom.n_harm, _ptr(lo), cap, _ptr(out_st),
+                                   _ptr(out_iz), _ptr(out_ir), _ptr(out_s))
+    if n > cap:
+        raise RuntimeError(f"oracle candidate buffer too small ({n} > {cap})")
+    st, iz, ir, s = out_st[:n], out_iz[:n], out_ir[:n], out_s[:n]
+    rec = np.empty(n, dtype=CAND_DTYPE)
+    rec["trial"] = trial
+    rec["harm"] = np.left_shift(1, st)
+    rec["iz"] = iz
+    rec["ir"] = ir
+    rec["power"] = s
+    rec["sigma"] = [sigma_equiv(float(v), int(h), mean, std, mode)
+                    for v, h in zip(s, rec["harm"])]
+    thr = T[st]
+    is_cand = s > thr
+    in_guard = np.abs(s - thr) <= guard * thr
+    cands = np.sort(rec[is_cand], order=["trial", "harm", "iz", "ir"])
+    guards = np.sort(rec[in_guard], order=["trial", "harm", "iz", "ir"])
+    return cands, guards
+
+
+# --------------------------------------------------------------------------
+# the whole path for one series
+# --------------------------------------------------------------------------
+def search(x: np.ndarray, z_max: float, z_step: float, n_harm: int,
+           sigma: float = 6.0, mode: int = GAMMA_TAIL, norm: str = "median",
+           norm_block: int = 2048, trial: int = 0, guard: float = 0.0,
+           bank: Bank | None = None):
+    """Run steps 1-8 on one series; returns a dict of every intermediate."""
+    geom = geometry(x.shape[0], z_max, z_step, n_harm)
+    X = spectrum(x)
+    Xn, meds = normalise(X, norm_block, norm)
+    if bank is None:
+        bank = template_bank(geom)
+    P = power_plane(Xn, bank)
+    mean, std = plane_stats(P)
+    cands, guards = candidates(P, geom, mean, std, sigma, mode, trial, guard)
+    return dict(geom=geom, X=X, Xn=Xn, medians=meds, bank=bank, P=P,
+                mean=mean, std=std, T=thresholds(n_harm, sigma, mode, mean, std),
+                candidates=cands, guard=guards)

@@ -1,0 +1,352 @@
+"""Pins of the FP64 oracle against what mathematics and the paper fix.
+
+None of these compares the oracle with itself: each one checks a step against
+a brute-force definition, a closed form, an independent library route
+(scipy's Fresnel integrals, scipy's incomplete gamma) or an invariant, chosen
+so that a dropped term, a wrong sign or index, or a transposed operand fails
+at least one of them.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.special as sps
+
+import oracle as O
+import synthetic as S
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def rho_fresnel(q, z):
+    """rho(q, z) through scipy's Fresnel integrals (independent of quadrature).
+
+    With a = z/2 the phase is 2 pi (a u^2 + (q - z/2) u); completing the square
+    gives t0 = (q - z/2)/sqrt(z/2), t1 = (q + z/2)/sqrt(z/2) and
+    rho = exp(-i pi (q - z/2)^2 / z) / (2 sqrt(z/2)) * [E(t1) - E(t0)],
+    E(t) = C(t) + i S(t).  Negative z uses rho(q, -z) = conj(rho(-q, z)).
+    """
+    q = np.atleast_1d(np.asarray(q, dtype=np.float64))
+    if z == 0:
+        return np.exp(1j * np.pi * q) * np.sinc(q)
+    if z < 0:
+        return np.conj(rho_fresnel(-q, -z))
+    a = z / 2.0
+    sa = math.sqrt(a)
+    b = q - a
+    s0, c0 = sps.fresnel(b / sa)
+    s1, c1 = sps.fresnel((2 * a + b) / sa)
+    return np.exp(-1j * np.pi * b * b / (2 * a)) / (2 * sa) * ((c1 - c0) + 1j * (s1 - s0))
+
+
+# --------------------------------------------------------------------------
+# spectrum
+# --------------------------------------------------------------------------
+def test_spectrum_matches_brute_force_dft():
+    n = 1024
+    x = S.white_noise(n, 11)
+    k = np.arange(n // 2)[:, None]
+    t = np.arange(n)[None, :]
+    ref = (x.astype(np.float64)[None, :] * np.exp(-2j * np.pi * k * t / n)).sum(axis=1)
+    ref[0] = 0.0
+    X = O.spectrum(x)
+    assert X.shape == (n // 2,)
+    assert np.max(np.abs(X - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+def test_spectrum_parseval():
+    n = 1 << 14
+    x = S.white_noise(n, 12).astype(np.float64)
+    X = O.spectrum(x)
+    dc = x.sum()
+    nyq = (x * (-1.0) ** np.arange(n)).sum()
+    lhs = (x * x).sum()
+    rhs = (dc * dc + 2 * np.sum(np.abs(X[1:]) ** 2) + nyq * nyq) / n
+    assert abs(lhs - rhs) <= 1e-12 * lhs
+
+
+def test_spectrum_sign_convention_pure_tone():
+    n, k0 = 4096, 37
+    x = np.sin(2 * np.pi * k0 * np.arange(n) / n)
+    X = O.spectrum(x)
+    # forward DFT with exp(-2 pi i k n/N): sin -> -i N/2 at k0
+    assert abs(X[k0] - (-0.5j * n)) < 1e-9 * n
+    X[k0] = 0
+    assert np.max(np.abs(X)) < 1e-9 * n
+
+
+# --------------------------------------------------------------------------
+# normalisation
+# --------------------------------------------------------------------------
+def test_block_medians_even_and_odd_counts():
+    B = 16
+    rng = np.random.default_rng(5)
+    p = np.empty(4 * B)
+    p[0] = 1e9                                  # k = 0 is skipped
+    p[1:B] = rng.permutation(np.arange(1, B))  # 15 values: median = 8
+    for b in range(1, 4):
+        p[b * B:(b + 1) * B] = rng.permutation(np.arange(1, B + 1)) * b  # even
+    X = np.sqrt(p).astype(np.complex128)
+    meds = O.block_medians(X, B)
+    assert abs(meds[0] - B / 2) < 1e-12 * B
+    for b in range(1, 4):
+        # mean of the two middle values
+        assert abs(meds[b] - b * (B + 1) / 2) < 1e-12 * B * b
+
+
+def test_normalised_noise_is_unit_exponential():
+    x = S.white_noise(1 << 18, 13)
+    Xn, _ = O.normalise(O.spectrum(x), 2048)
+    p = np.abs(Xn[1:]) ** 2
+    # Exp(1): mean 1, median ln 2
+    assert abs(p.mean() - 1.0) < 0.01
+    assert abs(np.median(p) - math.log(2)) < 0.01
+
+
+def test_normalise_none_is_identity():
+    X = O.spectrum(S.white_noise(4096, 3))
+    Xn, meds = O.normalise(X, 2048, "none")
+    assert meds is None and np.array_equal(Xn, X)
+
+
+# --------------------------------------------------------------------------
+# templates
+# --------------------------------------------------------------------------
+def test_rho_zero_z_is_fourier_interpolation_kernel():
+    q = np.array([-7.3, -2.5, -0.25, 0.0, 0.1, 0.5, 3.7, 11.0])
+    ref = np.exp(1j * np.pi * q) * np.sinc(q)
+    assert np.max(np.abs(O.rho(q, 0.0) - ref)) < 1e-13
+    e = np.arange(-20, 21)
+    d = O.rho(e, 0.0)
+    assert abs(d[20] - 1) < 1e-14 and np.max(np.abs(np.delete(d, 20))) < 1e-13
+
+
+@pytest.mark.parametrize("z", [0.5, 1.0, 7.5, -3.0, 16.0, -48.0, 96.0, -96.0])
+def test_rho_quadrature_matches_fresnel_route(z):
+    m = 8 + math.ceil(abs(z) / 2)
+    q = np.concatenate([np.arange(-m, m + 1), [0.3, -5.7, 2.5]])
+    a = O.rho(q, z)
+    b = rho_fresnel(q, z)
+    assert np.max(np.abs(a - b)) < 1e-12
+
+
+def test_rho_conjugate_symmetry():
+    q = np.linspace(-30, 30, 61) + 0.17
+    for z in (3.0, 40.0, 95.0):
+        assert np.max(np.abs(O.rho(q, -z) - np.conj(O.rho(-q, z)))) < 1e-13
+
+
+def test_rho_window_energy_approaches_one():
+    # sum over integer shifts of |rho(q+e, z)|^2 = 1 (Parseval for the
+    # unit-modulus signal on [0,1)); the truncated sum grows towards 1.
+    z, q = 20.0, 0.3
+    prev = 0.0
+    for M in (10, 40, 160):
+        e = np.arange(-M, M + 1)
+        s = np.sum(np.abs(rho_fresnel(q + e, z)) ** 2)
+        o = np.sum(np.abs(O.rho(q + e, z)) ** 2)
+        assert abs(s - o) < 1e-12
+        assert prev < o < 1.0
+        prev = o
+    assert 1.0 - prev < 5e-3
+
+
+def test_template_bank_geometry_and_energy():
+    g = O.geometry(1 << 17, 16.0, 2.0, 4)
+    assert g.n_z == 17 and g.iz0 == 8
+    assert list(g.m) == [8 + math.ceil(abs(z) / 2) for z in g.z]
+    assert g.m_max == 16
+    bank = O.template_bank(g)
+    assert abs(bank.energy[g.iz0] - 1.0) < 1e-13
+    for iz, t in enumerate(bank.taps):
+        assert t.shape[0] == 2 * g.m[iz] + 1
+        assert abs(np.sum(np.abs(t) ** 2) - 1.0) < 1e-12
+        # taps are conj(rho(e,z))/sqrt(E): compare with the Fresnel route
+        e = np.arange(-g.m[iz], g.m[iz] + 1)
+        ref = np.conj(rho_fresnel(e, g.z[iz])) / math.sqrt(bank.energy[iz])
+        assert np.max(np.abs(t - ref)) < 1e-12
+
+
+def test_paper_workload_geometry():
+    with open(os.path.join(GOLDEN, "paper_numbers.json")) as f:
+        pw = json.load(f)["ska_like_workload"]
+    g = O.geometry(1 << 23, 96.0, 1.0, 16)
+    assert g.n_z == pw["acceleration_trials"]
+    # 600 s at 64 us is 9.375e6 samples; the power-of-two length used is 2^23
+    n_paper = pw["t_obs_s"] / (pw["tsamp_us"] * 1e-6)
+    assert (1 << 23) <= n_paper < (1 << 24)
+
+
+# --------------------------------------------------------------------------
+# correlation (power plane)
+# --------------------------------------------------------------------------
+def _small_geom():
+    return O.geometry(1 << 12, 16.0, 2.0, 4)
+
+
+def test_zero_z_row_is_normalised_power_spectrum():
+    g = _small_geom()
+    x = S.white_noise(g.n_samples, 21)
+    Xn, _ = O.normalise(O.spectrum(x), 512)
+    P = O.power_plane(Xn, O.template_bank(g))
+    assert np.max(np.abs(P[g.iz0] - np.abs(Xn) ** 2)) < 1e-12 * np.max(P[g.iz0])
+
+
+@pytest.mark.parametrize("r0,z0", [(700, 6.0), (1500, -14.0), (20, 16.0), (2030, -2.0)])
+def test_fourier_domain_injection_peak_closed_form(r0, z0):
+    """X_k = c rho(r0 - k, z0): the plane peaks at (r0, z0) with P = |c|^2 E_z0."""
+    g = _small_geom()
+    k = np.arange(g.n_r)
+    c = 3.0 - 4.0j
+    X = c * rho_fresnel(r0 - k, z0)
+    X[0] = 0.0
+    P = O.power_plane(X, O.template_bank(g))
+    iz = int(round(z0 / g.z_step)) + g.iz0
+    m = g.m[iz]
+    e = np.arange(-m, m + 1)
+    Ez = np.sum(np.abs(rho_fresnel(e, z0)) ** 2)
+    assert abs(P[iz, r0] - abs(c) ** 2 * Ez) < 1e-10 * abs(c) ** 2
+    assert np.unravel_index(np.argmax(P), P.shape) == (iz, r0)
+
+
+def test_time_domain_chirp_matches_closed_form():
+    """A noise-free accelerated sinusoid gives X_k ~ (aN/2) e^{i pi z/4} rho(r-k, z)."""
+    n, r_bar, z0, a = 1 << 14, 1234.3, 7.5, 0.05
+    g = O.geometry(n, 16.0, 2.0, 4)
+    x = S.inject_sinusoid(np.zeros(n, np.float32), r_bar, z0, a).astype(np.float64)
+    # inject in FP64 to keep the float32 rounding out of the comparison
+    u = np.arange(n) / n
+    x = a * np.cos(2 * np.pi * (r_bar * u + z0 * (u - 0.5) ** 2 / 2))
+    bank = O.template_bank(g)
+    P = O.power_plane(O.spectrum(x), bank)
+    peak = np.unravel_index(np.argmax(P), P.shape)
+    # closed form at every cell of a 5 x 7 neighbourhood
+    best, best_cell = -1.0, None
+    for iz in range(g.n_z):
+        m = g.m[iz]
+        e = np.arange(-m, m + 1)
+        for r in range(1228, 1241):
+            F = (a * n / 2) * np.sum(rho_fresnel(r_bar - r + e, z0)
+                                     * np.conj(rho_fresnel(e, g.z[iz]))) / math.sqrt(bank.energy[iz])
+            ref = abs(F) ** 2
+            if abs(iz - peak[0]) <= 2 and abs(r - peak[1]) <= 3:
+                assert abs(P[iz, r] - ref) <= 2e-3 * P[peak] , (iz, r)
+            if ref > best:
+                best, best_cell = ref, (iz, r)
+    assert best_cell == peak
+    assert abs(P[peak] - best) < 1e-3 * best
+
+
+def test_plane_stats_are_mean_and_population_std():
+    P = np.arange(12, dtype=np.float64).reshape(3, 4)
+    m, s = O.plane_stats(P)
+    assert m == 5.5 and abs(s - math.sqrt(143 / 12)) < 1e-14
+
+
+# --------------------------------------------------------------------------
+# harmonic sum
+# --------------------------------------------------------------------------
+def test_harmonic_index_rounding_reading():
+    # round half up in r, half away from zero in the z offset, top index kept
+    assert O.harmonic_indices(8, 8, 8, 16, 1) == (8, 1)
+    assert O.harmonic_indices(7, 8, 8, 16, 1) == (8, 0)
+    assert O.harmonic_indices(9, 8, 8, 16, 1) == (8, 1)
+    assert O.harmonic_indices(24, 0, 8, 16, 1) == (7, 2)   # o=-8 -> -1; 24/16=1.5 -> 2
+    assert O.harmonic_indices(100, 3, 8, 16, 16) == (3, 100)
+    for ir in range(50):
+        for iz in range(17):
+            assert O.harmonic_indices(ir, iz, 8, 4, 4) == (iz, ir)
+
+
+def test_harmonic_stage_one_is_the_plane_and_constant_plane():
+    g = O.geometry(256, 8.0, 1.0, 16)
+    rng = np.random.default_rng(0)
+    P = rng.random((g.n_z, g.n_r))
+    Sp = O.harmonic_planes(P, g)
+    assert np.array_equal(Sp[0], P)
+    Sc = O.harmonic_planes(np.full((g.n_z, g.n_r), 2.5), g)
+    for st, h in enumerate(g.stages):
+        assert np.all(Sc[st] == 2.5 * h)
+
+
+@pytest.mark.parametrize("of", [3, -2, 0])
+def test_harmonic_sum_spike_train(of):
+    """Spikes v_j = 2^j at harmonic j of a fundamental; S_h at the top cell
+    must be exactly the binary sum of the harmonics that stage h reads."""
+    H = 16
+    g = O.geometry(4096, 48.0, 1.0, H)
+    rf = 97
+    P = np.zeros((g.n_z, g.n_r))
+    for j in range(1, H + 1):
+        P[g.iz0 + j * of, j * rf] += 2.0 ** j
+    top = (g.iz0 + H * of, H * rf)
+    Sp = O.harmonic_planes(P, g)
+    for st, h in enumerate(g.stages):
+        want = sum(2.0 ** (k * H // h) for k in range(1, h + 1))
+        assert Sp[st][top] == want, (h, Sp[st][top], want)
+
+
+def test_harmonic_sum_brute_force_small():
+    g = O.geometry(128, 4.0, 1.0, 8)
+    rng = np.random.default_rng(1)
+    P = rng.random((g.n_z, g.n_r))
+    Sp = O.harmonic_planes(P, g)
+    for st, h in enumerate(g.stages):
+        for iz in range(g.n_z):
+            for ir in range(g.n_r):
+                s = 0.0
+                for k in range(1, h + 1):
+                    j = k * (g.n_harm // h)
+                    siz, sir = O.harmonic_indices(ir, iz, g.iz0, g.n_harm, j)
+                    s += P[siz, sir]
+                assert abs(Sp[st, iz, ir] - s) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# thresholds
+# --------------------------------------------------------------------------
+def test_gamma_tail_factors_closed_form():
+    p = 0.5 * math.erfc(6 / math.sqrt(2))
+    G = O.gamma_tail_factors(16, 6.0)
+    assert abs(G[0] - (-math.log(p))) < 1e-10          # Q(1, x) = e^-x
+    for h, x in zip([1, 2, 4, 8, 16], G):
+        q = math.exp(-x) * sum(x ** k / math.factorial(k) for k in range(h))
+        assert abs(q - p) < 1e-9 * p
+
+
+def test_log_gamma_tail_matches_scipy_and_sigma_is_six_at_threshold():
+    for h in (1, 2, 4, 8, 16, 32):
+        for x in (0.5, 3.0, 20.0, 60.0):
+            assert abs(O.log_gamma_tail(h, x) - math.log(sps.gammaincc(h, x))) < 1e-9
+    G = O.gamma_tail_factors(16, 6.0)
+    for h, x in zip([1, 2, 4, 8, 16], G):
+        assert abs(O.sigma_equiv(x * 1.7, h, 1.7, 1.0, O.GAMMA_TAIL) - 6.0) < 1e-8
+
+
+def test_mean_plus_ksigma_threshold():
+    T = O.thresholds(4, 6.0, O.MEAN_PLUS_KSIGMA, 1.1, 0.9)
+    assert np.allclose(T, [1.1 + 6 * 0.9, 2.2 + 6 * math.sqrt(2) * 0.9, 4.4 + 12 * 0.9])
+
+
+# --------------------------------------------------------------------------
+# whole path on the 2^17-sample workload
+# --------------------------------------------------------------------------
+def test_sinusoid_workload_detected_at_expected_cell():
+    x = S.sinusoid_series()
+    r = O.search(x, 16.0, 2.0, 4)
+    P, g = r["P"], r["geom"]
+    iz, ir = np.unravel_index(np.argmax(P), P.shape)
+    assert ir == 5000 and g.z[iz] in (6.0, 8.0)
+    c = r["candidates"]
+    assert len(c) > 0 and np.all(np.diff(c["harm"]) >= 0)
+    assert np.any((c["ir"] == 5000) & (c["harm"] == 1))
+    # noise statistics after normalisation: mean near 1
+    assert abs(r["mean"] - 1.0) < 0.02
+
+
+def test_noise_only_false_alarms_are_rare():
+    x = S.white_noise(1 << 17, 99)
+    r = O.search(x, 16.0, 2.0, 4)
+    assert len(r["candidates"]) <= 3
