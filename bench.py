@@ -1,0 +1,449 @@
+#!/usr/bin/env python
+"""FDAS throughput on the SKA-like workload, one JSON line on stdout.
+
+Workload (paper §3: 600 s at 64 us, 193 acceleration trials; the batch of 256
+DM trials with BF16 storage beside FP32 is the mixed-precision batch case):
+each step searches a batch of `--batch` synthetic series of 2^23 FP32 samples
+(noise plus one accelerated sinusoid each) over z in [-96, 96] step 1 (193
+templates), 8192-bin overlap-save segments, 16 harmonics, 6-sigma threshold.
+The headline runs with BF16 spectra/templates/planes (FP32 arithmetic); the
+plain FP32 path is timed on the same inputs beside it.
+
+Timing: W untimed steps, then K steps bracketed by a barrier and
+torch.cuda.synchronize(), CUDA events on the caller's stream; every kernel
+group is also timed by the library's own events (fdas_profile_*) on the stream
+it runs on.  Inputs (8 GiB per batch) and the 1.6 GB power plane exceed the
+129 MB L2, so no explicit flush is needed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank searches its own batch (DM trials are
+independent: weak scaling, no data-path collective) and rank 0 prints the
+aggregate over max-over-ranks time.  `--impl reference` times the FP64 CPU
+oracle on a bounded sample of the same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "FDAS DM-trials/s (2^23 samples, 193 z); % HBM peak; BF16 vs FP32 at <=3% err"
+UNIT = "DM-trials/s"
+N_SAMPLES = 1 << 23
+TSAMP = 64e-6
+Z_MAX, Z_STEP = 96.0, 1.0
+SEG_LEN = 8192
+N_HARM = 16
+SIGMA = 6.0
+
+# FP32 ALU peak of a GB300: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz
+FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks and energy (read-only)
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons, power = [], None, set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_median": statistics.median(power) if power else None}
+
+
+class Energy:
+    """Total-energy counter through NVML (read-only), in joules."""
+
+    def __init__(self, gpu_index: int):
+        self.h = None
+        try:
+            nv = ctypes.CDLL("libnvidia-ml.so.1")
+            if nv.nvmlInit_v2() != 0:
+                return
+            h = ctypes.c_void_p()
+            if nv.nvmlDeviceGetHandleByIndex_v2(gpu_index, ctypes.byref(h)) != 0:
+                return
+            self.nv, self.h = nv, h
+        except OSError:
+            self.h = None
+
+    def read(self):
+        if self.h is None:
+            return None
+        v = ctypes.c_ulonglong(0)
+        if self.nv.nvmlDeviceGetTotalEnergyConsumption(self.h, ctypes.byref(v)) != 0:
+            return None
+        return v.value / 1000.0
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work per trial
+# ---------------------------------------------------------------------------
+def work_model(info, prec_bytes):
+    """Bytes/flops per trial of each kernel group (the roofline numerators)."""
+    b_s, b_p = (8, 4) if prec_bytes == 4 else (4, 2)
+    n, n_r, n_z, L, H = info.n_samples, info.n_r, info.n_z, info.seg_len, info.n_harm
+    gather = sum((j / H) ** 2 for j in range(1, H + 1))
+    plane = b_p * n_z * n_r
+    return {
+        # series read + spectrum write (FFT intermediates stay in L2)
+        "spectrum_bytes": 4 * n + b_s * n_r,
+        # FFT flop model per (segment, template): 4.25 L log2 L + 9 L
+        "correlate_flops": (4.25 * L * math.log2(L) + 9 * L) * info.n_seg * n_z,
+        "correlate_bytes": b_s * n_r + plane,
+        # harmonic gathers: unique cells of stream j are (j/H)^2 of the plane
+        "harmonic_bytes": plane * gather,
+        "alg_bytes": 4 * n + 2 * b_s * n_r + plane * (1 + gather),
+    }
+
+
+# ---------------------------------------------------------------------------
+# oracle on a bounded sample (CPU baseline and reference arm)
+# ---------------------------------------------------------------------------
+def oracle_trial_seconds(n_rows=9, r_decim=32):
+    """Seconds one 2^23-sample trial takes the FP64 oracle, from a sample:
+    spectrum + normalisation in full; the direct-correlation plane for
+    `n_rows` of the 193 templates (scaled by 193/n_rows); statistics, harmonic
+    sum and threshold over a 193 x (N_r/r_decim) plane (scaled by r_decim)."""
+    import numpy as np
+
+    import oracle as O
+    import synthetic as S
+    x, _ = S.batch_series(0, n=N_SAMPLES)
+    g = O.geometry(N_SAMPLES, Z_MAX, Z_STEP, N_HARM)
+    bank = O.template_bank(g)
+    t0 = time.perf_counter()
+    Xn, _ = O.normalise(O.spectrum(x), 2048)
+    t_spec = time.perf_counter() - t0
+    rows = np.linspace(0, g.n_z - 1, n_rows).round().astype(int)
+    sub = O.Bank(g, [bank.taps[i] for i in rows], bank.energy[rows])
+    sub_geom = O.geometry(N_SAMPLES, Z_MAX, Z_STEP, N_HARM)
+    sub_geom.n_z = len(rows)
+    sub_geom.m = g.m[rows]
+    sub.geom = sub_geom
+    t0 = time.perf_counter()
+    O.power_plane(Xn, sub)
+    t_rows = time.perf_counter() - t0
+    small = np.random.default_rng(0).exponential(size=(g.n_z, g.n_r // r_decim))
+    t0 = time.perf_counter()
+    mean, std = O.plane_stats(small)
+    O.candidates(small, g, mean, std, SIGMA)
+    t_hs = time.perf_counter() - t0
+    total = t_spec + t_rows * g.n_z / len(rows) + t_hs * r_decim
+    sample = (f"1 series of 2^23: spectrum+normalisation in full; direct-correlation plane for "
+              f"{len(rows)}/193 templates (x{g.n_z / len(rows):.1f}); stats+harmonic sum+"
+              f"threshold on 193 x N_r/{r_decim} cells (x{r_decim})")
+    return total, sample, time.perf_counter()
+
+
+def cpu_baseline():
+    import oracle as O
+    t0 = time.perf_counter()
+    per_trial, sample, _ = oracle_trial_seconds()
+    return {"value": 1.0 / per_trial, "unit": UNIT, "cores": O.threads(), "kind": "oracle",
+            "sample": sample, "wall_s": round(time.perf_counter() - t0, 2)}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    import oracle as O
+    O.build()
+    for _ in range(args.warmup):
+        oracle_trial_seconds()
+    per = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s, sample, _ = oracle_trial_seconds()
+        per.append(s)
+    wall = time.perf_counter() - t0
+    value = 1.0 / statistics.mean(per)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * statistics.mean(per), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": _config(args, "fp64 oracle"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": round(wall, 2),
+    }
+    print(json.dumps(line), flush=True)
+
+
+def _config(args, precision):
+    return {"workload": f"ska_2^23_193z_batch{args.batch}", "series_per_step": args.batch,
+            "n_samples": N_SAMPLES, "tsamp_s": TSAMP, "z_range": [-Z_MAX, Z_MAX],
+            "z_step": Z_STEP, "n_z": 193, "seg_len": SEG_LEN, "n_harm": N_HARM,
+            "threshold_sigma": SIGMA, "precision": precision,
+            "l2": "inputs larger than L2 (8 GiB batch, 1.6-3.2 GB plane per trial); no flush",
+            "parallelism": "dm-trial shards per GPU, no collective"}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_gpu(args, rank, world, local_rank, dist):
+    import numpy as np
+    import torch
+
+    import paper_2211_13517_gb300 as pkg
+    from paper_2211_13517_gb300 import capi
+    import synthetic as S
+
+    pkg.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+
+    xs, _ = S.torch_batch_series(args.batch, N_SAMPLES, base_seed=1000 + rank * args.batch,
+                                 device=dev)
+    torch.cuda.synchronize()
+    peak_hbm, peak_src = _peaks()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def timed(plan, inputs, steps, warmup, profile=False, energy=None, clocks=None):
+        for _ in range(warmup):
+            plan.search(inputs, capacity=1 << 16)
+        if profile:
+            plan.profile(True)
+        barrier()
+        if clocks:
+            clocks.start()
+        e0 = energy.read() if energy else None
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        nfound = 0
+        for _ in range(steps):
+            st, c, nf = plan.search(inputs, capacity=1 << 16)
+            nfound += nf
+        ev1.record(stream)
+        barrier()
+        e1 = energy.read() if energy else None
+        ck = clocks.stop() if clocks else None
+        ms = max_over_ranks(ev0.elapsed_time(ev1))
+        prof = plan.profile() if profile else None
+        joules = (e1 - e0) if (e0 is not None and e1 is not None) else None
+        return ms, prof, joules, ck, nfound
+
+    out = {}
+    energy = Energy(local_rank)
+    # --- headline: BF16 storage, device-resident inputs -------------------
+    plan = capi.Plan(N_SAMPLES, TSAMP, Z_MAX, Z_STEP, SEG_LEN, N_HARM, precision=capi.FDAS_BF16)
+    info = plan.info
+    clocks = ClockSampler(local_rank)
+    ms_bf16, prof_bf16, j_bf16, ck, nf_bf16 = timed(plan, xs, args.steps, args.warmup, True,
+                                                    energy, clocks)
+    # --- e2e: the same calls with the series in pinned host memory ----------
+    hosts = [x.cpu().pin_memory() for x in xs]
+    ms_e2e, _, _, _, nf_e2e = timed(plan, hosts, args.steps, max(1, args.warmup // 2))
+    del hosts
+    plan.close()
+    # --- FP32 path on the same inputs ---------------------------------------
+    ms_fp32 = prof_fp32 = None
+    if not args.no_fp32:
+        plan32 = capi.Plan(N_SAMPLES, TSAMP, Z_MAX, Z_STEP, SEG_LEN, N_HARM,
+                           precision=capi.FDAS_FP32)
+        ms_fp32, prof_fp32, j_fp32, _, _ = timed(plan32, xs, args.steps, args.warmup, True,
+                                                 energy)
+        plan32.close()
+
+    trials = args.batch * args.steps * world
+    value = trials / (ms_bf16 / 1000.0)
+    if rank != 0:
+        return
+    wm = work_model(info, 2)
+    groups = capi.PROFILE_GROUPS
+
+    def group_stats(prof, wmod):
+        res = {}
+        for g in groups:
+            launches, timed_n, ms = prof[g]
+            res[g] = {"launches": launches, "timed": timed_n, "ms_total": ms,
+                      "ms_per_trial": ms / max(1, prof["trials"])}
+        t_sp = res["spectrum"]["ms_per_trial"] / 1e3
+        t_co = res["correlate"]["ms_per_trial"] / 1e3
+        t_hs = res["harmonic"]["ms_per_trial"] / 1e3
+        res["spectrum"]["gbs"] = wmod["spectrum_bytes"] / t_sp / 1e9 if t_sp else None
+        res["correlate"]["tflops"] = wmod["correlate_flops"] / t_co / 1e12 if t_co else None
+        res["correlate"]["gbs"] = wmod["correlate_bytes"] / t_co / 1e9 if t_co else None
+        res["harmonic"]["gbs"] = wmod["harmonic_bytes"] / t_hs / 1e9 if t_hs else None
+        return res
+
+    k_bf16 = group_stats(prof_bf16, wm)
+    # dominant kernel by summed event time
+    dom = max(("correlate", "harmonic"), key=lambda g: k_bf16[g]["ms_total"])
+    traffic = _ncu_traffic(dom, "bf16")
+    if dom == "harmonic":
+        roof = {"kernel": "harmonic_threshold_kernel (bf16 plane)", "bound": "hbm",
+                "achieved": k_bf16["harmonic"]["gbs"], "peak": peak_hbm, "unit": "GB/s",
+                "frac": k_bf16["harmonic"]["gbs"] / peak_hbm, "traffic": traffic,
+                "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)"}
+    else:
+        a = k_bf16["correlate"]["tflops"]
+        roof = {"kernel": "correlate_kernel<8192> (bf16)", "bound": "alu", "achieved": a,
+                "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": a / FP32_ALU_PEAK_TFLOPS,
+                "traffic": traffic,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
+    alg_gbs = wm["alg_bytes"] * args.batch * args.steps / (ms_bf16 / 1000.0) / 1e9
+    launches = sum(prof_bf16[g][0] for g in groups)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_bf16 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "storage": "bf16",
+        "data": "synthetic", "config": _config(args, "bf16 storage, fp32 arithmetic"),
+        "roofline": roof,
+        "hbm_alg": {"bytes_per_trial": wm["alg_bytes"], "achieved_gbs": alg_gbs,
+                    "peak_gbs": peak_hbm, "frac": alg_gbs / peak_hbm,
+                    "note": f"B_alg of the whole path / step time, {peak_src} peak"},
+        "kernels": k_bf16,
+        "e2e": {"value": trials / (ms_e2e / 1000.0), "unit": UNIT,
+                "h2d_bytes_per_step": 4 * N_SAMPLES * args.batch,
+                "d2h_bytes_per_step": 20 * (nf_e2e // max(1, args.steps)) + 16},
+        "gpu_launches": launches,
+        "clocks": ck,
+        "joules_per_trial": (j_bf16 / (args.batch * args.steps)) if j_bf16 else None,
+        "candidates_per_trial": nf_bf16 / (args.batch * args.steps),
+    }
+    if ms_fp32 is not None:
+        v32 = trials / (ms_fp32 / 1000.0)
+        wm32 = work_model(info, 4)
+        line["fp32"] = {"value": v32, "ms_per_step": ms_fp32 / args.steps,
+                        "kernels": group_stats(prof_fp32, wm32),
+                        "joules_per_trial": (j_fp32 / (args.batch * args.steps)) if j_fp32 else None,
+                        "hbm_alg_frac": wm32["alg_bytes"] * args.batch * args.steps
+                        / (ms_fp32 / 1000.0) / 1e9 / peak_hbm}
+        line["bf16_speedup_vs_fp32"] = value / v32
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+
+
+def _ncu_traffic(kernel_group, prec):
+    """DRAM bytes per launch from the committed ncu summary, if it still
+    matches the kernel source; else None."""
+    try:
+        import hashlib
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            d = json.load(f)
+        ent = d[f"{kernel_group}_{prec}"]
+        src = os.path.join(ROOT, "paper_2211_13517_gb300", "csrc", ent["source"])
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        return ent["dram_bytes_per_launch_full_size"] if h == ent["source_sha"] else None
+    except Exception:
+        return None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--batch", type=int, default=256)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gb300":
+        ap.error("--warmup must be >= 3")
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as td
+        torch.cuda.set_device(local_rank)
+        td.init_process_group("nccl")
+        dist = td
+    run_gpu(args, rank, world, local_rank, dist)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

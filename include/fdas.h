@@ -1,0 +1,273 @@
+/*
+ * fdas.h -- C ABI of the GB300 (sm_103a) Fourier Domain Acceleration Search.
+ *
+ * Method: arXiv:2211.13517 (White, Adamek, Armour).  §2.1 "FDAS": a matched
+ * filter over a grid of constant-acceleration (constant-fdot) templates whose
+ * cost grows linearly with the number of templates; §2.2 "Mixed-Precision":
+ * the filter is an FFT-based (frequency-domain) convolution, the stage moved
+ * from FP32 to bfloat16, with at most 2.7% error in detection strength.
+ * The paper does not spell out the normalisation, the template formula, the
+ * harmonic sum or the threshold; the readings used here are written next to
+ * each entry point below.
+ *
+ * Conventions for every entry point:
+ *  - Pointers marked "device" are CUDA device (or managed) memory of the
+ *    current device; "host" pointers are ordinary CPU memory.  Nothing is
+ *    retained after the call returns unless stated.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Work is queued on it in order.
+ *  - Every call returns an fdas_status; no C++ exception crosses the ABI.
+ *    fdas_last_error() returns a thread-local message for the last failure.
+ *  - Arguments are validated before any GPU work is queued; an invalid
+ *    argument returns FDAS_ERR_ARG and queues nothing.
+ *  - There is no CPU fallback: without a usable CUDA device the calls that
+ *    need one return FDAS_ERR_CUDA.
+ *
+ * Notation: N = n_samples, N_r = N/2 spectral bins r = 0..N_r-1;
+ * z_i = (i - K) z_step, K = z_max/z_step, i = 0..n_z-1 (n_z = 2K+1, iz0 = K);
+ * m(z) = 8 + ceil(|z|/2) template half-width; H = n_harm.
+ */
+#ifndef FDAS_H
+#define FDAS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FDAS_OK = 0,
+    FDAS_ERR_ARG = 1,            /* invalid argument; nothing was queued     */
+    FDAS_ERR_CUDA = 2,           /* a CUDA runtime call failed               */
+    FDAS_ERR_OOM = 3,            /* device allocation failed                 */
+    FDAS_ERR_CAND_OVERFLOW = 4,  /* more candidates than the caller's buffer */
+    FDAS_ERR_NONFINITE = 5,      /* NaN or Inf in an input series           */
+    FDAS_ERR_TIMEOUT = 6,        /* a bounded device wait gave up            */
+    FDAS_ERR_UNSUPPORTED = 7     /* valid request this build cannot serve    */
+} fdas_status;
+
+/* storage precision of spectra, templates and the power plane; the
+ * arithmetic (butterflies, products, sums) is FP32 in every mode */
+enum { FDAS_FP32 = 0, FDAS_BF16 = 1, FDAS_FP16 = 2 };
+/* threshold rule */
+enum { FDAS_THRESH_GAMMA_TAIL = 0, FDAS_THRESH_MEAN_PLUS_KSIGMA = 1 };
+/* spectral normalisation */
+enum { FDAS_NORM_MEDIAN = 0, FDAS_NORM_NONE = 1 };
+
+typedef struct {
+    int32_t precision;       /* FDAS_FP32 (default), FDAS_BF16, FDAS_FP16          */
+    double threshold_sigma;  /* Gaussian-equivalent significance, default 6         */
+    int32_t threshold_mode;  /* FDAS_THRESH_GAMMA_TAIL (default)                    */
+    int32_t norm_mode;       /* FDAS_NORM_MEDIAN (default)                          */
+    int32_t norm_block;      /* bins per median block, power of 2 in [16, 8192]; 2048 */
+    int64_t max_candidates;  /* device candidate store per search call; 1<<20     */
+    int32_t autotune;        /* reserved, must be 0                                 */
+    int32_t reserved;
+} fdas_opts;
+
+/* One dedispersed time series (one DM trial).  `data` points to n_samples
+ * FP32 values (16-byte aligned) in device memory, or in host memory (pinned
+ * or pageable), which the search copies to the device itself; it is only
+ * read. */
+typedef struct {
+    const float *data;
+    int64_t n_samples;   /* must equal the plan's n_samples                 */
+    int32_t decimation;  /* informational (1 = full time resolution)        */
+    uint32_t trial_id;   /* caller's DM-trial id, echoed into candidates    */
+} fdas_series;
+
+/* One threshold crossing.  `harm` is the number of summed harmonics h (the
+ * stage), (ir, iz) the top-harmonic cell: spectral bin ir, z = (iz-K) z_step;
+ * the fundamental is at ir/h.  `power` is S_h, `sigma` its Gaussian-equivalent
+ * significance (see fdas_search). */
+typedef struct {
+    uint32_t trial_id;
+    uint32_t ir;
+    uint16_t iz;
+    uint16_t harm;
+    float power;
+    float sigma;
+} fdas_candidate;
+
+/* Read-only description of a plan (all derived from the create arguments). */
+typedef struct {
+    int64_t n_samples, n_r;
+    int32_t n_z, iz0, m_max, m_overlap, seg_len, valid_per_seg, n_seg;
+    int32_t n_harm, n_stages, precision, norm_block, threshold_mode;
+    double tsamp, z_max, z_step, threshold_sigma;
+    double stage_factor[6];   /* G_h = Q^-1(h, Phibar(sigma)) per stage h = 2^s */
+    int64_t workspace_bytes;  /* device memory the plan holds                  */
+} fdas_plan_info;
+
+typedef struct fdas_plan fdas_plan;
+
+/* Fill *opts with the defaults listed in fdas_opts. */
+void fdas_opts_default(fdas_opts *opts);
+
+/*
+ * Build a search plan on the current device: geometry, the frequency-domain
+ * template bank and all device workspace for one series at a time (two
+ * power planes, so consecutive series overlap).
+ *
+ * Templates (paper §2.1 matched filter; template formula is a reading): the
+ * response of a sinusoid whose frequency drifts by z bins over the
+ * observation, rho(q,z) = int_0^1 exp(2 pi i [(q - z/2)u + z u^2/2]) du,
+ * evaluated in FP64 on the GPU from Fresnel integrals; g_z[e] =
+ * conj(rho(e,z))/sqrt(E_z) for |e| <= m(z), E_z = sum_e |rho(e,z)|^2, placed
+ * circularly in seg_len points, transformed with an FP64 DFT, divided by
+ * seg_len and stored at the plan's precision.
+ *
+ * n_samples: power of 2 in [2^10, 2^24]. tsamp: sampling time in s (> 0,
+ * informational). z_max >= 0, z_step > 0 with z_max/z_step an integer and
+ * n_z <= 65535. seg_len: power of 2 in [1024, 16384], larger than
+ * 2*m_overlap + 64 where m_overlap = m(z_max) rounded up to a multiple of 8.
+ * n_harm in {1,2,4,8,16,32}.  opts may be NULL (defaults).
+ * On success *out owns device memory until fdas_plan_destroy.
+ * Errors: FDAS_ERR_ARG, FDAS_ERR_OOM, FDAS_ERR_CUDA (nothing is leaked).
+ * Synchronises the device before returning.
+ */
+fdas_status fdas_plan_create(fdas_plan **out, int64_t n_samples, double tsamp,
+                             double z_max, double z_step, int32_t seg_len,
+                             int32_t n_harm, const fdas_opts *opts);
+
+/* Release a plan (NULL is ignored).  Synchronises the plan's streams. */
+void fdas_plan_destroy(fdas_plan *plan);
+
+/* Copy the plan description into *info (host). */
+fdas_status fdas_plan_get_info(const fdas_plan *plan, fdas_plan_info *info);
+
+/*
+ * Full search of a batch of series: for each series, R2C FFT, median
+ * normalisation, overlap-save correlation with every template, |.|^2 power
+ * plane with FP64 mean/std, harmonic sum and threshold (the data-parallel hot
+ * path of the paper's FDAS, §2.1-§2.2).
+ *
+ * batch: host array of n_series descriptors.
+ * cands: caller-owned buffer (host or device) for `capacity` entries.
+ * n_found: host; receives the total number of threshold crossings.
+ * Candidates are every cell with S_h > T_h (strict), h = 1,2,4..H, ordered by
+ * (trial_id, harm, iz, ir).  T_h = mean * G_h (GAMMA_TAIL: G_h inverts the
+ * Gamma(h,1) upper tail at Phibar(threshold_sigma)) or h*mean +
+ * threshold_sigma*sqrt(h)*std (MEAN_PLUS_KSIGMA), with mean/std of the
+ * series' own plane.  sigma = Phibar^-1(Q(h, S/mean)) or
+ * (S - h mean)/(sqrt(h) std).
+ * Blocking: returns after the results are in `cands`.
+ * Errors: FDAS_ERR_ARG; FDAS_ERR_NONFINITE (a series holds NaN/Inf: no
+ * candidates are returned); FDAS_ERR_CAND_OVERFLOW (*n_found is the true
+ * total, the first `capacity` entries in the order above are written when the
+ * total fits the plan's max_candidates, otherwise an unspecified subset);
+ * FDAS_ERR_CUDA.
+ */
+fdas_status fdas_search(fdas_plan *plan, const fdas_series *batch,
+                        int32_t n_series, fdas_candidate *cands,
+                        int64_t capacity, int64_t *n_found, void *stream);
+
+/* ---------------------------------------------------------------------
+ * Stage entry points: one step of the path each, on device buffers, so each
+ * step can be checked on its own.  All are asynchronous on `stream`.
+ * --------------------------------------------------------------------- */
+
+/* Element type of spectra (complex pairs) and planes at each precision:
+ *   FDAS_FP32: float2 spectrum, float plane
+ *   FDAS_BF16: __nv_bfloat162 spectrum, __nv_bfloat16 plane
+ *   FDAS_FP16: __half2 spectrum, __half plane holding P/16 (range).       */
+
+/*
+ * R2C FFT + median normalisation of one series.  X_k = sum_n x_n
+ * exp(-2 pi i k n/N) for k in [0, N_r), X_0 set to 0; per block of
+ * norm_block bins the median mu_b of |X_k|^2 (block 0 without k = 0; the mean
+ * of the two middle values for an even count) gives X'_k = X_k sqrt(ln2/mu_b)
+ * (0 when mu_b = 0).  Exponential noise has median ln2 times its mean, so
+ * white noise leaves with unit mean power.
+ * series: device, N floats.  spectrum_out: device, N_r complex elements of
+ * the plan's precision.  medians_out: device float[N_r / norm_block] or NULL.
+ * Returns FDAS_ERR_NONFINITE after the fact only through fdas_search; this
+ * call does not check.
+ */
+fdas_status fdas_spectrum(fdas_plan *plan, const float *series,
+                          void *spectrum_out, float *medians_out, void *stream);
+
+/*
+ * Overlap-save correlation and power plane of one normalised spectrum:
+ * P[iz][r] = |sum_{|e|<=m(z_iz)} X'_{r-e} g_z[e]|^2 for r in [0, N_r), with
+ * X'_k = 0 outside [0, N_r), computed per segment of seg_len bins (forward
+ * FFT, product with the template bank, inverse FFT, keep the valid part).
+ * spectrum: device, N_r complex elements (plan precision).  plane_out:
+ * device, n_z * N_r elements (plan precision, row-major, r contiguous).
+ * stats_out: device double[2] = {mean, population std} of P in FP64 (may be
+ * NULL).
+ */
+fdas_status fdas_power_plane(fdas_plan *plan, const void *spectrum,
+                             void *plane_out, double *stats_out, void *stream);
+
+/*
+ * Harmonic sums of a plane, written out (for checking; the search itself
+ * never stores them).  Top-harmonic indexing: for the cell (ir, iz), o =
+ * iz - iz0, harmonic j of H reads (iz0 + sign(o) floor((|o| j + H/2)/H),
+ * floor((ir j + H/2)/H)); stage h = 2^s sums the harmonics j = kH/h, k=1..h.
+ * plane: device (plan precision).  sums_out: device float[n_stages][n_z][N_r].
+ */
+fdas_status fdas_harmonic_sums(fdas_plan *plan, const void *plane,
+                               float *sums_out, void *stream);
+
+/*
+ * Harmonic sum + threshold of one plane with given statistics.
+ * stats: device double[2] {mean, std} (e.g. from fdas_power_plane).
+ * cands/capacity/n_found as in fdas_search (one trial, id `trial_id`).
+ * Blocking.
+ */
+fdas_status fdas_threshold(fdas_plan *plan, const void *plane,
+                           const double *stats, uint32_t trial_id,
+                           fdas_candidate *cands, int64_t capacity,
+                           int64_t *n_found, void *stream);
+
+/*
+ * The template bank as the plan holds it.
+ * taps_out: host double[2 * sum_iz (2 m(z_iz) + 1)] or NULL -- the FP64
+ *   taps g_z[e] (re, im) for iz = 0.., e = -m..m, concatenated.
+ * energy_out: host double[n_z] or NULL -- E_z.
+ * bank_out: device, n_z * seg_len complex elements of the plan precision or
+ *   NULL -- the stored frequency-domain bank (FP16 holds seg_len times it).
+ * Blocking.
+ */
+fdas_status fdas_template_bank(fdas_plan *plan, double *taps_out,
+                               double *energy_out, void *bank_out,
+                               void *stream);
+
+/* ---------------------------------------------------------------------
+ * Tracing: per-kernel-group launch counts (always kept) and CUDA-event
+ * durations (kept while enabled).  Events are recorded on the stream each
+ * group runs on, so overlapping groups are each timed as they ran.
+ * Groups: [0] R2C FFT + normalisation, [1] fused correlation/power,
+ * [2] statistics + harmonic sum/threshold, [3] candidate ordering/output.
+ * --------------------------------------------------------------------- */
+enum { FDAS_PROF_SPECTRUM = 0, FDAS_PROF_CORRELATE = 1, FDAS_PROF_HARMONIC = 2,
+       FDAS_PROF_FINISH = 3 };
+
+typedef struct {
+    int64_t trials;        /* series searched since the last reset           */
+    int64_t launches[4];   /* kernel launches per group                      */
+    int64_t timed[4];      /* timed intervals per group                      */
+    double ms[4];          /* summed event-timed milliseconds per group      */
+} fdas_profile;
+
+/* Reset the counters; on != 0 also times every group of later fdas_search
+ * calls with CUDA events (a few microseconds per series). */
+fdas_status fdas_profile_enable(fdas_plan *plan, int32_t on);
+
+/* Copy the counters into *out (host). */
+fdas_status fdas_profile_read(const fdas_plan *plan, fdas_profile *out);
+
+/* Thread-local message describing the last failed call ("" if none). */
+const char *fdas_last_error(void);
+
+/* Library version string. */
+const char *fdas_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FDAS_H */

@@ -1,0 +1,345 @@
+"""ctypes binding of libfdas.so -- argument marshalling only.
+
+Every function here has the name of the C entry point it calls (see
+include/fdas.h for the semantics).  No step of the search runs in Python:
+the binding converts arguments, calls the library and turns a non-OK status
+into an exception.  If the library is missing, `lib()` raises; there is no
+fallback.
+
+`Plan` is a small convenience wrapper that takes torch tensors (device memory
+and streams only) and calls the same entry points.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import (POINTER, Structure, c_char_p, c_double, c_int32, c_int64,
+                    c_uint16, c_uint32, c_void_p, c_float)
+
+import numpy as np
+
+from .build import LIB
+
+FDAS_OK = 0
+FDAS_ERR_ARG = 1
+FDAS_ERR_CUDA = 2
+FDAS_ERR_OOM = 3
+FDAS_ERR_CAND_OVERFLOW = 4
+FDAS_ERR_NONFINITE = 5
+FDAS_ERR_TIMEOUT = 6
+FDAS_ERR_UNSUPPORTED = 7
+STATUS_NAMES = {0: "FDAS_OK", 1: "FDAS_ERR_ARG", 2: "FDAS_ERR_CUDA", 3: "FDAS_ERR_OOM",
+                4: "FDAS_ERR_CAND_OVERFLOW", 5: "FDAS_ERR_NONFINITE",
+                6: "FDAS_ERR_TIMEOUT", 7: "FDAS_ERR_UNSUPPORTED"}
+
+FDAS_FP32, FDAS_BF16, FDAS_FP16 = 0, 1, 2
+FDAS_THRESH_GAMMA_TAIL, FDAS_THRESH_MEAN_PLUS_KSIGMA = 0, 1
+FDAS_NORM_MEDIAN, FDAS_NORM_NONE = 0, 1
+
+EXPORTED = ["fdas_opts_default", "fdas_plan_create", "fdas_plan_destroy",
+            "fdas_plan_get_info", "fdas_search", "fdas_spectrum", "fdas_power_plane",
+            "fdas_harmonic_sums", "fdas_threshold", "fdas_template_bank",
+            "fdas_profile_enable", "fdas_profile_read", "fdas_last_error", "fdas_version"]
+
+
+class fdas_opts(Structure):
+    _fields_ = [("precision", c_int32), ("threshold_sigma", c_double),
+                ("threshold_mode", c_int32), ("norm_mode", c_int32),
+                ("norm_block", c_int32), ("max_candidates", c_int64),
+                ("autotune", c_int32), ("reserved", c_int32)]
+
+
+class fdas_series(Structure):
+    _fields_ = [("data", c_void_p), ("n_samples", c_int64), ("decimation", c_int32),
+                ("trial_id", c_uint32)]
+
+
+class fdas_candidate(Structure):
+    _fields_ = [("trial_id", c_uint32), ("ir", c_uint32), ("iz", c_uint16),
+                ("harm", c_uint16), ("power", c_float), ("sigma", c_float)]
+
+
+CANDIDATE_DTYPE = np.dtype([("trial_id", np.uint32), ("ir", np.uint32), ("iz", np.uint16),
+                            ("harm", np.uint16), ("power", np.float32), ("sigma", np.float32)])
+
+
+class fdas_plan_info(Structure):
+    _fields_ = [("n_samples", c_int64), ("n_r", c_int64),
+                ("n_z", c_int32), ("iz0", c_int32), ("m_max", c_int32), ("m_overlap", c_int32),
+                ("seg_len", c_int32), ("valid_per_seg", c_int32), ("n_seg", c_int32),
+                ("n_harm", c_int32), ("n_stages", c_int32), ("precision", c_int32),
+                ("norm_block", c_int32), ("threshold_mode", c_int32),
+                ("tsamp", c_double), ("z_max", c_double), ("z_step", c_double),
+                ("threshold_sigma", c_double), ("stage_factor", c_double * 6),
+                ("workspace_bytes", c_int64)]
+
+
+class fdas_profile(Structure):
+    _fields_ = [("trials", c_int64), ("launches", c_int64 * 4), ("timed", c_int64 * 4),
+                ("ms", c_double * 4)]
+
+
+PROFILE_GROUPS = ["spectrum", "correlate", "harmonic", "finish"]
+
+
+class FdasError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libfdas.so (built in-tree by build.build()); raise if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError(f"libfdas.so is not built ({LIB}); run "
+                               "paper_2211_13517_gb300.build.build() first")
+        L = ctypes.CDLL(LIB)
+        L.fdas_opts_default.argtypes = [POINTER(fdas_opts)]
+        L.fdas_opts_default.restype = None
+        L.fdas_plan_create.argtypes = [POINTER(c_void_p), c_int64, c_double, c_double,
+                                       c_double, c_int32, c_int32, POINTER(fdas_opts)]
+        L.fdas_plan_create.restype = c_int32
+        L.fdas_plan_destroy.argtypes = [c_void_p]
+        L.fdas_plan_destroy.restype = None
+        L.fdas_plan_get_info.argtypes = [c_void_p, POINTER(fdas_plan_info)]
+        L.fdas_plan_get_info.restype = c_int32
+        L.fdas_search.argtypes = [c_void_p, POINTER(fdas_series), c_int32, c_void_p, c_int64,
+                                  POINTER(c_int64), c_void_p]
+        L.fdas_search.restype = c_int32
+        L.fdas_spectrum.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
+        L.fdas_spectrum.restype = c_int32
+        L.fdas_power_plane.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
+        L.fdas_power_plane.restype = c_int32
+        L.fdas_harmonic_sums.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
+        L.fdas_harmonic_sums.restype = c_int32
+        L.fdas_threshold.argtypes = [c_void_p, c_void_p, c_void_p, c_uint32, c_void_p, c_int64,
+                                     POINTER(c_int64), c_void_p]
+        L.fdas_threshold.restype = c_int32
+        L.fdas_template_bank.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
+        L.fdas_template_bank.restype = c_int32
+        L.fdas_profile_enable.argtypes = [c_void_p, c_int32]
+        L.fdas_profile_enable.restype = c_int32
+        L.fdas_profile_read.argtypes = [c_void_p, POINTER(fdas_profile)]
+        L.fdas_profile_read.restype = c_int32
+        L.fdas_last_error.argtypes = []
+        L.fdas_last_error.restype = c_char_p
+        L.fdas_version.argtypes = []
+        L.fdas_version.restype = c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(status: int, where: str, allow=()):
+    if status != FDAS_OK and status not in allow:
+        raise FdasError(status, where, fdas_last_error())
+    return status
+
+
+# ----------------------------------------------------------------------------
+# the C entry points, same names
+# ----------------------------------------------------------------------------
+def fdas_opts_default() -> fdas_opts:
+    o = fdas_opts()
+    lib().fdas_opts_default(ctypes.byref(o))
+    return o
+
+
+def fdas_plan_create(n_samples, tsamp, z_max, z_step, seg_len, n_harm, opts=None) -> c_void_p:
+    h = c_void_p()
+    _check(lib().fdas_plan_create(ctypes.byref(h), n_samples, tsamp, z_max, z_step, seg_len,
+                                  n_harm, ctypes.byref(opts) if opts is not None else None),
+           "fdas_plan_create")
+    return h
+
+
+def fdas_plan_destroy(plan) -> None:
+    lib().fdas_plan_destroy(plan)
+
+
+def fdas_plan_get_info(plan) -> fdas_plan_info:
+    info = fdas_plan_info()
+    _check(lib().fdas_plan_get_info(plan, ctypes.byref(info)), "fdas_plan_get_info")
+    return info
+
+
+def fdas_search(plan, batch, n_series, cands_ptr, capacity, stream=None):
+    """Returns (status, n_found); FDAS_ERR_CAND_OVERFLOW is returned, not raised."""
+    n = c_int64(0)
+    st = lib().fdas_search(plan, batch, n_series, cands_ptr, capacity, ctypes.byref(n), stream)
+    _check(st, "fdas_search", allow=(FDAS_ERR_CAND_OVERFLOW,))
+    return st, n.value
+
+
+def fdas_spectrum(plan, series_ptr, spectrum_ptr, medians_ptr=None, stream=None):
+    _check(lib().fdas_spectrum(plan, series_ptr, spectrum_ptr, medians_ptr, stream), "fdas_spectrum")
+
+
+def fdas_power_plane(plan, spectrum_ptr, plane_ptr, stats_ptr=None, stream=None):
+    _check(lib().fdas_power_plane(plan, spectrum_ptr, plane_ptr, stats_ptr, stream),
+           "fdas_power_plane")
+
+
+def fdas_harmonic_sums(plan, plane_ptr, sums_ptr, stream=None):
+    _check(lib().fdas_harmonic_sums(plan, plane_ptr, sums_ptr, stream), "fdas_harmonic_sums")
+
+
+def fdas_threshold(plan, plane_ptr, stats_ptr, trial_id, cands_ptr, capacity, stream=None):
+    n = c_int64(0)
+    st = lib().fdas_threshold(plan, plane_ptr, stats_ptr, trial_id, cands_ptr, capacity,
+                              ctypes.byref(n), stream)
+    _check(st, "fdas_threshold", allow=(FDAS_ERR_CAND_OVERFLOW,))
+    return st, n.value
+
+
+def fdas_template_bank(plan, taps_ptr=None, energy_ptr=None, bank_ptr=None, stream=None):
+    _check(lib().fdas_template_bank(plan, taps_ptr, energy_ptr, bank_ptr, stream),
+           "fdas_template_bank")
+
+
+def fdas_profile_enable(plan, on: bool) -> None:
+    _check(lib().fdas_profile_enable(plan, 1 if on else 0), "fdas_profile_enable")
+
+
+def fdas_profile_read(plan) -> fdas_profile:
+    out = fdas_profile()
+    _check(lib().fdas_profile_read(plan, ctypes.byref(out)), "fdas_profile_read")
+    return out
+
+
+def fdas_last_error() -> str:
+    return lib().fdas_last_error().decode()
+
+
+def fdas_version() -> str:
+    return lib().fdas_version().decode()
+
+
+# ----------------------------------------------------------------------------
+# torch convenience wrapper (device memory and streams only)
+# ----------------------------------------------------------------------------
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return c_void_p(stream.cuda_stream)
+
+
+class Plan:
+    """Owns an fdas_plan; methods take torch tensors and call the C ABI."""
+
+    def __init__(self, n_samples, tsamp=64e-6, z_max=96.0, z_step=1.0, seg_len=8192,
+                 n_harm=16, precision=FDAS_FP32, threshold_sigma=6.0,
+                 threshold_mode=FDAS_THRESH_GAMMA_TAIL, norm_mode=FDAS_NORM_MEDIAN,
+                 norm_block=2048, max_candidates=1 << 20):
+        o = fdas_opts_default()
+        o.precision = precision
+        o.threshold_sigma = threshold_sigma
+        o.threshold_mode = threshold_mode
+        o.norm_mode = norm_mode
+        o.norm_block = norm_block
+        o.max_candidates = max_candidates
+        self.handle = fdas_plan_create(n_samples, tsamp, z_max, z_step, seg_len, n_harm, o)
+        self.info = fdas_plan_get_info(self.handle)
+
+    def close(self):
+        if self.handle:
+            fdas_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # dtypes of the plan's storage
+    @property
+    def spec_dtype(self):
+        import torch
+        return {FDAS_FP32: torch.float32, FDAS_BF16: torch.bfloat16,
+                FDAS_FP16: torch.float16}[self.info.precision]
+
+    def search(self, series, trial_ids=None, capacity=1 << 16, stream=None, out=None):
+        """series: list of 1-D float32 tensors (device or host).  Returns
+        (status, numpy structured array of the first min(n, capacity)
+        candidates, n_found)."""
+        n = len(series)
+        batch = (fdas_series * max(n, 1))()
+        for i, x in enumerate(series):
+            batch[i].data = x.data_ptr()
+            batch[i].n_samples = x.numel()
+            batch[i].decimation = 1
+            batch[i].trial_id = i if trial_ids is None else int(trial_ids[i])
+        if out is None:
+            out = np.zeros(capacity, dtype=CANDIDATE_DTYPE)
+        st, nf = fdas_search(self.handle, batch, n, out.ctypes.data_as(c_void_p), out.shape[0],
+                             _stream_ptr(stream))
+        return st, out[:min(nf, out.shape[0])], nf
+
+    def profile(self, on=None):
+        """Enable/disable tracing (resetting it) or, with no argument, read it
+        as a dict {group: (launches, timed intervals, ms)}."""
+        if on is not None:
+            fdas_profile_enable(self.handle, on)
+            return None
+        p = fdas_profile_read(self.handle)
+        return {"trials": p.trials, **{g: (p.launches[i], p.timed[i], p.ms[i])
+                                         for i, g in enumerate(PROFILE_GROUPS)}}
+
+    def spectrum(self, x, stream=None, medians=False):
+        import torch
+        nr = self.info.n_r
+        spec = torch.empty(2 * nr, dtype=self.spec_dtype, device=x.device)
+        med = None
+        if medians:
+            med = torch.empty(max(1, nr // min(self.info.norm_block, nr)), dtype=torch.float32,
+                              device=x.device)
+        fdas_spectrum(self.handle, c_void_p(x.data_ptr()), c_void_p(spec.data_ptr()),
+                      c_void_p(med.data_ptr()) if med is not None else None, _stream_ptr(stream))
+        return (spec, med) if medians else spec
+
+    def power_plane(self, spec, stream=None):
+        import torch
+        plane = torch.empty((self.info.n_z, self.info.n_r), dtype=self.spec_dtype,
+                            device=spec.device)
+        stats = torch.empty(2, dtype=torch.float64, device=spec.device)
+        fdas_power_plane(self.handle, c_void_p(spec.data_ptr()), c_void_p(plane.data_ptr()),
+                         c_void_p(stats.data_ptr()), _stream_ptr(stream))
+        return plane, stats
+
+    def harmonic_sums(self, plane, stream=None):
+        import torch
+        out = torch.empty((self.info.n_stages, self.info.n_z, self.info.n_r),
+                          dtype=torch.float32, device=plane.device)
+        fdas_harmonic_sums(self.handle, c_void_p(plane.data_ptr()), c_void_p(out.data_ptr()),
+                           _stream_ptr(stream))
+        return out
+
+    def threshold(self, plane, stats, trial_id=0, capacity=1 << 16, stream=None):
+        out = np.zeros(capacity, dtype=CANDIDATE_DTYPE)
+        st, nf = fdas_threshold(self.handle, c_void_p(plane.data_ptr()),
+                                c_void_p(stats.data_ptr()), trial_id,
+                                out.ctypes.data_as(c_void_p), capacity, _stream_ptr(stream))
+        return st, out[:min(nf, capacity)], nf
+
+    def template_bank(self):
+        """(taps list per z of complex128 arrays, energies)."""
+        info = self.info
+        m = [8 + int(np.ceil(abs(i - info.iz0) * info.z_step / 2.0 - 1e-9))
+             for i in range(info.n_z)]
+        n_taps = sum(2 * mm + 1 for mm in m)
+        taps = np.zeros(2 * n_taps, dtype=np.float64)
+        energy = np.zeros(info.n_z, dtype=np.float64)
+        fdas_template_bank(self.handle, taps.ctypes.data_as(c_void_p),
+                           energy.ctypes.data_as(c_void_p), None, None)
+        c = taps[0::2] + 1j * taps[1::2]
+        out, acc = [], 0
+        for mm in m:
+            out.append(c[acc:acc + 2 * mm + 1])
+            acc += 2 * mm + 1
+        return out, energy

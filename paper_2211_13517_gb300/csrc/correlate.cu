@@ -1,0 +1,153 @@
+// Fused overlap-save correlation -> |.|^2 power plane (the "convolution
+// stage" of paper §2.2; the matched filter of §2.1), plus FP64 statistics.
+//
+// The normalised spectrum lives in a zero-padded buffer: element m_ov + k
+// holds X'_k and everything outside k in [0, N_r) is 0, so segment s is the
+// contiguous window [s V, s V + L) of the buffer (local index j <-> bin
+// s V - m_ov + j).  One CTA takes one segment and a chunk of templates:
+//
+//   1. load the window and FFT it forward (CTA FFT, shared memory) -> S_s;
+//   2. keep, in registers, the 16 values of S_s this thread feeds into the
+//      first inverse pass;
+//   3. for each template z of the chunk: Y = S_s * bank_z (bank_z already
+//      holds FFT_L(g_z)/L), inverse FFT, and for the outputs j in
+//      [m_ov, m_ov + V) the power |y_j|^2 = P(s V + j - m_ov, z) goes to the
+//      plane (one coalesced store per output register).
+//
+// Since |e| <= m(z) <= m_ov the circular correlation equals the linear one on
+// the kept outputs, so P is exactly sum_e X'_{r-e} g_z[e] squared.  Every
+// thread keeps compensated FP32 sums of P and P^2 over its outputs; the CTA
+// adds them in FP64 in a fixed order and writes one partial per CTA, which the
+// statistics kernel reduces in a fixed order (deterministic mean and std).
+#include "fdas_internal.cuh"
+#include "fft_cta.cuh"
+
+namespace fdas {
+namespace {
+
+struct Kahan {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+};
+
+template <int L, class P>
+__global__ void __launch_bounds__(L / 16, 1)
+    correlate_kernel(const typename P::cpx *__restrict__ spec_pad,
+                     const typename P::cpx *__restrict__ bank, typename P::real *__restrict__ plane,
+                     double2 *__restrict__ partials, int64_t n_r, int n_z, int V, int m_ov,
+                     int z_per_cta, float bank_scale) {
+    using Fw = CtaFft<L, -1>;
+    using Iv = CtaFft<L, +1>;
+    constexpr int T = L / 16;
+    extern __shared__ float2 buf[];
+    __shared__ double red[2][T / 32];
+    const int tid = threadIdx.x;
+    const int64_t seg0 = (int64_t)blockIdx.x * V;
+    const int iz_begin = blockIdx.y * z_per_cta;
+    const int iz_end = min(n_z, iz_begin + z_per_cta);
+
+    float2 v[16], S[16], tw[Fw::NPASS];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = P::ld(spec_pad[seg0 + tid + r * T]);
+    Fw::make_twiddles(tid, tw);
+    Fw::to_smem(v, buf, tid, tw);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) S[r] = cscale(buf[fft_pad(tid + r * T)], bank_scale);
+    Iv::make_twiddles(tid, tw);
+
+    Kahan sp, sq;
+    constexpr int K = Iv::NPASS - 1;
+    constexpr int R = Iv::template Pass<K>::R, NB = Iv::template Pass<K>::NB;
+    for (int iz = iz_begin; iz < iz_end; ++iz) {
+        __syncthreads();   // the previous last pass has read buf
+        const typename P::cpx *h = bank + (int64_t)iz * L;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[r] = cmul(S[r], P::ld(__ldg(h + tid + r * T)));
+        float2 o[16];
+        Iv::to_regs(v, buf, tid, tw, o);
+        typename P::real *row = plane + (int64_t)iz * n_r;
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int n = Iv::last_index(tid, b, r);
+                const int64_t rr = seg0 + n - m_ov;
+                if (n >= m_ov && n < m_ov + V && rr < n_r) {
+                    const float2 y = o[b * R + r];
+                    const float pw = y.x * y.x + y.y * y.y;
+                    row[rr] = P::str(pw * P::plane_scale);
+                    sp.add(pw);
+                    sq.add(pw * pw);
+                }
+            }
+    }
+    // fixed-order FP64 reduction of the CTA's sums
+    double a = (double)sp.s - (double)sp.c, b2 = (double)sq.s - (double)sq.c;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, off);
+        b2 += __shfl_down_sync(0xffffffffu, b2, off);
+    }
+    if ((tid & 31) == 0) {
+        red[0][tid >> 5] = a;
+        red[1][tid >> 5] = b2;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double ta = 0.0, tb = 0.0;
+        for (int w = 0; w < T / 32; ++w) {
+            ta += red[0][w];
+            tb += red[1][w];
+        }
+        partials[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = make_double2(ta, tb);
+    }
+}
+
+template <int L, class P>
+fdas_status launch_L(Plan &p, const void *spec_padded, void *plane, double2 *partials,
+                     cudaStream_t s) {
+    const size_t smem = sizeof(float2) * CtaFft<L, 1>::SMEM_ELEMS;
+    auto k = correlate_kernel<L, P>;
+    FDAS_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int zper = (p.n_z + p.n_zchunk - 1) / p.n_zchunk;
+    dim3 grid(p.n_seg, p.n_zchunk);
+    const float bank_scale = P::id == FDAS_FP16 ? 1.0f / (float)p.L : 1.0f;
+    k<<<grid, L / 16, smem, s>>>((const typename P::cpx *)spec_padded,
+                                 (const typename P::cpx *)p.bank, (typename P::real *)plane,
+                                 partials, p.n_r, p.n_z, p.V, p.m_ov, zper, bank_scale);
+    FDAS_CUDA_TRY(cudaGetLastError());
+    return FDAS_OK;
+}
+
+template <class P>
+fdas_status launch_P(Plan &p, const void *spec, void *plane, double2 *partials, cudaStream_t s) {
+    switch (p.L) {
+        case 1024: return launch_L<1024, P>(p, spec, plane, partials, s);
+        case 2048: return launch_L<2048, P>(p, spec, plane, partials, s);
+        case 4096: return launch_L<4096, P>(p, spec, plane, partials, s);
+        case 8192: return launch_L<8192, P>(p, spec, plane, partials, s);
+        default:
+            set_error("seg_len " + std::to_string(p.L) + " is not built");
+            return FDAS_ERR_UNSUPPORTED;
+    }
+}
+
+}  // namespace
+
+int correlate_ctas(const Plan &p) { return p.n_seg * p.n_zchunk; }
+
+fdas_status launch_correlate(Plan &p, const void *spec_padded, void *plane, double2 *partials,
+                             cudaStream_t s) {
+    switch (p.prec) {
+        case FDAS_FP32: return launch_P<PrecF32>(p, spec_padded, plane, partials, s);
+        case FDAS_BF16: return launch_P<PrecBF16>(p, spec_padded, plane, partials, s);
+        default: return launch_P<PrecF16>(p, spec_padded, plane, partials, s);
+    }
+}
+
+}  // namespace fdas

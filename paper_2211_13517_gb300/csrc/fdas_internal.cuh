@@ -1,0 +1,167 @@
+// Internal declarations of the FDAS CUDA library (sm_103a).
+//
+// Shared by the .cu files of the library only.  Nothing here is part of the
+// C ABI (include/fdas.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/fdas.h"
+
+namespace fdas {
+
+// ---------------------------------------------------------------------------
+// error plumbing
+// ---------------------------------------------------------------------------
+void set_error(const std::string &msg);
+fdas_status cuda_status(cudaError_t e, const char *what);
+
+#define FDAS_CUDA_TRY(expr)                                                   \
+    do {                                                                      \
+        cudaError_t _e = (expr);                                              \
+        if (_e != cudaSuccess) return ::fdas::cuda_status(_e, #expr);         \
+    } while (0)
+
+#define FDAS_TRY(expr)                                                        \
+    do {                                                                      \
+        fdas_status _s = (expr);                                              \
+        if (_s != FDAS_OK) return _s;                                         \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// storage precisions: spectra/templates are complex pairs, planes scalars.
+// All arithmetic is FP32; conversion happens on load and store.
+// ---------------------------------------------------------------------------
+struct PrecF32 {
+    using cpx = float2;
+    using real = float;
+    static constexpr int id = FDAS_FP32;
+    static constexpr float plane_scale = 1.0f;       // stored = P * scale
+    __device__ __forceinline__ static float2 ld(const cpx &v) { return v; }
+    __device__ __forceinline__ static cpx st(float2 v) { return v; }
+    __device__ __forceinline__ static float ldr(real v) { return v; }
+    __device__ __forceinline__ static real str(float v) { return v; }
+};
+
+struct PrecBF16 {
+    using cpx = __nv_bfloat162;
+    using real = __nv_bfloat16;
+    static constexpr int id = FDAS_BF16;
+    static constexpr float plane_scale = 1.0f;
+    __device__ __forceinline__ static float2 ld(const cpx &v) { return __bfloat1622float2(v); }
+    __device__ __forceinline__ static cpx st(float2 v) { return __float22bfloat162_rn(v); }
+    __device__ __forceinline__ static float ldr(real v) { return __bfloat162float(v); }
+    __device__ __forceinline__ static real str(float v) { return __float2bfloat16_rn(v); }
+};
+
+struct PrecF16 {
+    using cpx = __half2;
+    using real = __half;
+    static constexpr int id = FDAS_FP16;
+    static constexpr float plane_scale = 0.0625f;    // P/16 keeps P < 1e6 in range
+    __device__ __forceinline__ static float2 ld(const cpx &v) { return __half22float2(v); }
+    __device__ __forceinline__ static cpx st(float2 v) { return __float22half2_rn(v); }
+    __device__ __forceinline__ static float ldr(real v) { return __half2float(v); }
+    __device__ __forceinline__ static real str(float v) { return __float2half_rn(v); }
+};
+
+inline size_t cpx_bytes(int prec) { return prec == FDAS_FP32 ? 8 : 4; }
+inline size_t real_bytes(int prec) { return prec == FDAS_FP32 ? 4 : 2; }
+
+// ---------------------------------------------------------------------------
+// candidate records kept on the device during a search
+// key bits: [0,23) ir, [23,39) iz, [39,42) stage, [42,64) batch rank
+// ---------------------------------------------------------------------------
+struct CandRec {
+    unsigned long long key;
+    float power;
+    float pad;
+};
+
+__host__ __device__ inline unsigned long long cand_key(uint32_t rank, int stage, int iz,
+                                                       uint32_t ir) {
+    return ((unsigned long long)rank << 42) | ((unsigned long long)stage << 39) |
+           ((unsigned long long)iz << 23) | (unsigned long long)ir;
+}
+
+// per-trial statistics and thresholds written on the device
+struct TrialStats {
+    double mean, std;
+    float thr[8];   // T_h per stage (FP32, compared against FP32 sums)
+};
+
+// ---------------------------------------------------------------------------
+// plan
+// ---------------------------------------------------------------------------
+struct Plan {
+    // geometry
+    int64_t n_samples, n_r;
+    int n_z, iz0, m_max, m_ov, L, V, n_seg, H, n_stages;
+    int prec, norm_mode, norm_block, thr_mode;
+    double tsamp, z_max, z_step, sigma;
+    double G[6];
+    int64_t max_cands;
+    int device;
+    int n_zchunk;           // z chunks per segment in the correlation grid
+    // FFT split of the N/2-point complex FFT in the spectrum stage
+    int fft_m1, fft_m2;     // M = m1 * m2 (m1 = 1: single pass)
+    // device memory
+    void *bank = nullptr;           // [n_z][L] cpx (plan precision)
+    double *taps = nullptr;         // FP64 taps, concatenated (re, im)
+    double *energy = nullptr;       // [n_z]
+    int64_t *tap_off = nullptr;     // [n_z] offsets (complex units)
+    int32_t *tap_m = nullptr;       // [n_z]
+    int64_t n_taps = 0;
+    float2 *fft_a = nullptr, *fft_b = nullptr;   // [M] scratch each
+    void *spec_pad = nullptr;       // [n_seg*V + 2 m_ov] cpx, zero-padded
+    void *plane[2] = {nullptr, nullptr};
+    double2 *partials[2] = {nullptr, nullptr};   // per correlation CTA
+    TrialStats *stats = nullptr;    // [stats_cap]
+    int64_t stats_cap = 0;
+    CandRec *cand = nullptr;        // [max_cands]
+    unsigned long long *cand_count = nullptr;
+    unsigned int *flags = nullptr;  // [0]: non-finite input seen
+    uint32_t *rank_ids = nullptr;   // [stats_cap] trial id per rank
+    fdas_candidate *out_stage = nullptr;   // [max_cands] ordered output
+    float *stage = nullptr;         // [n_samples] device copy of a host series
+    unsigned long long *host_small = nullptr;  // pinned: {count, flags}
+    int64_t ws_bytes = 0;
+    // tracing
+    bool profiling = false;
+    int64_t prof_trials = 0;
+    int64_t launches[4] = {0, 0, 0, 0};
+    int64_t timed[4] = {0, 0, 0, 0};
+    double prof_ms[4] = {0, 0, 0, 0};
+    std::vector<cudaEvent_t> events;   // pool for timed intervals
+    cudaStream_t aux = nullptr;     // second stream (harmonic sum overlap)
+    cudaEvent_t ev_conv[2] = {nullptr, nullptr};
+    cudaEvent_t ev_hsum[2] = {nullptr, nullptr};
+};
+
+// ---------------------------------------------------------------------------
+// launchers (each returns the launch status)
+// ---------------------------------------------------------------------------
+fdas_status launch_template_bank(Plan &p, cudaStream_t s);
+fdas_status launch_spectrum(Plan &p, const float *x, void *spec_out_padded,
+                            float *medians, cudaStream_t s);
+fdas_status launch_correlate(Plan &p, const void *spec_padded, void *plane,
+                             double2 *partials, cudaStream_t s);
+int correlate_ctas(const Plan &p);
+fdas_status launch_finalize_stats(Plan &p, const double2 *partials, int n_partials,
+                                  const double *given_stats, TrialStats *out,
+                                  cudaStream_t s);
+fdas_status launch_harmonic_threshold(Plan &p, const void *plane,
+                                      const TrialStats *st, uint32_t rank,
+                                      cudaStream_t s);
+fdas_status launch_harmonic_sums(Plan &p, const void *plane, float *out,
+                                 cudaStream_t s);
+fdas_status launch_candidates_finish(Plan &p, int64_t n, fdas_candidate *out_dev,
+                                     cudaStream_t s);
+
+}  // namespace fdas

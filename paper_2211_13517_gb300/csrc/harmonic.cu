@@ -1,0 +1,387 @@
+// Plane statistics, harmonic sum + threshold, and candidate ordering.
+//
+// Harmonic sum (top-harmonic indexing): the cell (ir, iz) with o = iz - iz0 is
+// taken as harmonic H of a signal; harmonic j reads the cell
+//     (iz0 + sign(o) floor((|o| j + H/2)/H),  floor((ir j + H/2)/H))
+// (rounded half up, the z offset away from zero), and stage h = 2^s sums the
+// harmonics j = k H / h, k = 1..h.  Stage s therefore equals stage s-1 plus
+// the odd multiples of H/h, so one pass over j = H, H/2, H/4, 3H/4, ... gives
+// every stage with H gathers per cell.
+//
+// Threshold: S_h > T_h (strict).  T_h = mean * G_h, G_h = Q^-1(h, Phibar(sigma))
+// (the Gamma(h, 1) tail of a sum of h unit exponentials at the Gaussian
+// false-alarm probability), or h mean + sigma sqrt(h) std.  Candidates are
+// appended with an atomic counter and ordered afterwards by
+// (trial rank, stage, iz, ir), so the list does not depend on scheduling.
+#include "fdas_internal.cuh"
+
+namespace fdas {
+namespace {
+
+constexpr int ilog2h(int n) { return n <= 1 ? 0 : 1 + ilog2h(n >> 1); }
+
+// ---------------------------------------------------------------------------
+// statistics: mean/std from the correlation partials (fixed order) or from a
+// given {mean, std}; thresholds per stage
+// ---------------------------------------------------------------------------
+struct ThrParams {
+    double G[6];
+    double sigma;
+    int mode, n_stages;
+    double n_cells;
+};
+
+__global__ void finalize_stats_kernel(const double2 *__restrict__ partials, int n_partials,
+                                      const double *__restrict__ given, TrialStats *out,
+                                      ThrParams tp) {
+    __shared__ double sa[256], sb[256];
+    const int tid = threadIdx.x;
+    double a = 0.0, b = 0.0;
+    if (given == nullptr) {
+        for (int i = tid; i < n_partials; i += 256) {
+            a += partials[i].x;
+            b += partials[i].y;
+        }
+    }
+    sa[tid] = a;
+    sb[tid] = b;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (tid < w) {
+            sa[tid] += sa[tid + w];
+            sb[tid] += sb[tid + w];
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        double mean, sd;
+        if (given != nullptr) {
+            mean = given[0];
+            sd = given[1];
+        } else {
+            mean = sa[0] / tp.n_cells;
+            const double var = sb[0] / tp.n_cells - mean * mean;
+            sd = sqrt(var > 0.0 ? var : 0.0);
+        }
+        out->mean = mean;
+        out->std = sd;
+        for (int s = 0; s < 8; ++s) {
+            float t = 0.f;
+            if (s < tp.n_stages) {
+                const double h = (double)(1 << s);
+                t = tp.mode == FDAS_THRESH_GAMMA_TAIL ? (float)(mean * tp.G[s])
+                                                     : (float)(h * mean + tp.sigma * sqrt(h) * sd);
+            }
+            out->thr[s] = t;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// harmonic sum + threshold: one thread per top cell; grid x over r, y over iz
+// ---------------------------------------------------------------------------
+constexpr int kHsThreads = 256;
+
+template <class P, int H>
+__global__ void __launch_bounds__(kHsThreads)
+    harmonic_threshold_kernel(const typename P::real *__restrict__ plane, int64_t n_r, int iz0,
+                              const TrialStats *__restrict__ st, uint32_t rank,
+                              CandRec *__restrict__ cand, unsigned long long *__restrict__ count,
+                              int64_t cap) {
+    constexpr int NST = ilog2h(H) + 1;
+    const int64_t ir = (int64_t)blockIdx.x * kHsThreads + threadIdx.x;
+    const int iz = blockIdx.y;
+    if (ir >= n_r) return;
+    const int o = iz - iz0;
+    const int ao = o < 0 ? -o : o;
+    const float inv = 1.0f / P::plane_scale;
+    float thr[NST];
+#pragma unroll
+    for (int s = 0; s < NST; ++s) thr[s] = st->thr[s];
+    float S = 0.f;
+#pragma unroll
+    for (int s = 0; s < NST; ++s) {
+        const int h = 1 << s;
+        const int step = H / h;
+#pragma unroll
+        for (int k = 1; k <= h; k += 2) {
+            const int j = k * step;
+            const int64_t sr = (ir * j + H / 2) / H;
+            const int so = (ao * j + H / 2) / H;
+            const int siz = iz0 + (o < 0 ? -so : so);
+            S += P::ldr(__ldg(plane + (int64_t)siz * n_r + sr));
+        }
+        const float Sv = S * inv;
+        if (Sv > thr[s]) {
+            const unsigned long long idx = atomicAdd(count, 1ull);
+            if ((int64_t)idx < cap) {
+                CandRec c;
+                c.key = cand_key(rank, s, iz, (uint32_t)ir);
+                c.power = Sv;
+                c.pad = 0.f;
+                cand[idx] = c;
+            }
+        }
+    }
+}
+
+// all stage sums written out (checking entry point)
+template <class P, int H>
+__global__ void __launch_bounds__(kHsThreads)
+    harmonic_sums_kernel(const typename P::real *__restrict__ plane, int64_t n_r, int n_z,
+                         int iz0, float *__restrict__ out) {
+    constexpr int NST = ilog2h(H) + 1;
+    const int64_t ir = (int64_t)blockIdx.x * kHsThreads + threadIdx.x;
+    const int iz = blockIdx.y;
+    if (ir >= n_r) return;
+    const int o = iz - iz0;
+    const int ao = o < 0 ? -o : o;
+    const float inv = 1.0f / P::plane_scale;
+    float S = 0.f;
+#pragma unroll
+    for (int s = 0; s < NST; ++s) {
+        const int h = 1 << s;
+        const int step = H / h;
+#pragma unroll
+        for (int k = 1; k <= h; k += 2) {
+            const int j = k * step;
+            const int64_t sr = (ir * j + H / 2) / H;
+            const int so = (ao * j + H / 2) / H;
+            const int siz = iz0 + (o < 0 ? -so : so);
+            S += P::ldr(__ldg(plane + (int64_t)siz * n_r + sr));
+        }
+        out[((int64_t)s * n_z + iz) * n_r + ir] = S * inv;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// candidate ordering and output
+// ---------------------------------------------------------------------------
+constexpr int kSortThreads = 1024;
+constexpr int kSortSmemMax = 8192;
+
+__device__ __forceinline__ bool rec_less(const CandRec &a, const CandRec &b) { return a.key < b.key; }
+
+// single-CTA bitonic sort in shared memory of n <= 8192 records (padded)
+__global__ void __launch_bounds__(kSortThreads) sort_small_kernel(CandRec *rec, int n, int n_pow2) {
+    extern __shared__ CandRec sh[];
+    const int tid = threadIdx.x;
+    for (int i = tid; i < n_pow2; i += kSortThreads) {
+        if (i < n) sh[i] = rec[i];
+        else {
+            sh[i].key = ~0ull;
+            sh[i].power = 0.f;
+            sh[i].pad = 0.f;
+        }
+    }
+    __syncthreads();
+    for (int k = 2; k <= n_pow2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = tid; i < n_pow2; i += kSortThreads) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const bool up = (i & k) == 0;
+                    const CandRec a = sh[i], b = sh[ixj];
+                    if (rec_less(b, a) == up) {
+                        sh[i] = b;
+                        sh[ixj] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = tid; i < n; i += kSortThreads) rec[i] = sh[i];
+}
+
+// pad records [n, n_pow2) with the largest key
+__global__ void pad_kernel(CandRec *rec, int64_t n, int64_t n_pow2) {
+    const int64_t i = n + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_pow2) return;
+    CandRec c;
+    c.key = ~0ull;
+    c.power = 0.f;
+    c.pad = 0.f;
+    rec[i] = c;
+}
+
+// one compare-exchange step (k, j) of a bitonic network over n_pow2 records
+__global__ void bitonic_step_kernel(CandRec *rec, int64_t n_pow2, int64_t k, int64_t j) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_pow2) return;
+    const int64_t ixj = i ^ j;
+    if (ixj <= i) return;
+    const bool up = (i & k) == 0;
+    const CandRec a = rec[i], b = rec[ixj];
+    if (rec_less(b, a) == up) {
+        rec[i] = b;
+        rec[ixj] = a;
+    }
+}
+
+// log Q(h, x) for integer h: Q = exp(-x) sum_{k<h} x^k / k!
+__device__ double log_gamma_tail(int h, double x) {
+    if (x <= 0.0) return 0.0;
+    const double lx = log(x);
+    double lt[32];
+    double mx = -1e300, lf = 0.0;
+    for (int k = 0; k < h; ++k) {
+        if (k > 0) lf += log((double)k);
+        lt[k] = k * lx - lf;
+        mx = fmax(mx, lt[k]);
+    }
+    double s = 0.0;
+    for (int k = 0; k < h; ++k) s += exp(lt[k] - mx);
+    return -x + mx + log(s);
+}
+
+// Gaussian-equivalent sigma of an upper-tail probability given as log p
+__device__ double sigma_from_logp(double lp) {
+    if (lp > -700.0) return -normcdfinv(exp(lp));
+    // log Phibar(s) = -s^2/2 - log(s sqrt(2 pi)) + log(1 - 1/s^2 + 3/s^4 - 15/s^6)
+    double s = sqrt(-2.0 * lp);
+    for (int it = 0; it < 30; ++it) {
+        const double s2 = s * s;
+        const double corr = log1p(-1.0 / s2 + 3.0 / (s2 * s2) - 15.0 / (s2 * s2 * s2));
+        const double f = -0.5 * s2 - log(s) - 0.91893853320467274178 + corr - lp;
+        const double df = -s - 1.0 / s;   // derivative of the leading terms
+        const double ns = s - f / df;
+        if (fabs(ns - s) < 1e-14 * s) {
+            s = ns;
+            break;
+        }
+        s = ns;
+    }
+    return s;
+}
+
+__global__ void finish_kernel(const CandRec *__restrict__ rec, int64_t n,
+                              const TrialStats *__restrict__ st, const uint32_t *__restrict__ ids,
+                              fdas_candidate *__restrict__ out, int mode) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const CandRec c = rec[i];
+    const uint32_t rank = (uint32_t)(c.key >> 42);
+    const int s = (int)((c.key >> 39) & 7);
+    const int iz = (int)((c.key >> 23) & 0xffff);
+    const uint32_t ir = (uint32_t)(c.key & 0x7fffff);
+    const int h = 1 << s;
+    const TrialStats t = st[rank];
+    double sig;
+    if (mode == FDAS_THRESH_GAMMA_TAIL)
+        sig = sigma_from_logp(log_gamma_tail(h, (double)c.power / t.mean));
+    else
+        sig = ((double)c.power - h * t.mean) / (sqrt((double)h) * t.std);
+    fdas_candidate o;
+    o.trial_id = ids[rank];
+    o.ir = ir;
+    o.iz = (uint16_t)iz;
+    o.harm = (uint16_t)h;
+    o.power = c.power;
+    o.sigma = (float)sig;
+    out[i] = o;
+}
+
+template <class P>
+fdas_status launch_hs_P(Plan &p, const void *plane, const TrialStats *st, uint32_t rank,
+                        cudaStream_t s) {
+    dim3 grid((unsigned)((p.n_r + kHsThreads - 1) / kHsThreads), p.n_z);
+    const auto *pl = (const typename P::real *)plane;
+    switch (p.H) {
+#define HS_CASE(HH)                                                                          \
+    case HH:                                                                                 \
+        harmonic_threshold_kernel<P, HH><<<grid, kHsThreads, 0, s>>>(                        \
+            pl, p.n_r, p.iz0, st, rank, p.cand, p.cand_count, p.max_cands);                  \
+        break;
+        HS_CASE(1) HS_CASE(2) HS_CASE(4) HS_CASE(8) HS_CASE(16) HS_CASE(32)
+#undef HS_CASE
+        default: set_error("bad n_harm"); return FDAS_ERR_ARG;
+    }
+    FDAS_CUDA_TRY(cudaGetLastError());
+    return FDAS_OK;
+}
+
+template <class P>
+fdas_status launch_sums_P(Plan &p, const void *plane, float *out, cudaStream_t s) {
+    dim3 grid((unsigned)((p.n_r + kHsThreads - 1) / kHsThreads), p.n_z);
+    const auto *pl = (const typename P::real *)plane;
+    switch (p.H) {
+#define HS_CASE(HH)                                                                          \
+    case HH:                                                                                 \
+        harmonic_sums_kernel<P, HH><<<grid, kHsThreads, 0, s>>>(pl, p.n_r, p.n_z, p.iz0, out); \
+        break;
+        HS_CASE(1) HS_CASE(2) HS_CASE(4) HS_CASE(8) HS_CASE(16) HS_CASE(32)
+#undef HS_CASE
+        default: set_error("bad n_harm"); return FDAS_ERR_ARG;
+    }
+    FDAS_CUDA_TRY(cudaGetLastError());
+    return FDAS_OK;
+}
+
+}  // namespace
+
+fdas_status launch_finalize_stats(Plan &p, const double2 *partials, int n_partials,
+                                  const double *given_stats, TrialStats *out, cudaStream_t s) {
+    ThrParams tp;
+    for (int i = 0; i < 6; ++i) tp.G[i] = p.G[i];
+    tp.sigma = p.sigma;
+    tp.mode = p.thr_mode;
+    tp.n_stages = p.n_stages;
+    tp.n_cells = (double)p.n_z * (double)p.n_r;
+    finalize_stats_kernel<<<1, 256, 0, s>>>(partials, n_partials, given_stats, out, tp);
+    FDAS_CUDA_TRY(cudaGetLastError());
+    return FDAS_OK;
+}
+
+fdas_status launch_harmonic_threshold(Plan &p, const void *plane, const TrialStats *st,
+                                      uint32_t rank, cudaStream_t s) {
+    switch (p.prec) {
+        case FDAS_FP32: return launch_hs_P<PrecF32>(p, plane, st, rank, s);
+        case FDAS_BF16: return launch_hs_P<PrecBF16>(p, plane, st, rank, s);
+        default: return launch_hs_P<PrecF16>(p, plane, st, rank, s);
+    }
+}
+
+fdas_status launch_harmonic_sums(Plan &p, const void *plane, float *out, cudaStream_t s) {
+    switch (p.prec) {
+        case FDAS_FP32: return launch_sums_P<PrecF32>(p, plane, out, s);
+        case FDAS_BF16: return launch_sums_P<PrecBF16>(p, plane, out, s);
+        default: return launch_sums_P<PrecF16>(p, plane, out, s);
+    }
+}
+
+// sort the first n stored records and convert them to fdas_candidate
+fdas_status launch_candidates_finish(Plan &p, int64_t n, fdas_candidate *out_dev, cudaStream_t s) {
+    if (n <= 0) return FDAS_OK;
+    int64_t n_pow2 = 1;
+    while (n_pow2 < n) n_pow2 <<= 1;
+    if (n_pow2 <= kSortSmemMax) {
+        const size_t smem = sizeof(CandRec) * (size_t)n_pow2;
+        FDAS_CUDA_TRY(cudaFuncSetAttribute(sort_small_kernel,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        sort_small_kernel<<<1, kSortThreads, smem, s>>>(p.cand, (int)n, (int)n_pow2);
+        FDAS_CUDA_TRY(cudaGetLastError());
+        p.launches[FDAS_PROF_FINISH] += 1;
+    } else {
+        // the record store holds a power-of-two number of entries >= max_cands
+        const unsigned nb = (unsigned)((n_pow2 + 255) / 256);
+        if (n_pow2 > n) {
+            pad_kernel<<<(unsigned)((n_pow2 - n + 255) / 256), 256, 0, s>>>(p.cand, n, n_pow2);
+            FDAS_CUDA_TRY(cudaGetLastError());
+            p.launches[FDAS_PROF_FINISH] += 1;
+        }
+        for (int64_t k = 2; k <= n_pow2; k <<= 1)
+            for (int64_t j = k >> 1; j > 0; j >>= 1) {
+                bitonic_step_kernel<<<nb, 256, 0, s>>>(p.cand, n_pow2, k, j);
+                FDAS_CUDA_TRY(cudaGetLastError());
+                p.launches[FDAS_PROF_FINISH] += 1;
+            }
+    }
+    finish_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p.cand, n, p.stats, p.rank_ids,
+                                                               out_dev, p.thr_mode);
+    FDAS_CUDA_TRY(cudaGetLastError());
+    p.launches[FDAS_PROF_FINISH] += 1;
+    return FDAS_OK;
+}
+
+}  // namespace fdas

@@ -1,0 +1,660 @@
+// C ABI of the FDAS library: plan construction, the search driver and the
+// stage entry points (declared in include/fdas.h).
+#include "fdas_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+namespace fdas {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+fdas_status cuda_status(cudaError_t e, const char *what) {
+    set_error(std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+    return e == cudaErrorMemoryAllocation ? FDAS_ERR_OOM : FDAS_ERR_CUDA;
+}
+
+static fdas_status arg_error(const std::string &msg) {
+    set_error(msg);
+    return FDAS_ERR_ARG;
+}
+
+// ---------------------------------------------------------------------------
+// threshold factors: G_h = Q^-1(h, Phibar(sigma)), Q the regularised upper
+// incomplete gamma function of integer order h (Poisson form, log scale),
+// solved by bisection in FP64 on the host at plan time.
+// ---------------------------------------------------------------------------
+static double log_q_int(int h, double x) {
+    if (x <= 0.0) return 0.0;
+    const double lx = std::log(x);
+    std::vector<double> lt(h);
+    double lf = 0.0, mx = -1e300;
+    for (int k = 0; k < h; ++k) {
+        if (k > 0) lf += std::log((double)k);
+        lt[k] = k * lx - lf;
+        mx = std::max(mx, lt[k]);
+    }
+    double s = 0.0;
+    for (int k = 0; k < h; ++k) s += std::exp(lt[k] - mx);
+    return -x + mx + std::log(s);
+}
+
+static double gamma_tail_factor(int h, double sigma) {
+    const double lp = std::log(0.5 * std::erfc(sigma / std::sqrt(2.0)));
+    double lo = 0.0, hi = 1.0;
+    while (log_q_int(h, hi) > lp) hi *= 2.0;
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (log_q_int(h, mid) > lp) lo = mid;
+        else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+static bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+static int ilog2(int64_t v) {
+    int l = 0;
+    while ((int64_t(1) << l) < v) ++l;
+    return l;
+}
+
+static void free_plan_memory(Plan *p) {
+    cudaFree(p->bank);
+    cudaFree(p->taps);
+    cudaFree(p->energy);
+    cudaFree(p->tap_off);
+    cudaFree(p->tap_m);
+    cudaFree(p->fft_a);
+    cudaFree(p->fft_b);
+    cudaFree(p->spec_pad);
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(p->plane[b]);
+        cudaFree(p->partials[b]);
+        if (p->ev_conv[b]) cudaEventDestroy(p->ev_conv[b]);
+        if (p->ev_hsum[b]) cudaEventDestroy(p->ev_hsum[b]);
+    }
+    cudaFree(p->stats);
+    cudaFree(p->rank_ids);
+    cudaFree(p->cand);
+    cudaFree(p->cand_count);
+    cudaFree(p->flags);
+    cudaFree(p->out_stage);
+    cudaFree(p->stage);
+    if (p->host_small) cudaFreeHost(p->host_small);
+    for (cudaEvent_t e : p->events) cudaEventDestroy(e);
+    if (p->aux) cudaStreamDestroy(p->aux);
+}
+
+template <class T>
+static fdas_status dalloc(Plan &p, T **ptr, size_t bytes) {
+    cudaError_t e = cudaMalloc((void **)ptr, bytes);
+    if (e != cudaSuccess) {
+        *ptr = nullptr;
+        cudaGetLastError();
+        set_error("cudaMalloc(" + std::to_string(bytes) + " bytes) failed: " +
+                  cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? FDAS_ERR_OOM : FDAS_ERR_CUDA;
+    }
+    p.ws_bytes += (int64_t)bytes;
+    return FDAS_OK;
+}
+
+static fdas_status grow_stats(Plan &p, int64_t need) {
+    if (need <= p.stats_cap) return FDAS_OK;
+    int64_t cap = std::max<int64_t>(need, 2 * p.stats_cap);
+    FDAS_CUDA_TRY(cudaDeviceSynchronize());
+    cudaFree(p.stats);
+    cudaFree(p.rank_ids);
+    p.stats = nullptr;
+    p.rank_ids = nullptr;
+    p.ws_bytes -= p.stats_cap * (int64_t)(sizeof(TrialStats) + sizeof(uint32_t));
+    p.stats_cap = 0;
+    FDAS_TRY(dalloc(p, &p.stats, sizeof(TrialStats) * (size_t)cap));
+    FDAS_TRY(dalloc(p, &p.rank_ids, sizeof(uint32_t) * (size_t)cap));
+    p.stats_cap = cap;
+    return FDAS_OK;
+}
+
+static int64_t next_pow2(int64_t v) {
+    int64_t p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+// correlation grid: z chunks per segment chosen to fill the GPU evenly,
+// counting one extra forward FFT per CTA
+static int choose_zchunks(const Plan &p, int slots) {
+    int best = 1;
+    double best_eff = 0.0;
+    for (int c = 1; c <= std::min(32, p.n_z); ++c) {
+        const int zper = (p.n_z + c - 1) / c;
+        const int64_t ctas = (int64_t)p.n_seg * c;
+        const int64_t waves = (ctas + slots - 1) / slots;
+        const double eff = (double)p.n_seg * p.n_z / ((double)slots * waves * (zper + 1));
+        if (eff > best_eff + 1e-9) {
+            best_eff = eff;
+            best = c;
+        }
+    }
+    return best;
+}
+
+static fdas_status create(Plan *&out, int64_t n_samples, double tsamp, double z_max, double z_step,
+                          int32_t seg_len, int32_t n_harm, const fdas_opts *o) {
+    if (!is_pow2(n_samples) || n_samples < (1 << 10) || n_samples > (1 << 24))
+        return arg_error("n_samples must be a power of two in [2^10, 2^24]");
+    if (!(tsamp > 0.0) || !std::isfinite(tsamp)) return arg_error("tsamp must be > 0");
+    if (!(z_step > 0.0) || !std::isfinite(z_step) || !(z_max >= 0.0) || !std::isfinite(z_max))
+        return arg_error("need z_step > 0 and z_max >= 0");
+    const double ratio = z_max / z_step;
+    const double K = std::round(ratio);
+    if (std::fabs(ratio - K) > 1e-9 * std::max(1.0, ratio))
+        return arg_error("z_max / z_step must be an integer");
+    if (2 * K + 1 > 65535) return arg_error("too many z trials (n_z > 65535)");
+    if (!(n_harm == 1 || n_harm == 2 || n_harm == 4 || n_harm == 8 || n_harm == 16 || n_harm == 32))
+        return arg_error("n_harm must be one of 1, 2, 4, 8, 16, 32");
+    if (!is_pow2(seg_len) || seg_len < 1024 || seg_len > 16384)
+        return arg_error("seg_len must be a power of two in [1024, 16384]");
+    if (o->precision != FDAS_FP32 && o->precision != FDAS_BF16 && o->precision != FDAS_FP16)
+        return arg_error("unknown precision");
+    if (o->threshold_mode != FDAS_THRESH_GAMMA_TAIL && o->threshold_mode != FDAS_THRESH_MEAN_PLUS_KSIGMA)
+        return arg_error("unknown threshold_mode");
+    if (o->norm_mode != FDAS_NORM_MEDIAN && o->norm_mode != FDAS_NORM_NONE)
+        return arg_error("unknown norm_mode");
+    if (!is_pow2(o->norm_block) || o->norm_block < 16 || o->norm_block > 8192)
+        return arg_error("norm_block must be a power of two in [16, 8192]");
+    if (!(o->threshold_sigma > 0.0) || o->threshold_sigma > 37.0)
+        return arg_error("threshold_sigma must be in (0, 37]");
+    if (o->max_candidates < 1 || o->max_candidates > (int64_t(1) << 26))
+        return arg_error("max_candidates must be in [1, 2^26]");
+    if (o->autotune != 0) return arg_error("autotune is reserved and must be 0");
+
+    Plan *pp = new (std::nothrow) Plan();
+    if (!pp) return arg_error("out of host memory");
+    Plan &p = *pp;
+    p.n_samples = n_samples;
+    p.n_r = n_samples / 2;
+    p.tsamp = tsamp;
+    p.z_max = z_max;
+    p.z_step = z_step;
+    p.iz0 = (int)K;
+    p.n_z = 2 * (int)K + 1;
+    p.H = n_harm;
+    p.n_stages = ilog2(n_harm) + 1;
+    p.prec = o->precision;
+    p.norm_mode = o->norm_mode;
+    p.norm_block = o->norm_block;
+    p.thr_mode = o->threshold_mode;
+    p.sigma = o->threshold_sigma;
+    p.max_cands = o->max_candidates;
+    for (int s = 0; s < 6; ++s) p.G[s] = s < p.n_stages ? gamma_tail_factor(1 << s, p.sigma) : 0.0;
+
+    // template half-widths m(z) = 8 + ceil(|z|/2) on the exact grid
+    std::vector<int32_t> m(p.n_z);
+    std::vector<int64_t> off(p.n_z);
+    int64_t acc = 0;
+    p.m_max = 0;
+    for (int i = 0; i < p.n_z; ++i) {
+        const double az = std::fabs((double)(i - p.iz0)) * z_step;
+        m[i] = 8 + (int32_t)std::ceil(az / 2.0 - 1e-9);
+        p.m_max = std::max(p.m_max, (int)m[i]);
+        off[i] = acc;
+        acc += 2 * m[i] + 1;
+    }
+    p.n_taps = acc;
+    p.m_ov = (p.m_max + 7) / 8 * 8;
+    p.L = seg_len;
+    if (seg_len <= 2 * p.m_ov + 64) {
+        delete pp;
+        return arg_error("seg_len must exceed 2*m_overlap + 64 (m_overlap = " +
+                         std::to_string(p.m_ov) + ")");
+    }
+    if (seg_len > 8192) {
+        delete pp;
+        set_error("seg_len 16384 is accepted by the interface but not built in this version");
+        return FDAS_ERR_UNSUPPORTED;
+    }
+    p.V = p.L - 2 * p.m_ov;
+    p.n_seg = (int)((p.n_r + p.V - 1) / p.V);
+    const int lm = ilog2(p.n_r);
+    if (p.n_r <= 8192) {
+        p.fft_m1 = 1;
+        p.fft_m2 = (int)p.n_r;
+    } else {
+        p.fft_m1 = 1 << (lm / 2);
+        p.fft_m2 = 1 << (lm - lm / 2);
+    }
+
+    cudaError_t ce = cudaGetDevice(&p.device);
+    if (ce != cudaSuccess) {
+        delete pp;
+        return cuda_status(ce, "cudaGetDevice");
+    }
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device);
+    p.n_zchunk = choose_zchunks(p, std::max(1, sms));
+
+    fdas_status st = FDAS_OK;
+    auto fail = [&](fdas_status s) {
+        cudaDeviceSynchronize();
+        free_plan_memory(pp);
+        delete pp;
+        return s;
+    };
+#define PLAN_TRY(expr)                  \
+    do {                                \
+        st = (expr);                    \
+        if (st != FDAS_OK) return fail(st); \
+    } while (0)
+#define PLAN_CUDA(expr)                                   \
+    do {                                                  \
+        cudaError_t _e = (expr);                          \
+        if (_e != cudaSuccess) return fail(cuda_status(_e, #expr)); \
+    } while (0)
+
+    const size_t cb = cpx_bytes(p.prec), rb = real_bytes(p.prec);
+    PLAN_TRY(dalloc(p, &p.bank, cb * (size_t)p.n_z * p.L));
+    PLAN_TRY(dalloc(p, &p.taps, sizeof(double) * 2 * (size_t)p.n_taps));
+    PLAN_TRY(dalloc(p, &p.energy, sizeof(double) * p.n_z));
+    PLAN_TRY(dalloc(p, &p.tap_off, sizeof(int64_t) * p.n_z));
+    PLAN_TRY(dalloc(p, &p.tap_m, sizeof(int32_t) * p.n_z));
+    if (p.fft_m1 > 1) PLAN_TRY(dalloc(p, &p.fft_a, sizeof(float2) * (size_t)p.n_r));
+    PLAN_TRY(dalloc(p, &p.fft_b, sizeof(float2) * (size_t)p.n_r));
+    const size_t pad_elems = (size_t)p.n_seg * p.V + 2 * (size_t)p.m_ov;
+    PLAN_TRY(dalloc(p, &p.spec_pad, cb * pad_elems));
+    for (int b = 0; b < 2; ++b) {
+        PLAN_TRY(dalloc(p, &p.plane[b], rb * (size_t)p.n_z * (size_t)p.n_r));
+        PLAN_TRY(dalloc(p, &p.partials[b], sizeof(double2) * (size_t)correlate_ctas(p)));
+        PLAN_CUDA(cudaEventCreateWithFlags(&p.ev_conv[b], cudaEventDisableTiming));
+        PLAN_CUDA(cudaEventCreateWithFlags(&p.ev_hsum[b], cudaEventDisableTiming));
+    }
+    PLAN_TRY(grow_stats(p, 64));
+    const int64_t rec_cap = next_pow2(p.max_cands);
+    PLAN_TRY(dalloc(p, &p.cand, sizeof(CandRec) * (size_t)rec_cap));
+    PLAN_TRY(dalloc(p, &p.cand_count, sizeof(unsigned long long)));
+    PLAN_TRY(dalloc(p, &p.flags, sizeof(unsigned int)));
+    PLAN_TRY(dalloc(p, &p.out_stage, sizeof(fdas_candidate) * (size_t)p.max_cands));
+    PLAN_TRY(dalloc(p, &p.stage, sizeof(float) * (size_t)p.n_samples));
+    PLAN_CUDA(cudaMallocHost((void **)&p.host_small, 4 * sizeof(unsigned long long)));
+    PLAN_CUDA(cudaStreamCreateWithFlags(&p.aux, cudaStreamNonBlocking));
+
+    PLAN_CUDA(cudaMemset(p.spec_pad, 0, cb * pad_elems));
+    PLAN_CUDA(cudaMemcpy(p.tap_off, off.data(), sizeof(int64_t) * p.n_z, cudaMemcpyHostToDevice));
+    PLAN_CUDA(cudaMemcpy(p.tap_m, m.data(), sizeof(int32_t) * p.n_z, cudaMemcpyHostToDevice));
+    PLAN_TRY(launch_template_bank(p, p.aux));
+    PLAN_CUDA(cudaStreamSynchronize(p.aux));
+    PLAN_CUDA(cudaDeviceSynchronize());
+#undef PLAN_TRY
+#undef PLAN_CUDA
+    out = pp;
+    return FDAS_OK;
+}
+
+// pointer kinds
+static bool is_device_ptr(const void *ptr) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// sort/convert the stored candidates and copy them out; blocking
+static fdas_status collect(Plan &p, fdas_candidate *cands, int64_t capacity, int64_t *n_found,
+                           cudaStream_t s) {
+    FDAS_CUDA_TRY(cudaMemcpyAsync(p.host_small, p.cand_count, sizeof(unsigned long long),
+                                  cudaMemcpyDeviceToHost, s));
+    FDAS_CUDA_TRY(cudaMemcpyAsync(p.host_small + 1, p.flags, sizeof(unsigned int),
+                                  cudaMemcpyDeviceToHost, s));
+    FDAS_CUDA_TRY(cudaStreamSynchronize(s));
+    const int64_t total = (int64_t)p.host_small[0];
+    const unsigned int flags = (unsigned int)(p.host_small[1] & 0xffffffffu);
+    if (flags & 1u) {
+        *n_found = 0;
+        set_error("non-finite values in an input series");
+        return FDAS_ERR_NONFINITE;
+    }
+    const int64_t stored = std::min(total, p.max_cands);
+    FDAS_TRY(launch_candidates_finish(p, stored, p.out_stage, s));
+    const int64_t n_copy = std::min(stored, capacity);
+    if (n_copy > 0)
+        FDAS_CUDA_TRY(cudaMemcpyAsync(cands, p.out_stage, sizeof(fdas_candidate) * (size_t)n_copy,
+                                      cudaMemcpyDefault, s));
+    FDAS_CUDA_TRY(cudaStreamSynchronize(s));
+    *n_found = total;
+    if (total > capacity) {
+        set_error("candidate buffer too small: " + std::to_string(total) + " found, capacity " +
+                  std::to_string(capacity));
+        return FDAS_ERR_CAND_OVERFLOW;
+    }
+    return FDAS_OK;
+}
+
+class DeviceGuard {
+   public:
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&old_);
+        if (old_ != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (cur != old_) cudaSetDevice(old_);
+    }
+
+   private:
+    int old_ = 0;
+};
+
+// event pool for the tracing intervals
+static fdas_status events_reserve(Plan &p, size_t n) {
+    while (p.events.size() < n) {
+        cudaEvent_t e;
+        FDAS_CUDA_TRY(cudaEventCreate(&e));
+        p.events.push_back(e);
+    }
+    return FDAS_OK;
+}
+
+struct Interval {
+    int group;
+    cudaEvent_t a, b;
+};
+
+static void accumulate(Plan &p, const std::vector<Interval> &iv) {
+    for (const Interval &x : iv) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, x.a, x.b) == cudaSuccess) {
+            p.prof_ms[x.group] += ms;
+            p.timed[x.group] += 1;
+        } else {
+            cudaGetLastError();
+        }
+    }
+}
+
+static fdas_status search(Plan &p, const fdas_series *batch, int32_t n_series,
+                          fdas_candidate *cands, int64_t capacity, int64_t *n_found,
+                          cudaStream_t s) {
+    if (n_series < 0) return arg_error("n_series < 0");
+    if (n_series > (1 << 22)) return arg_error("n_series > 2^22");
+    if (n_series > 0 && batch == nullptr) return arg_error("batch is NULL");
+    if (n_found == nullptr) return arg_error("n_found is NULL");
+    if (capacity < 0 || (capacity > 0 && cands == nullptr)) return arg_error("bad cands/capacity");
+    for (int32_t i = 0; i < n_series; ++i) {
+        if (batch[i].data == nullptr) return arg_error("series " + std::to_string(i) + " has NULL data");
+        if (batch[i].n_samples != p.n_samples)
+            return arg_error("series " + std::to_string(i) + " length differs from the plan");
+        if (((uintptr_t)batch[i].data & 15u) != 0)
+            return arg_error("series " + std::to_string(i) + " is not 16-byte aligned");
+    }
+    *n_found = 0;
+    DeviceGuard guard(p.device);
+    FDAS_TRY(grow_stats(p, std::max<int64_t>(1, n_series)));
+    // rank = position in trial_id order (stable), so the output order is
+    // (trial_id, stage, iz, ir)
+    std::vector<int32_t> order(n_series), rank(n_series);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t a, int32_t b) { return batch[a].trial_id < batch[b].trial_id; });
+    std::vector<uint32_t> ids(std::max(1, (int)n_series));
+    for (int32_t i = 0; i < n_series; ++i) {
+        rank[order[i]] = i;
+        ids[i] = batch[order[i]].trial_id;
+    }
+    if (n_series > 0)
+        FDAS_CUDA_TRY(cudaMemcpyAsync(p.rank_ids, ids.data(), sizeof(uint32_t) * n_series,
+                                      cudaMemcpyHostToDevice, s));
+    FDAS_CUDA_TRY(cudaMemsetAsync(p.cand_count, 0, sizeof(unsigned long long), s));
+    FDAS_CUDA_TRY(cudaMemsetAsync(p.flags, 0, sizeof(unsigned int), s));
+    const size_t cb = cpx_bytes(p.prec);
+    void *spec = (char *)p.spec_pad + cb * (size_t)p.m_ov;
+    std::vector<Interval> iv;
+    if (p.profiling) {
+        FDAS_TRY(events_reserve(p, 6 * (size_t)n_series + 2));
+        iv.reserve(3 * (size_t)n_series + 1);
+    }
+    size_t ev = 0;
+    auto mark = [&](cudaStream_t st) -> cudaEvent_t {
+        cudaEvent_t e = p.events[ev++];
+        cudaEventRecord(e, st);
+        return e;
+    };
+    const int spectrum_launches = (p.fft_m1 == 1 ? 1 : 2) + 1;
+    for (int32_t t = 0; t < n_series; ++t) {
+        const int b = t & 1;
+        const float *x = batch[t].data;
+        if (!is_device_ptr(x)) {
+            FDAS_CUDA_TRY(cudaMemcpyAsync(p.stage, x, sizeof(float) * (size_t)p.n_samples,
+                                          cudaMemcpyHostToDevice, s));
+            x = p.stage;
+        }
+        if (t >= 2) FDAS_CUDA_TRY(cudaStreamWaitEvent(s, p.ev_hsum[b], 0));
+        cudaEvent_t e0 = p.profiling ? mark(s) : nullptr;
+        FDAS_TRY(launch_spectrum(p, x, spec, nullptr, s));
+        cudaEvent_t e1 = p.profiling ? mark(s) : nullptr;
+        FDAS_TRY(launch_correlate(p, p.spec_pad, p.plane[b], p.partials[b], s));
+        cudaEvent_t e2 = p.profiling ? mark(s) : nullptr;
+        FDAS_CUDA_TRY(cudaEventRecord(p.ev_conv[b], s));
+        FDAS_CUDA_TRY(cudaStreamWaitEvent(p.aux, p.ev_conv[b], 0));
+        cudaEvent_t e3 = p.profiling ? mark(p.aux) : nullptr;
+        TrialStats *ts = p.stats + rank[t];
+        FDAS_TRY(launch_finalize_stats(p, p.partials[b], correlate_ctas(p), nullptr, ts, p.aux));
+        FDAS_TRY(launch_harmonic_threshold(p, p.plane[b], ts, (uint32_t)rank[t], p.aux));
+        cudaEvent_t e4 = p.profiling ? mark(p.aux) : nullptr;
+        FDAS_CUDA_TRY(cudaEventRecord(p.ev_hsum[b], p.aux));
+        p.launches[FDAS_PROF_SPECTRUM] += spectrum_launches;
+        p.launches[FDAS_PROF_CORRELATE] += 1;
+        p.launches[FDAS_PROF_HARMONIC] += 2;
+        if (p.profiling) {
+            iv.push_back({FDAS_PROF_SPECTRUM, e0, e1});
+            iv.push_back({FDAS_PROF_CORRELATE, e1, e2});
+            iv.push_back({FDAS_PROF_HARMONIC, e3, e4});
+        }
+    }
+    p.prof_trials += n_series;
+    for (int b = 0; b < 2 && b < n_series; ++b)
+        FDAS_CUDA_TRY(cudaStreamWaitEvent(s, p.ev_hsum[(n_series - 1 - b) & 1], 0));
+    cudaEvent_t f0 = p.profiling ? mark(s) : nullptr;
+    fdas_status st = collect(p, cands, capacity, n_found, s);
+    if (p.profiling) {
+        cudaEvent_t f1 = mark(s);
+        cudaEventSynchronize(f1);
+        iv.push_back({FDAS_PROF_FINISH, f0, f1});
+        accumulate(p, iv);
+    }
+    return st;
+}
+
+}  // namespace fdas
+
+using namespace fdas;
+
+extern "C" {
+
+void fdas_opts_default(fdas_opts *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = FDAS_FP32;
+    o->threshold_sigma = 6.0;
+    o->threshold_mode = FDAS_THRESH_GAMMA_TAIL;
+    o->norm_mode = FDAS_NORM_MEDIAN;
+    o->norm_block = 2048;
+    o->max_candidates = int64_t(1) << 20;
+    o->autotune = 0;
+}
+
+fdas_status fdas_plan_create(fdas_plan **out, int64_t n_samples, double tsamp, double z_max,
+                             double z_step, int32_t seg_len, int32_t n_harm, const fdas_opts *opts) {
+    try {
+        if (!out) return arg_error("out is NULL");
+        *out = nullptr;
+        fdas_opts o;
+        fdas_opts_default(&o);
+        if (opts) o = *opts;
+        Plan *p = nullptr;
+        fdas_status s = create(p, n_samples, tsamp, z_max, z_step, seg_len, n_harm, &o);
+        if (s == FDAS_OK) *out = reinterpret_cast<fdas_plan *>(p);
+        return s;
+    } catch (...) {
+        set_error("unexpected C++ exception in fdas_plan_create");
+        return FDAS_ERR_CUDA;
+    }
+}
+
+void fdas_plan_destroy(fdas_plan *plan) {
+    if (!plan) return;
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    DeviceGuard guard(p->device);
+    cudaDeviceSynchronize();
+    free_plan_memory(p);
+    delete p;
+}
+
+fdas_status fdas_plan_get_info(const fdas_plan *plan, fdas_plan_info *info) {
+    if (!plan || !info) return arg_error("NULL argument");
+    const Plan &p = *reinterpret_cast<const Plan *>(plan);
+    std::memset(info, 0, sizeof(*info));
+    info->n_samples = p.n_samples;
+    info->n_r = p.n_r;
+    info->n_z = p.n_z;
+    info->iz0 = p.iz0;
+    info->m_max = p.m_max;
+    info->m_overlap = p.m_ov;
+    info->seg_len = p.L;
+    info->valid_per_seg = p.V;
+    info->n_seg = p.n_seg;
+    info->n_harm = p.H;
+    info->n_stages = p.n_stages;
+    info->precision = p.prec;
+    info->norm_block = p.norm_block;
+    info->threshold_mode = p.thr_mode;
+    info->tsamp = p.tsamp;
+    info->z_max = p.z_max;
+    info->z_step = p.z_step;
+    info->threshold_sigma = p.sigma;
+    for (int s = 0; s < 6; ++s) info->stage_factor[s] = p.G[s];
+    info->workspace_bytes = p.ws_bytes;
+    return FDAS_OK;
+}
+
+fdas_status fdas_search(fdas_plan *plan, const fdas_series *batch, int32_t n_series,
+                        fdas_candidate *cands, int64_t capacity, int64_t *n_found, void *stream) {
+    try {
+        if (!plan) return arg_error("plan is NULL");
+        return search(*reinterpret_cast<Plan *>(plan), batch, n_series, cands, capacity, n_found,
+                      (cudaStream_t)stream);
+    } catch (...) {
+        set_error("unexpected C++ exception in fdas_search");
+        return FDAS_ERR_CUDA;
+    }
+}
+
+fdas_status fdas_spectrum(fdas_plan *plan, const float *series, void *spectrum_out,
+                          float *medians_out, void *stream) {
+    if (!plan || !series || !spectrum_out) return arg_error("NULL argument");
+    if (((uintptr_t)series & 15u) != 0) return arg_error("series is not 16-byte aligned");
+    Plan &p = *reinterpret_cast<Plan *>(plan);
+    DeviceGuard guard(p.device);
+    return launch_spectrum(p, series, spectrum_out, medians_out, (cudaStream_t)stream);
+}
+
+fdas_status fdas_power_plane(fdas_plan *plan, const void *spectrum, void *plane_out,
+                             double *stats_out, void *stream) {
+    if (!plan || !spectrum || !plane_out) return arg_error("NULL argument");
+    Plan &p = *reinterpret_cast<Plan *>(plan);
+    DeviceGuard guard(p.device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t cb = cpx_bytes(p.prec);
+    FDAS_CUDA_TRY(cudaMemcpyAsync((char *)p.spec_pad + cb * (size_t)p.m_ov, spectrum,
+                                  cb * (size_t)p.n_r, cudaMemcpyDeviceToDevice, s));
+    FDAS_TRY(launch_correlate(p, p.spec_pad, plane_out, p.partials[0], s));
+    if (stats_out) {
+        FDAS_TRY(launch_finalize_stats(p, p.partials[0], correlate_ctas(p), nullptr, p.stats, s));
+        FDAS_CUDA_TRY(cudaMemcpyAsync(stats_out, p.stats, 2 * sizeof(double),
+                                      cudaMemcpyDeviceToDevice, s));
+    }
+    return FDAS_OK;
+}
+
+fdas_status fdas_harmonic_sums(fdas_plan *plan, const void *plane, float *sums_out, void *stream) {
+    if (!plan || !plane || !sums_out) return arg_error("NULL argument");
+    Plan &p = *reinterpret_cast<Plan *>(plan);
+    DeviceGuard guard(p.device);
+    return launch_harmonic_sums(p, plane, sums_out, (cudaStream_t)stream);
+}
+
+fdas_status fdas_threshold(fdas_plan *plan, const void *plane, const double *stats,
+                           uint32_t trial_id, fdas_candidate *cands, int64_t capacity,
+                           int64_t *n_found, void *stream) {
+    if (!plan || !plane || !stats || !n_found) return arg_error("NULL argument");
+    if (capacity < 0 || (capacity > 0 && !cands)) return arg_error("bad cands/capacity");
+    Plan &p = *reinterpret_cast<Plan *>(plan);
+    DeviceGuard guard(p.device);
+    cudaStream_t s = (cudaStream_t)stream;
+    *n_found = 0;
+    FDAS_CUDA_TRY(cudaMemcpyAsync(p.rank_ids, &trial_id, sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+    FDAS_CUDA_TRY(cudaMemsetAsync(p.cand_count, 0, sizeof(unsigned long long), s));
+    FDAS_CUDA_TRY(cudaMemsetAsync(p.flags, 0, sizeof(unsigned int), s));
+    FDAS_TRY(launch_finalize_stats(p, nullptr, 0, stats, p.stats, s));
+    FDAS_TRY(launch_harmonic_threshold(p, plane, p.stats, 0, s));
+    return collect(p, cands, capacity, n_found, s);
+}
+
+fdas_status fdas_template_bank(fdas_plan *plan, double *taps_out, double *energy_out,
+                               void *bank_out, void *stream) {
+    if (!plan) return arg_error("plan is NULL");
+    Plan &p = *reinterpret_cast<Plan *>(plan);
+    DeviceGuard guard(p.device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (taps_out)
+        FDAS_CUDA_TRY(cudaMemcpyAsync(taps_out, p.taps, sizeof(double) * 2 * (size_t)p.n_taps,
+                                      cudaMemcpyDeviceToHost, s));
+    if (energy_out)
+        FDAS_CUDA_TRY(cudaMemcpyAsync(energy_out, p.energy, sizeof(double) * p.n_z,
+                                      cudaMemcpyDeviceToHost, s));
+    if (bank_out)
+        FDAS_CUDA_TRY(cudaMemcpyAsync(bank_out, p.bank, cpx_bytes(p.prec) * (size_t)p.n_z * p.L,
+                                      cudaMemcpyDeviceToDevice, s));
+    FDAS_CUDA_TRY(cudaStreamSynchronize(s));
+    return FDAS_OK;
+}
+
+fdas_status fdas_profile_enable(fdas_plan *plan, int32_t on) {
+    if (!plan) return arg_error("plan is NULL");
+    Plan &p = *reinterpret_cast<Plan *>(plan);
+    p.profiling = on != 0;
+    p.prof_trials = 0;
+    for (int g = 0; g < 4; ++g) {
+        p.launches[g] = 0;
+        p.timed[g] = 0;
+        p.prof_ms[g] = 0.0;
+    }
+    return FDAS_OK;
+}
+
+fdas_status fdas_profile_read(const fdas_plan *plan, fdas_profile *out) {
+    if (!plan || !out) return arg_error("NULL argument");
+    const Plan &p = *reinterpret_cast<const Plan *>(plan);
+    out->trials = p.prof_trials;
+    for (int g = 0; g < 4; ++g) {
+        out->launches[g] = p.launches[g];
+        out->timed[g] = p.timed[g];
+        out->ms[g] = p.prof_ms[g];
+    }
+    return FDAS_OK;
+}
+
+const char *fdas_last_error(void) { return g_last_error.c_str(); }
+
+const char *fdas_version(void) { return "fdas-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

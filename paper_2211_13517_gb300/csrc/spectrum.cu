@@ -1,0 +1,196 @@
+// R2C FFT of one series and median normalisation (the input of the
+// convolution stage of paper §2.2).
+//
+// The N real samples are read as M = N/2 complex values z_n = x_{2n} +
+// i x_{2n+1}.  Their M-point FFT Z_k (one CTA when M <= 8192, otherwise the
+// four-step split M = M1 * M2: M1 column FFTs of length M2 with the twiddle
+// W_M^{n1 k2}, then M2 FFTs of length M1) gives the real-input spectrum
+//
+//     X_k = (Z_k + conj(Z_{M-k}))/2 - (i/2) W_N^k (Z_k - conj(Z_{M-k})),
+//
+// k in [0, M) (Z_M = Z_0), with X_0 set to 0.  The normalisation kernel then
+// takes blocks of B bins, sorts |X_k|^2 (bitonic, shared memory), takes the
+// median mu_b (block 0 without k = 0; the mean of the two middle values for
+// an even count) and stores X'_k = X_k sqrt(ln 2 / mu_b) at the plan's
+// precision: exponential noise has median ln 2 times its mean, so white noise
+// leaves with unit mean power.  Non-finite spectrum values raise a flag.
+#include "fdas_internal.cuh"
+#include "fft_cta.cuh"
+
+#include <algorithm>
+
+namespace fdas {
+namespace {
+
+// Strided FFT of length L per CTA: input element n of CTA c at
+// in[c*in_cs + n*in_es], output element k to out[c*out_cs + k*out_es],
+// multiplied by W_tw^{c k} when tw_m > 0.
+template <int L>
+__global__ void __launch_bounds__(L / 16) fft_strided_kernel(const float2 *__restrict__ in,
+                                                             float2 *__restrict__ out,
+                                                             int64_t in_cs, int64_t in_es,
+                                                             int64_t out_cs, int64_t out_es,
+                                                             int64_t tw_m) {
+    using F = CtaFft<L, -1>;
+    extern __shared__ float2 buf[];
+    const int tid = threadIdx.x;
+    const int64_t c = blockIdx.x;
+    float2 v[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = in[c * in_cs + (int64_t)(tid + r * (L / 16)) * in_es];
+    float2 tw[F::NPASS];
+    F::make_twiddles(tid, tw);
+    float2 o[16];
+    F::to_regs(v, buf, tid, tw, o);
+    constexpr int K = F::NPASS - 1;
+    constexpr int R = F::template Pass<K>::R, NB = F::template Pass<K>::NB;
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int k = F::last_index(tid, b, r);
+            float2 y = o[b * R + r];
+            if (tw_m > 0) {
+                const int64_t e = (c * k) % tw_m;
+                float s, co;
+                sincospif(-2.0f * (float)e / (float)tw_m, &s, &co);
+                y = cmul(y, make_float2(co, s));
+            }
+            out[c * out_cs + (int64_t)k * out_es] = y;
+        }
+}
+
+template <int L>
+fdas_status launch_fft(const float2 *in, float2 *out, int n_cta, int64_t in_cs, int64_t in_es,
+                       int64_t out_cs, int64_t out_es, int64_t tw_m, cudaStream_t s) {
+    const size_t smem = sizeof(float2) * CtaFft<L, -1>::SMEM_ELEMS;
+    FDAS_CUDA_TRY(cudaFuncSetAttribute(fft_strided_kernel<L>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    fft_strided_kernel<L><<<n_cta, L / 16, smem, s>>>(in, out, in_cs, in_es, out_cs, out_es, tw_m);
+    FDAS_CUDA_TRY(cudaGetLastError());
+    return FDAS_OK;
+}
+
+fdas_status fft_any(int L, const float2 *in, float2 *out, int n_cta, int64_t in_cs, int64_t in_es,
+                    int64_t out_cs, int64_t out_es, int64_t tw_m, cudaStream_t s) {
+    switch (L) {
+        case 128: return launch_fft<128>(in, out, n_cta, in_cs, in_es, out_cs, out_es, tw_m, s);
+        case 256: return launch_fft<256>(in, out, n_cta, in_cs, in_es, out_cs, out_es, tw_m, s);
+        case 512: return launch_fft<512>(in, out, n_cta, in_cs, in_es, out_cs, out_es, tw_m, s);
+        case 1024: return launch_fft<1024>(in, out, n_cta, in_cs, in_es, out_cs, out_es, tw_m, s);
+        case 2048: return launch_fft<2048>(in, out, n_cta, in_cs, in_es, out_cs, out_es, tw_m, s);
+        case 4096: return launch_fft<4096>(in, out, n_cta, in_cs, in_es, out_cs, out_es, tw_m, s);
+        case 8192: return launch_fft<8192>(in, out, n_cta, in_cs, in_es, out_cs, out_es, tw_m, s);
+        default:
+            set_error("internal: unsupported FFT length " + std::to_string(L));
+            return FDAS_ERR_UNSUPPORTED;
+    }
+}
+
+constexpr int kNormThreads = 512;
+
+// One CTA per normalisation block of B bins (B a power of two <= 8192).
+template <class P>
+__global__ void __launch_bounds__(kNormThreads) normalise_kernel(
+    const float2 *__restrict__ Z, typename P::cpx *__restrict__ out, float *__restrict__ medians,
+    unsigned int *__restrict__ flags, int64_t M, int B, int median_mode) {
+    extern __shared__ float smem[];
+    float *key = smem;                       // [B]
+    float2 *xs = (float2 *)(smem + B);       // [B]
+    const int tid = threadIdx.x;
+    const int64_t k0 = (int64_t)blockIdx.x * B;
+    const int64_t N = 2 * M;
+    bool bad = false;
+    for (int i = tid; i < B; i += kNormThreads) {
+        const int64_t k = k0 + i;
+        float2 X = make_float2(0.f, 0.f);
+        float p = __int_as_float(0x7f800000);   // +inf: k = 0 sorts last
+        if (k != 0) {
+            const float2 zk = Z[k];
+            const float2 zm = Z[(M - k) % M];
+            const float2 e = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+            // (Z_k - conj(Z_{M-k})) / (2i)
+            const float2 d = make_float2(zk.x - zm.x, zk.y + zm.y);
+            const float2 o = make_float2(0.5f * d.y, -0.5f * d.x);
+            float sn, cs;
+            sincospif(-2.0f * (float)k / (float)N, &sn, &cs);
+            X = cadd(e, cmul(make_float2(cs, sn), o));
+            p = X.x * X.x + X.y * X.y;
+            if (!isfinite(p)) bad = true;
+        }
+        key[i] = p;
+        xs[i] = X;
+    }
+    if (bad) atomicOr(flags, 1u);
+    __syncthreads();
+    float f = 1.0f;
+    if (median_mode == FDAS_NORM_MEDIAN) {
+        for (int k = 2; k <= B; k <<= 1) {
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int i = tid; i < B; i += kNormThreads) {
+                    const int ixj = i ^ j;
+                    if (ixj > i) {
+                        const bool up = (i & k) == 0;
+                        const float a = key[i], b = key[ixj];
+                        if ((a > b) == up) {
+                            key[i] = b;
+                            key[ixj] = a;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        const int cnt = (k0 == 0) ? B - 1 : B;
+        const float med = (cnt & 1) ? key[cnt / 2] : 0.5f * (key[cnt / 2 - 1] + key[cnt / 2]);
+        f = med > 0.f ? (float)sqrt(0.69314718055994530942 / (double)med) : 0.f;
+        if (medians != nullptr && tid == 0) medians[blockIdx.x] = med;
+    }
+    for (int i = tid; i < B; i += kNormThreads) out[k0 + i] = P::st(cscale(xs[i], f));
+}
+
+}  // namespace
+
+fdas_status launch_spectrum(Plan &p, const float *x, void *spec_out, float *medians,
+                            cudaStream_t s) {
+    const int64_t M = p.n_r;
+    const float2 *z = (const float2 *)x;
+    if (p.fft_m1 == 1) {
+        FDAS_TRY(fft_any((int)M, z, p.fft_b, 1, 0, 1, 0, 1, 0, s));
+    } else {
+        const int64_t m1 = p.fft_m1, m2 = p.fft_m2;
+        // columns: n1 = CTA, length m2 over z[n1 + m1 n2]; twiddle W_M^{n1 k2}
+        FDAS_TRY(fft_any((int)m2, z, p.fft_a, (int)m1, 1, m1, m2, 1, M, s));
+        // rows: k2 = CTA, length m1 over a[n1 m2 + k2]; out[k2 + m2 k1]
+        FDAS_TRY(fft_any((int)m1, p.fft_a, p.fft_b, (int)m2, 1, m2, 1, m2, 0, s));
+    }
+    const int B = (int)std::min<int64_t>(p.norm_block, M);
+    const int nb = (int)(M / B);
+    const size_t smem = (size_t)B * (sizeof(float) + sizeof(float2));
+    switch (p.prec) {
+        case FDAS_FP32: {
+            auto k = normalise_kernel<PrecF32>;
+            FDAS_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k<<<nb, kNormThreads, smem, s>>>(p.fft_b, (float2 *)spec_out, medians, p.flags, M, B, p.norm_mode);
+            break;
+        }
+        case FDAS_BF16: {
+            auto k = normalise_kernel<PrecBF16>;
+            FDAS_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k<<<nb, kNormThreads, smem, s>>>(p.fft_b, (__nv_bfloat162 *)spec_out, medians, p.flags, M, B,
+                                             p.norm_mode);
+            break;
+        }
+        default: {
+            auto k = normalise_kernel<PrecF16>;
+            FDAS_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k<<<nb, kNormThreads, smem, s>>>(p.fft_b, (__half2 *)spec_out, medians, p.flags, M, B,
+                                             p.norm_mode);
+            break;
+        }
+    }
+    FDAS_CUDA_TRY(cudaGetLastError());
+    return FDAS_OK;
+}
+
+}  // namespace fdas

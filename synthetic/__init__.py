@@ -118,3 +118,32 @@ def batch_series(i: int, n: int = 1 << 23, base_seed: int = 1000,
     (r0, z0), = draw_signal_params(seed, 1, min(1e4, 0.1 * r_hi), r_hi, z_abs)
     amp = 0.05 * np.sqrt((1 << 17) / n)
     return inject_sinusoid(white_noise(n, seed), r0, z0, amp), (r0, z0)
+
+
+def torch_batch_series(count: int, n: int = 1 << 23, base_seed: int = 1000,
+                       device="cuda", z_abs: float = 90.0):
+    """Device-side batch with the recipe of `batch_series` (for large batches).
+
+    Series i: N(0,1) noise from torch's generator seeded base_seed+i plus one
+    sinusoid of amplitude 0.05*sqrt(2^17/n), (r0, z0) drawn by
+    draw_signal_params(base_seed+i).  Returns (list of float32 tensors,
+    [(r0, z0), ...]).
+    """
+    import math as _m
+
+    import torch
+    out, params = [], []
+    r_hi = min(4e6, 0.45 * n)
+    amp = 0.05 * _m.sqrt((1 << 17) / n)
+    u = torch.arange(n, device=device, dtype=torch.float64) / n
+    for i in range(count):
+        seed = base_seed + i
+        g = torch.Generator(device=device)
+        g.manual_seed(seed)
+        x = torch.randn(n, generator=g, device=device, dtype=torch.float32)
+        (r0, z0), = draw_signal_params(seed, 1, min(1e4, 0.1 * r_hi), r_hi, z_abs)
+        ph = r0 * u + z0 * (u - 0.5) ** 2 / 2.0
+        x += (amp * torch.cos(2.0 * _m.pi * ph)).to(torch.float32)
+        out.append(x)
+        params.append((r0, z0))
+    return out, params

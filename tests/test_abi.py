@@ -1,0 +1,95 @@
+"""The C-ABI library builds, loads and exports what include/fdas.h declares.
+
+These run without a GPU: they check the build, the exported symbols, the
+struct layouts the binding relies on, and the argument validation that every
+entry point performs before touching CUDA.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def capi():
+    import paper_2211_13517_gb300 as pkg
+    pkg.build()
+    from paper_2211_13517_gb300 import capi as c
+    c.lib()
+    return c
+
+
+def _declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(fdas_[a-z0-9_]+)\s*\(", src))
+    return names
+
+
+def test_every_declared_symbol_is_exported(capi):
+    declared = _declared_symbols()
+    assert "fdas_search" in declared and "fdas_plan_create" in declared
+    lib = ctypes.CDLL(capi.LIB)
+    missing = [n for n in sorted(declared) if not hasattr(lib, n)]
+    assert not missing, missing
+    # and the binding covers every one of them under the same name
+    assert set(capi.EXPORTED) == declared
+
+
+def test_struct_layouts(capi):
+    assert ctypes.sizeof(capi.fdas_candidate) == 20
+    assert ctypes.sizeof(capi.fdas_series) == 24
+    assert ctypes.sizeof(capi.fdas_opts) == 48
+    assert ctypes.sizeof(capi.fdas_plan_info) == 152
+    assert capi.CANDIDATE_DTYPE.itemsize == 20
+
+
+def test_defaults_and_version(capi):
+    o = capi.fdas_opts_default()
+    assert o.precision == capi.FDAS_FP32 and o.threshold_sigma == 6.0
+    assert o.norm_block == 2048 and o.max_candidates == 1 << 20
+    assert "sm_103a" in capi.fdas_version()
+
+
+@pytest.mark.parametrize("args,frag", [
+    ((1000, 64e-6, 16.0, 2.0, 2048, 4), "n_samples"),
+    ((1 << 25, 64e-6, 16.0, 2.0, 2048, 4), "n_samples"),
+    ((1 << 17, 64e-6, 16.0, 3.0, 2048, 4), "integer"),
+    ((1 << 17, 64e-6, 16.0, 2.0, 2048, 3), "n_harm"),
+    ((1 << 17, 64e-6, 16.0, 2.0, 1000, 4), "seg_len"),
+    ((1 << 17, 64e-6, 16.0, 2.0, 32768, 4), "seg_len"),
+    ((1 << 17, 64e-6, 1000.0, 1.0, 1024, 4), "seg_len must exceed"),
+    ((1 << 17, 0.0, 16.0, 2.0, 2048, 4), "tsamp"),
+    ((1 << 17, 64e-6, 16.0, -1.0, 2048, 4), "z_step"),
+])
+def test_plan_argument_validation(capi, args, frag):
+    with pytest.raises(capi.FdasError) as ei:
+        capi.fdas_plan_create(*args)
+    assert ei.value.status == capi.FDAS_ERR_ARG
+    assert frag in str(ei.value)
+
+
+def test_opts_validation(capi):
+    o = capi.fdas_opts_default()
+    o.norm_block = 1000
+    with pytest.raises(capi.FdasError) as ei:
+        capi.fdas_plan_create(1 << 17, 64e-6, 16.0, 2.0, 2048, 4, o)
+    assert ei.value.status == capi.FDAS_ERR_ARG
+    o = capi.fdas_opts_default()
+    o.precision = 7
+    with pytest.raises(capi.FdasError):
+        capi.fdas_plan_create(1 << 17, 64e-6, 16.0, 2.0, 2048, 4, o)
+
+
+def test_null_arguments_rejected(capi):
+    lib = capi.lib()
+    assert lib.fdas_search(None, None, 0, None, 0, None, None) == capi.FDAS_ERR_ARG
+    assert lib.fdas_plan_get_info(None, None) == capi.FDAS_ERR_ARG
+    assert "NULL" in capi.fdas_last_error() or "plan" in capi.fdas_last_error()
+    lib.fdas_plan_destroy(None)   # ignored
