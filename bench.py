@@ -240,7 +240,8 @@ def run_reference(args, rank):
 
 
 def _config(args, precision):
-    return {"workload": f"ska_2^23_193z_batch{args.batch}", "series_per_step": args.batch,
+    return {"workload": f"ska_2^{args.n_log2}_193z_batch{args.batch}",
+            "series_per_step": args.batch,
             "n_samples": N_SAMPLES, "tsamp_s": TSAMP, "z_range": [-Z_MAX, Z_MAX],
             "z_step": Z_STEP, "n_z": 193, "seg_len": SEG_LEN, "n_harm": N_HARM,
             "threshold_sigma": SIGMA, "precision": precision,
@@ -423,7 +424,11 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n-log2", type=int, default=23,
+                    help="series length 2^n (smaller only for profiling captures)")
     args = ap.parse_args()
+    global N_SAMPLES
+    N_SAMPLES = 1 << args.n_log2
     if args.warmup < 3 and args.impl == "gb300":
         ap.error("--warmup must be >= 3")
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -16,11 +16,13 @@
 //
 // Since |e| <= m(z) <= m_ov the circular correlation equals the linear one on
 // the kept outputs, so P is exactly sum_e X'_{r-e} g_z[e] squared.  Every
-// thread keeps compensated FP32 sums of P and P^2 over its outputs; the CTA
+// thread sums P and P^2 of its 16 outputs per template in FP32 and adds those
+// partial sums across templates with compensated (Kahan) FP32 sums; the CTA
 // adds them in FP64 in a fixed order and writes one partial per CTA, which the
 // statistics kernel reduces in a fixed order (deterministic mean and std).
 #include "fdas_internal.cuh"
 #include "fft_cta.cuh"
+#include "fft8k.cuh"
 
 namespace fdas {
 namespace {
@@ -71,6 +73,7 @@ __global__ void __launch_bounds__(L / 16, 1)
         float2 o[16];
         Iv::to_regs(v, buf, tid, tw, o);
         typename P::real *row = plane + (int64_t)iz * n_r;
+        float zs = 0.f, zq = 0.f;   // this template's 16 outputs, plain FP32
 #pragma unroll
         for (int b = 0; b < NB; ++b)
 #pragma unroll
@@ -79,12 +82,14 @@ __global__ void __launch_bounds__(L / 16, 1)
                 const int64_t rr = seg0 + n - m_ov;
                 if (n >= m_ov && n < m_ov + V && rr < n_r) {
                     const float2 y = o[b * R + r];
-                    const float pw = y.x * y.x + y.y * y.y;
+                    const float pw = fmaf(y.x, y.x, y.y * y.y);
                     row[rr] = P::str(pw * P::plane_scale);
-                    sp.add(pw);
-                    sq.add(pw * pw);
+                    zs += pw;
+                    zq = fmaf(pw, pw, zq);
                 }
             }
+        sp.add(zs);   // compensated across templates
+        sq.add(zq);
     }
     // fixed-order FP64 reduction of the CTA's sums
     double a = (double)sp.s - (double)sp.c, b2 = (double)sq.s - (double)sq.c;
@@ -106,6 +111,111 @@ __global__ void __launch_bounds__(L / 16, 1)
         }
         partials[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = make_double2(ta, tb);
     }
+}
+
+// The same correlation for L = 8192 with 256 threads x 32 points (fft8k.cuh):
+// two shared-memory exchanges per inverse transform instead of three.
+template <class P>
+__global__ void __launch_bounds__(256, 1)
+    correlate8k_kernel(const typename P::cpx *__restrict__ spec_pad,
+                       const typename P::cpx *__restrict__ bank, typename P::real *__restrict__ plane,
+                       double2 *__restrict__ partials, int64_t n_r, int n_z, int V, int m_ov,
+                       int z_per_cta, float bank_scale) {
+    using Fw = Fft8k<-1>;
+    using Iv = Fft8k<+1>;
+    constexpr int L = 8192;
+    extern __shared__ float2 buf[];
+    __shared__ double red[2][8];
+    const int t = threadIdx.x;
+    const int64_t seg0 = (int64_t)blockIdx.x * V;
+    const int iz_begin = blockIdx.y * z_per_cta;
+    const int iz_end = min(n_z, iz_begin + z_per_cta);
+
+    float2 v[32], S[32], o[32], w1, w2;
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[16 * b + r] = P::ld(spec_pad[seg0 + t + 256 * b + 512 * r]);
+    Fw::make_twiddles(t, w1, w2);
+    Fw::pass0(v, buf, t);
+    __syncthreads();
+    Fw::pass1(buf, t, w1);
+    Fw::pass2(buf, t, w2, o);
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 32; ++r) buf[fft_pad(t + 256 * r)] = o[r];
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int r = 0; r < 16; ++r)
+            S[16 * b + r] = cscale(buf[fft_pad(t + 256 * b + 512 * r)], bank_scale);
+    Iv::make_twiddles(t, w1, w2);
+
+    Kahan sp, sq;
+    for (int iz = iz_begin; iz < iz_end; ++iz) {
+        __syncthreads();   // the previous pass 2 has read buf
+        const typename P::cpx *h = bank + (int64_t)iz * L;
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int r = 0; r < 16; ++r)
+                v[16 * b + r] = cmul(S[16 * b + r], P::ld(__ldg(h + t + 256 * b + 512 * r)));
+        Iv::pass0(v, buf, t);
+        __syncthreads();
+        Iv::pass1(buf, t, w1);
+        Iv::pass2(buf, t, w2, o);
+        typename P::real *row = plane + (int64_t)iz * n_r;
+        float zs = 0.f, zq = 0.f;
+#pragma unroll
+        for (int r = 0; r < 32; ++r) {
+            const int n = t + 256 * r;
+            const int64_t rr = seg0 + n - m_ov;
+            if (n >= m_ov && n < m_ov + V && rr < n_r) {
+                const float pw = fmaf(o[r].x, o[r].x, o[r].y * o[r].y);
+                row[rr] = P::str(pw * P::plane_scale);
+                zs += pw;
+                zq = fmaf(pw, pw, zq);
+            }
+        }
+        sp.add(zs);
+        sq.add(zq);
+    }
+    double a = (double)sp.s - (double)sp.c, b2 = (double)sq.s - (double)sq.c;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, off);
+        b2 += __shfl_down_sync(0xffffffffu, b2, off);
+    }
+    if ((t & 31) == 0) {
+        red[0][t >> 5] = a;
+        red[1][t >> 5] = b2;
+    }
+    __syncthreads();
+    if (t == 0) {
+        double ta = 0.0, tb = 0.0;
+        for (int w = 0; w < 8; ++w) {
+            ta += red[0][w];
+            tb += red[1][w];
+        }
+        partials[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = make_double2(ta, tb);
+    }
+}
+
+template <class P>
+fdas_status launch_8k(Plan &p, const void *spec_padded, void *plane, double2 *partials,
+                      cudaStream_t s) {
+    const size_t smem = sizeof(float2) * Fft8k<1>::SMEM_ELEMS;
+    auto k = correlate8k_kernel<P>;
+    FDAS_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int zper = (p.n_z + p.n_zchunk - 1) / p.n_zchunk;
+    dim3 grid(p.n_seg, p.n_zchunk);
+    const float bank_scale = P::id == FDAS_FP16 ? 1.0f / (float)p.L : 1.0f;
+    k<<<grid, 256, smem, s>>>((const typename P::cpx *)spec_padded, (const typename P::cpx *)p.bank,
+                              (typename P::real *)plane, partials, p.n_r, p.n_z, p.V, p.m_ov, zper,
+                              bank_scale);
+    FDAS_CUDA_TRY(cudaGetLastError());
+    return FDAS_OK;
 }
 
 template <int L, class P>
@@ -130,7 +240,7 @@ fdas_status launch_P(Plan &p, const void *spec, void *plane, double2 *partials, 
         case 1024: return launch_L<1024, P>(p, spec, plane, partials, s);
         case 2048: return launch_L<2048, P>(p, spec, plane, partials, s);
         case 4096: return launch_L<4096, P>(p, spec, plane, partials, s);
-        case 8192: return launch_L<8192, P>(p, spec, plane, partials, s);
+        case 8192: return launch_8k<P>(p, spec, plane, partials, s);
         default:
             set_error("seg_len " + std::to_string(p.L) + " is not built");
             return FDAS_ERR_UNSUPPORTED;

@@ -109,6 +109,7 @@ struct Plan {
     int64_t max_cands;
     int device;
     int n_zchunk;           // z chunks per segment in the correlation grid
+    int n_sms = 1;          // streaming multiprocessors of the device
     // FFT split of the N/2-point complex FFT in the spectrum stage
     int fft_m1, fft_m2;     // M = m1 * m2 (m1 = 1: single pass)
     // device memory

@@ -15,6 +15,8 @@
 // (trial rank, stage, iz, ir), so the list does not depend on scheduling.
 #include "fdas_internal.cuh"
 
+#include <algorithm>
+
 namespace fdas {
 namespace {
 
@@ -78,80 +80,113 @@ __global__ void finalize_stats_kernel(const double2 *__restrict__ partials, int 
 }
 
 // ---------------------------------------------------------------------------
-// harmonic sum + threshold: one thread per top cell; grid x over r, y over iz
+// harmonic sum + threshold.
+//
+// One thread owns NC cells of one top row, ir = ir0 + c * 256 (c < NC), so
+// every warp-wide load covers 32 consecutive cells.  Because 256 j / H is an
+// integer, the source bin of harmonic j for cell c is exactly
+// floor((ir0 j + H/2)/H) + c * 256 j / H: per harmonic one row pointer and one
+// 32-bit index, and the NC loads use compile-time offsets.  All NC * H loads
+// are issued before the first add (they are independent), which keeps enough
+// of them in flight to cover the memory latency.  The sums then run in stage
+// order (j = H; H/2; H/4, 3H/4; ...), so stage s is a prefix of the running
+// sum, and each stage is compared with its threshold.  The grid covers the
+// row exactly (NC * 256 divides N/2), so no load needs a bounds test.
 // ---------------------------------------------------------------------------
 constexpr int kHsThreads = 256;
 
-template <class P, int H>
+// harmonic visited at position idx of the stage order
+__host__ __device__ constexpr int j_at(int H, int idx) {
+    return idx == 0 ? H : ((2 * (idx - (1 << ilog2h(idx))) + 1) * H) >> (ilog2h(idx) + 1);
+}
+
+__host__ __device__ constexpr int src_off(int H, int o, int j) {
+    return o < 0 ? -(((-o) * j + H / 2) / H) : ((o * j + H / 2) / H);
+}
+
+template <class P, int H, int NC>
+struct HsLoad {
+    // v[idx][c]: harmonic j_at(H, idx) of cell c
+    template <int IDX>
+    __device__ __forceinline__ static void run(const typename P::real *__restrict__ plane,
+                                               int64_t n_r, int iz0, int o, int ir0,
+                                               float (&v)[H][NC]) {
+        if constexpr (IDX < H) {
+            constexpr int J = j_at(H, IDX);
+            constexpr int STEP = kHsThreads * J / H;
+            const typename P::real *src = plane + (int64_t)(iz0 + src_off(H, o, J)) * n_r +
+                                          (uint32_t)((ir0 * J + H / 2) / H);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) v[IDX][c] = P::ldr(__ldg(src + c * STEP));
+            run<IDX + 1>(plane, n_r, iz0, o, ir0, v);
+        }
+    }
+};
+
+// sums in stage order; stage(s, S) at the end of every stage
+template <int H, int NC, class F>
+__device__ __forceinline__ void hs_sums(const float (&v)[H][NC], F &&stage) {
+    float S[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) S[c] = 0.f;
+#pragma unroll
+    for (int idx = 0; idx < H; ++idx) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) S[c] += v[idx][c];
+        if (((idx + 1) & idx) == 0) stage(ilog2h(idx + 1), S);
+    }
+}
+
+template <class P, int H, int NC>
 __global__ void __launch_bounds__(kHsThreads)
     harmonic_threshold_kernel(const typename P::real *__restrict__ plane, int64_t n_r, int iz0,
                               const TrialStats *__restrict__ st, uint32_t rank,
                               CandRec *__restrict__ cand, unsigned long long *__restrict__ count,
                               int64_t cap) {
-    constexpr int NST = ilog2h(H) + 1;
-    const int64_t ir = (int64_t)blockIdx.x * kHsThreads + threadIdx.x;
+    const int ir0 = blockIdx.x * (kHsThreads * NC) + threadIdx.x;
     const int iz = blockIdx.y;
-    if (ir >= n_r) return;
-    const int o = iz - iz0;
-    const int ao = o < 0 ? -o : o;
+    float v[H][NC];
+    HsLoad<P, H, NC>::template run<0>(plane, n_r, iz0, iz - iz0, ir0, v);
     const float inv = 1.0f / P::plane_scale;
-    float thr[NST];
+    hs_sums<H, NC>(v, [&](int s, float (&S)[NC]) {
+        const float th = st->thr[s];
+        float m = S[0];
 #pragma unroll
-    for (int s = 0; s < NST; ++s) thr[s] = st->thr[s];
-    float S = 0.f;
+        for (int c = 1; c < NC; ++c) m = fmaxf(m, S[c]);
+        if (m * inv > th) {
 #pragma unroll
-    for (int s = 0; s < NST; ++s) {
-        const int h = 1 << s;
-        const int step = H / h;
-#pragma unroll
-        for (int k = 1; k <= h; k += 2) {
-            const int j = k * step;
-            const int64_t sr = (ir * j + H / 2) / H;
-            const int so = (ao * j + H / 2) / H;
-            const int siz = iz0 + (o < 0 ? -so : so);
-            S += P::ldr(__ldg(plane + (int64_t)siz * n_r + sr));
-        }
-        const float Sv = S * inv;
-        if (Sv > thr[s]) {
-            const unsigned long long idx = atomicAdd(count, 1ull);
-            if ((int64_t)idx < cap) {
-                CandRec c;
-                c.key = cand_key(rank, s, iz, (uint32_t)ir);
-                c.power = Sv;
-                c.pad = 0.f;
-                cand[idx] = c;
+            for (int c = 0; c < NC; ++c) {
+                const float val = S[c] * inv;
+                if (val > th) {
+                    const unsigned long long idx = atomicAdd(count, 1ull);
+                    if ((int64_t)idx < cap) {
+                        CandRec rec;
+                        rec.key = cand_key(rank, s, iz, (uint32_t)(ir0 + c * kHsThreads));
+                        rec.power = val;
+                        rec.pad = 0.f;
+                        cand[idx] = rec;
+                    }
+                }
             }
         }
-    }
+    });
 }
 
 // all stage sums written out (checking entry point)
-template <class P, int H>
+template <class P, int H, int NC>
 __global__ void __launch_bounds__(kHsThreads)
     harmonic_sums_kernel(const typename P::real *__restrict__ plane, int64_t n_r, int n_z,
                          int iz0, float *__restrict__ out) {
-    constexpr int NST = ilog2h(H) + 1;
-    const int64_t ir = (int64_t)blockIdx.x * kHsThreads + threadIdx.x;
+    const int ir0 = blockIdx.x * (kHsThreads * NC) + threadIdx.x;
     const int iz = blockIdx.y;
-    if (ir >= n_r) return;
-    const int o = iz - iz0;
-    const int ao = o < 0 ? -o : o;
+    float v[H][NC];
+    HsLoad<P, H, NC>::template run<0>(plane, n_r, iz0, iz - iz0, ir0, v);
     const float inv = 1.0f / P::plane_scale;
-    float S = 0.f;
+    hs_sums<H, NC>(v, [&](int s, float (&S)[NC]) {
 #pragma unroll
-    for (int s = 0; s < NST; ++s) {
-        const int h = 1 << s;
-        const int step = H / h;
-#pragma unroll
-        for (int k = 1; k <= h; k += 2) {
-            const int j = k * step;
-            const int64_t sr = (ir * j + H / 2) / H;
-            const int so = (ao * j + H / 2) / H;
-            const int siz = iz0 + (o < 0 ? -so : so);
-            S += P::ldr(__ldg(plane + (int64_t)siz * n_r + sr));
-        }
-        out[((int64_t)s * n_z + iz) * n_r + ir] = S * inv;
-    }
+        for (int c = 0; c < NC; ++c)
+            out[((int64_t)s * n_z + iz) * n_r + ir0 + c * kHsThreads] = S[c] * inv;
+    });
 }
 
 // ---------------------------------------------------------------------------
@@ -282,40 +317,47 @@ __global__ void finish_kernel(const CandRec *__restrict__ rec, int64_t n,
     out[i] = o;
 }
 
-template <class P>
-fdas_status launch_hs_P(Plan &p, const void *plane, const TrialStats *st, uint32_t rank,
-                        cudaStream_t s) {
-    dim3 grid((unsigned)((p.n_r + kHsThreads - 1) / kHsThreads), p.n_z);
+template <class P, int H, bool kWriteSums>
+fdas_status launch_hs(Plan &p, const void *plane, const TrialStats *st, uint32_t rank,
+                      float *sums_out, cudaStream_t s) {
+    // cells per thread: as many as the register budget allows (NC * H <= 64)
+    // and as divide the row into whole CTAs (N/2 is a power of two >= 512)
+    constexpr int NCMAX = H >= 32 ? 2 : 4;
     const auto *pl = (const typename P::real *)plane;
-    switch (p.H) {
-#define HS_CASE(HH)                                                                          \
-    case HH:                                                                                 \
-        harmonic_threshold_kernel<P, HH><<<grid, kHsThreads, 0, s>>>(                        \
-            pl, p.n_r, p.iz0, st, rank, p.cand, p.cand_count, p.max_cands);                  \
-        break;
-        HS_CASE(1) HS_CASE(2) HS_CASE(4) HS_CASE(8) HS_CASE(16) HS_CASE(32)
-#undef HS_CASE
-        default: set_error("bad n_harm"); return FDAS_ERR_ARG;
+    const bool four = NCMAX >= 4 && p.n_r % (kHsThreads * 4) == 0;
+    const int nc = four ? 4 : 2;
+    dim3 grid((unsigned)(p.n_r / (kHsThreads * nc)), p.n_z);
+    if (four) {
+        if constexpr (kWriteSums)
+            harmonic_sums_kernel<P, H, (NCMAX >= 4 ? 4 : 2)><<<grid, kHsThreads, 0, s>>>(
+                pl, p.n_r, p.n_z, p.iz0, sums_out);
+        else
+            harmonic_threshold_kernel<P, H, (NCMAX >= 4 ? 4 : 2)><<<grid, kHsThreads, 0, s>>>(
+                pl, p.n_r, p.iz0, st, rank, p.cand, p.cand_count, p.max_cands);
+    } else {
+        if constexpr (kWriteSums)
+            harmonic_sums_kernel<P, H, 2><<<grid, kHsThreads, 0, s>>>(pl, p.n_r, p.n_z, p.iz0,
+                                                                     sums_out);
+        else
+            harmonic_threshold_kernel<P, H, 2><<<grid, kHsThreads, 0, s>>>(
+                pl, p.n_r, p.iz0, st, rank, p.cand, p.cand_count, p.max_cands);
     }
     FDAS_CUDA_TRY(cudaGetLastError());
     return FDAS_OK;
 }
 
-template <class P>
-fdas_status launch_sums_P(Plan &p, const void *plane, float *out, cudaStream_t s) {
-    dim3 grid((unsigned)((p.n_r + kHsThreads - 1) / kHsThreads), p.n_z);
-    const auto *pl = (const typename P::real *)plane;
+template <class P, bool kWriteSums>
+fdas_status launch_hs_P(Plan &p, const void *plane, const TrialStats *st, uint32_t rank,
+                        float *sums_out, cudaStream_t s) {
     switch (p.H) {
-#define HS_CASE(HH)                                                                          \
-    case HH:                                                                                 \
-        harmonic_sums_kernel<P, HH><<<grid, kHsThreads, 0, s>>>(pl, p.n_r, p.n_z, p.iz0, out); \
-        break;
-        HS_CASE(1) HS_CASE(2) HS_CASE(4) HS_CASE(8) HS_CASE(16) HS_CASE(32)
-#undef HS_CASE
+        case 1: return launch_hs<P, 1, kWriteSums>(p, plane, st, rank, sums_out, s);
+        case 2: return launch_hs<P, 2, kWriteSums>(p, plane, st, rank, sums_out, s);
+        case 4: return launch_hs<P, 4, kWriteSums>(p, plane, st, rank, sums_out, s);
+        case 8: return launch_hs<P, 8, kWriteSums>(p, plane, st, rank, sums_out, s);
+        case 16: return launch_hs<P, 16, kWriteSums>(p, plane, st, rank, sums_out, s);
+        case 32: return launch_hs<P, 32, kWriteSums>(p, plane, st, rank, sums_out, s);
         default: set_error("bad n_harm"); return FDAS_ERR_ARG;
     }
-    FDAS_CUDA_TRY(cudaGetLastError());
-    return FDAS_OK;
 }
 
 }  // namespace
@@ -336,17 +378,17 @@ fdas_status launch_finalize_stats(Plan &p, const double2 *partials, int n_partia
 fdas_status launch_harmonic_threshold(Plan &p, const void *plane, const TrialStats *st,
                                       uint32_t rank, cudaStream_t s) {
     switch (p.prec) {
-        case FDAS_FP32: return launch_hs_P<PrecF32>(p, plane, st, rank, s);
-        case FDAS_BF16: return launch_hs_P<PrecBF16>(p, plane, st, rank, s);
-        default: return launch_hs_P<PrecF16>(p, plane, st, rank, s);
+        case FDAS_FP32: return launch_hs_P<PrecF32, false>(p, plane, st, rank, nullptr, s);
+        case FDAS_BF16: return launch_hs_P<PrecBF16, false>(p, plane, st, rank, nullptr, s);
+        default: return launch_hs_P<PrecF16, false>(p, plane, st, rank, nullptr, s);
     }
 }
 
 fdas_status launch_harmonic_sums(Plan &p, const void *plane, float *out, cudaStream_t s) {
     switch (p.prec) {
-        case FDAS_FP32: return launch_sums_P<PrecF32>(p, plane, out, s);
-        case FDAS_BF16: return launch_sums_P<PrecBF16>(p, plane, out, s);
-        default: return launch_sums_P<PrecF16>(p, plane, out, s);
+        case FDAS_FP32: return launch_hs_P<PrecF32, true>(p, plane, nullptr, 0, out, s);
+        case FDAS_BF16: return launch_hs_P<PrecBF16, true>(p, plane, nullptr, 0, out, s);
+        default: return launch_hs_P<PrecF16, true>(p, plane, nullptr, 0, out, s);
     }
 }
 

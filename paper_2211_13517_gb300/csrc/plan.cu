@@ -239,7 +239,8 @@ static fdas_status create(Plan *&out, int64_t n_samples, double tsamp, double z_
     }
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device);
-    p.n_zchunk = choose_zchunks(p, std::max(1, sms));
+    p.n_sms = std::max(1, sms);
+    p.n_zchunk = choose_zchunks(p, p.n_sms);
 
     fdas_status st = FDAS_OK;
     auto fail = [&](fdas_status s) {
