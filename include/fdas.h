@@ -236,6 +236,37 @@ fdas_status fdas_template_bank(fdas_plan *plan, double *taps_out,
                                double *energy_out, void *bank_out,
                                void *stream);
 
+/*
+ * Allocation-free spectrum (no counterpart in the paper; an addition for
+ * callers that must not allocate device memory, such as code that runs while
+ * a stream is being captured into a CUDA graph, or a real-time pipeline that
+ * reserves all of its GPU memory up front and forbids allocation afterwards).
+ *
+ * Computes exactly what fdas_spectrum computes (R2C FFT, X_0 = 0, median
+ * normalisation with blocks of norm_block bins) without a plan: the FFT
+ * intermediates live in a fixed array of device memory defined by the
+ * library, 2^20 complex FP32 values (8 MiB) plus a flag word, which every
+ * device that loads the library keeps reserved until the process exits.
+ * The call allocates nothing and calls no allocating routine.
+ *
+ * series: device, n_samples floats, 16-byte aligned.  n_samples: power of
+ * two in [2^10, 2^20]; longer series are rejected with FDAS_ERR_ARG (the fixed
+ * array holds at most 2^20 samples).  precision, norm_mode, norm_block as in
+ * fdas_opts.  spectrum_out: device, n_samples/2 complex elements of
+ * `precision`.  medians_out: device float[n_samples/2 / min(norm_block,
+ * n_samples/2)] or NULL.  Asynchronous on `stream`.
+ *
+ * The first call on a device looks up the array's device address and caches
+ * it; make that first call before any stream capture.  All calls share the
+ * one array and each call overwrites what the previous left there, so calls
+ * whose work may overlap on the GPU (different streams without ordering, or
+ * several host threads) race with one another: order them on one stream.
+ */
+fdas_status fdas_spectrum_static(const float *series, int64_t n_samples,
+                                 int32_t precision, int32_t norm_mode,
+                                 int32_t norm_block, void *spectrum_out,
+                                 float *medians_out, void *stream);
+
 /* ---------------------------------------------------------------------
  * Tracing: per-kernel-group launch counts (always kept) and CUDA-event
  * durations (kept while enabled).  Events are recorded on the stream each

@@ -39,7 +39,8 @@ FDAS_NORM_MEDIAN, FDAS_NORM_NONE = 0, 1
 EXPORTED = ["fdas_opts_default", "fdas_plan_create", "fdas_plan_destroy",
             "fdas_plan_get_info", "fdas_search", "fdas_spectrum", "fdas_power_plane",
             "fdas_harmonic_sums", "fdas_threshold", "fdas_template_bank",
-            "fdas_profile_enable", "fdas_profile_read", "fdas_last_error", "fdas_version"]
+            "fdas_spectrum_static", "fdas_profile_enable", "fdas_profile_read",
+            "fdas_last_error", "fdas_version"]
 
 
 class fdas_opts(Structure):
@@ -122,6 +123,9 @@ def lib() -> ctypes.CDLL:
         L.fdas_threshold.restype = c_int32
         L.fdas_template_bank.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
         L.fdas_template_bank.restype = c_int32
+        L.fdas_spectrum_static.argtypes = [c_void_p, c_int64, c_int32, c_int32, c_int32,
+                                           c_void_p, c_void_p, c_void_p]
+        L.fdas_spectrum_static.restype = c_int32
         L.fdas_profile_enable.argtypes = [c_void_p, c_int32]
         L.fdas_profile_enable.restype = c_int32
         L.fdas_profile_read.argtypes = [c_void_p, POINTER(fdas_profile)]
@@ -199,6 +203,12 @@ def fdas_threshold(plan, plane_ptr, stats_ptr, trial_id, cands_ptr, capacity, st
 def fdas_template_bank(plan, taps_ptr=None, energy_ptr=None, bank_ptr=None, stream=None):
     _check(lib().fdas_template_bank(plan, taps_ptr, energy_ptr, bank_ptr, stream),
            "fdas_template_bank")
+
+
+def fdas_spectrum_static(series_ptr, n_samples, precision, norm_mode, norm_block,
+                         spectrum_ptr, medians_ptr=None, stream=None):
+    _check(lib().fdas_spectrum_static(series_ptr, n_samples, precision, norm_mode, norm_block,
+                                      spectrum_ptr, medians_ptr, stream), "fdas_spectrum_static")
 
 
 def fdas_profile_enable(plan, on: bool) -> None:
