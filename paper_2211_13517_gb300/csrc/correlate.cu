@@ -151,6 +151,12 @@ __global__ void __launch_bounds__(256, 1)
         for (int r = 0; r < 16; ++r)
             S[16 * b + r] = cscale(buf[fft_pad(t + 256 * b + 512 * r)], bank_scale);
     Iv::make_twiddles(t, w1, w2);
+    // CTA-uniform: every output but r = 0 and r = 31 is kept, and those two
+    // by a per-thread test, unless the overlap is wide or this is the last
+    // segment (then every output is tested)
+    const bool interior = m_ov <= 256 && seg0 + L - m_ov <= n_r;
+    const bool keep0 = t >= m_ov;
+    const bool keep31 = t + 256 * 31 < m_ov + V;
 
     Kahan sp, sq;
     for (int iz = iz_begin; iz < iz_end; ++iz) {
@@ -165,17 +171,30 @@ __global__ void __launch_bounds__(256, 1)
         __syncthreads();
         Iv::pass1(buf, t, w1);
         Iv::pass2(buf, t, w2, o);
-        typename P::real *row = plane + (int64_t)iz * n_r;
+        typename P::real *row = plane + (seg0 - m_ov) + (int64_t)iz * n_r + t;
         float zs = 0.f, zq = 0.f;
+        if (interior) {
+            // outputs r = 1..30 lie inside [m_ov, L - m_ov) when m_ov <= 256,
+            // and inside the plane row when the segment is not the last
 #pragma unroll
-        for (int r = 0; r < 32; ++r) {
-            const int n = t + 256 * r;
-            const int64_t rr = seg0 + n - m_ov;
-            if (n >= m_ov && n < m_ov + V && rr < n_r) {
+            for (int r = 0; r < 32; ++r) {
+                if ((r == 0 && !keep0) || (r == 31 && !keep31)) continue;
                 const float pw = fmaf(o[r].x, o[r].x, o[r].y * o[r].y);
-                row[rr] = P::str(pw * P::plane_scale);
+                row[256 * r] = P::str(pw * P::plane_scale);
                 zs += pw;
                 zq = fmaf(pw, pw, zq);
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < 32; ++r) {
+                const int n = t + 256 * r;
+                const int64_t rr = seg0 + n - m_ov;
+                if (n >= m_ov && n < m_ov + V && rr < n_r) {
+                    const float pw = fmaf(o[r].x, o[r].x, o[r].y * o[r].y);
+                    row[256 * r] = P::str(pw * P::plane_scale);
+                    zs += pw;
+                    zq = fmaf(pw, pw, zq);
+                }
             }
         }
         sp.add(zs);

@@ -64,9 +64,9 @@ struct Fft8k {
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
             Dft<16, D>::run(v + 16 * b);
-            const int j = t + 256 * b;
+            float2 *dst = buf + 17 * (t + 256 * b);   // fft_pad(16 j + r) = 17 j + r
 #pragma unroll
-            for (int r = 0; r < 16; ++r) buf[fft_pad(16 * j + r)] = v[16 * b + r];
+            for (int r = 0; r < 16; ++r) dst[r] = v[16 * b + r];
         }
     }
 
@@ -75,9 +75,9 @@ struct Fft8k {
         float2 v[32];
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
-            const int j = t + 256 * b;
+            const float2 *src = buf + fft_pad(t + 256 * b);   // + 544 r = fft_pad(j + 512 r)
 #pragma unroll
-            for (int r = 0; r < 16; ++r) v[16 * b + r] = buf[fft_pad(j + 512 * r)];
+            for (int r = 0; r < 16; ++r) v[16 * b + r] = src[544 * r];
         }
         __syncthreads();
         float2 p[16];
@@ -90,17 +90,18 @@ struct Fft8k {
             for (int r = 1; r < 16; ++r) v[16 * b + r] = cmul(v[16 * b + r], p[r]);
             Dft<16, D>::run(v + 16 * b);
             const int j = t + 256 * b;
-            const int idxD = (j >> 4) * 256 + (j & 15);
+            float2 *dst = buf + fft_pad((j >> 4) * 256 + (j & 15));   // + 17 r
 #pragma unroll
-            for (int r = 0; r < 16; ++r) buf[fft_pad(idxD + 16 * r)] = v[16 * b + r];
+            for (int r = 0; r < 16; ++r) dst[17 * r] = v[16 * b + r];
         }
         __syncthreads();
     }
 
     // pass 2 (Ns = 256, R = 32) into registers: out[r] is element t + 256 r
     __device__ __forceinline__ static void pass2(const float2 *buf, int t, float2 w2, float2 *out) {
+        const float2 *src = buf + fft_pad(t);   // + 272 r = fft_pad(t + 256 r)
 #pragma unroll
-        for (int r = 0; r < 32; ++r) out[r] = buf[fft_pad(t + 256 * r)];
+        for (int r = 0; r < 32; ++r) out[r] = src[272 * r];
         apply_twiddles<32>(out, w2);
         Dft<32, D>::run(out);
     }

@@ -14,6 +14,9 @@
 // appended with an atomic counter and ordered afterwards by
 // (trial rank, stage, iz, ir), so the list does not depend on scheduling.
 #include "fdas_internal.cuh"
+#include "fft_cta.cuh"   // cadd
+
+#include <cstring>
 
 #include <algorithm>
 
@@ -104,36 +107,64 @@ __host__ __device__ constexpr int src_off(int H, int o, int j) {
     return o < 0 ? -(((-o) * j + H / 2) / H) : ((o * j + H / 2) / H);
 }
 
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all_() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// element offset of the source row of every harmonic for top row iz (the
+// same for the whole CTA): threads 0..H-1 fill it, then the CTA synchronises
+template <int H>
+__device__ __forceinline__ void hs_row_offsets(int iz0, int iz, int64_t n_r, int64_t *rowoff) {
+    if (threadIdx.x < H) {
+        const int j = threadIdx.x + 1;
+        rowoff[threadIdx.x] = (int64_t)(iz0 + src_off(H, iz - iz0, j)) * n_r;
+    }
+    __syncthreads();
+}
+
 template <class P, int H, int NC>
 struct HsLoad {
-    // v[idx][c]: harmonic j_at(H, idx) of cell c
+    // v[idx][c]: harmonic j_at(H, idx) of cell c (ir0 + c * kHsThreads)
     template <int IDX>
     __device__ __forceinline__ static void run(const typename P::real *__restrict__ plane,
-                                               int64_t n_r, int iz0, int o, int ir0,
+                                               const int64_t *rowoff, unsigned ir0,
                                                float (&v)[H][NC]) {
         if constexpr (IDX < H) {
             constexpr int J = j_at(H, IDX);
-            constexpr int STEP = kHsThreads * J / H;
-            const typename P::real *src = plane + (int64_t)(iz0 + src_off(H, o, J)) * n_r +
-                                          (uint32_t)((ir0 * J + H / 2) / H);
+            constexpr unsigned STEP = kHsThreads * J / H;
+            constexpr int SH = ilog2h(H);
+            const typename P::real *src = plane + rowoff[J - 1] + ((ir0 * J + H / 2) >> SH);
 #pragma unroll
             for (int c = 0; c < NC; ++c) v[IDX][c] = P::ldr(__ldg(src + c * STEP));
-            run<IDX + 1>(plane, n_r, iz0, o, ir0, v);
+            run<IDX + 1>(plane, rowoff, ir0, v);
         }
     }
 };
 
-// sums in stage order; stage(s, S) at the end of every stage
+// sums in stage order (pairs of cells with packed FP32x2 adds); stage(s, S)
+// at the end of every stage
 template <int H, int NC, class F>
 __device__ __forceinline__ void hs_sums(const float (&v)[H][NC], F &&stage) {
-    float S[NC];
+    static_assert(NC % 2 == 0, "cells come in pairs");
+    float2 S2[NC / 2];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) S[c] = 0.f;
+    for (int c = 0; c < NC / 2; ++c) S2[c] = make_float2(0.f, 0.f);
 #pragma unroll
     for (int idx = 0; idx < H; ++idx) {
 #pragma unroll
-        for (int c = 0; c < NC; ++c) S[c] += v[idx][c];
-        if (((idx + 1) & idx) == 0) stage(ilog2h(idx + 1), S);
+        for (int c = 0; c < NC / 2; ++c)
+            S2[c] = cadd(S2[c], make_float2(v[idx][2 * c], v[idx][2 * c + 1]));
+        if (((idx + 1) & idx) == 0) {
+            float S[NC];
+#pragma unroll
+            for (int c = 0; c < NC / 2; ++c) {
+                S[2 * c] = S2[c].x;
+                S[2 * c + 1] = S2[c].y;
+            }
+            stage(ilog2h(idx + 1), S);
+        }
     }
 }
 
@@ -143,10 +174,12 @@ __global__ void __launch_bounds__(kHsThreads)
                               const TrialStats *__restrict__ st, uint32_t rank,
                               CandRec *__restrict__ cand, unsigned long long *__restrict__ count,
                               int64_t cap) {
-    const int ir0 = blockIdx.x * (kHsThreads * NC) + threadIdx.x;
+    const unsigned ir0 = blockIdx.x * (kHsThreads * NC) + threadIdx.x;
     const int iz = blockIdx.y;
+    __shared__ int64_t rowoff[H];
+    hs_row_offsets<H>(iz0, iz, n_r, rowoff);
     float v[H][NC];
-    HsLoad<P, H, NC>::template run<0>(plane, n_r, iz0, iz - iz0, ir0, v);
+    HsLoad<P, H, NC>::template run<0>(plane, rowoff, ir0, v);
     const float inv = 1.0f / P::plane_scale;
     hs_sums<H, NC>(v, [&](int s, float (&S)[NC]) {
         const float th = st->thr[s];
@@ -177,15 +210,183 @@ template <class P, int H, int NC>
 __global__ void __launch_bounds__(kHsThreads)
     harmonic_sums_kernel(const typename P::real *__restrict__ plane, int64_t n_r, int n_z,
                          int iz0, float *__restrict__ out) {
-    const int ir0 = blockIdx.x * (kHsThreads * NC) + threadIdx.x;
+    const unsigned ir0 = blockIdx.x * (kHsThreads * NC) + threadIdx.x;
     const int iz = blockIdx.y;
+    __shared__ int64_t rowoff[H];
+    hs_row_offsets<H>(iz0, iz, n_r, rowoff);
     float v[H][NC];
-    HsLoad<P, H, NC>::template run<0>(plane, n_r, iz0, iz - iz0, ir0, v);
+    HsLoad<P, H, NC>::template run<0>(plane, rowoff, ir0, v);
     const float inv = 1.0f / P::plane_scale;
     hs_sums<H, NC>(v, [&](int s, float (&S)[NC]) {
 #pragma unroll
         for (int c = 0; c < NC; ++c)
             out[((int64_t)s * n_z + iz) * n_r + ir0 + c * kHsThreads] = S[c] * inv;
+    });
+}
+
+// ---------------------------------------------------------------------------
+// harmonic sum + threshold for H <= 16 with consecutive cells per thread.
+//
+// Thread t of a CTA owns the R = 16 consecutive cells b = B + 16 t + i of one
+// top row (B = the CTA's first cell, a multiple of 16 T).  Because 16 is a
+// multiple of H, harmonic j of cell i reads source bin
+//     j (B + 16 t)/H + d_i,   d_i = floor((i j + H/2)/H) <= DMAX_j,
+// so the thread needs only the DMAX_j + 1 consecutive bins starting at
+// j (B + 16 t)/H, and which of them each cell adds is a compile-time index.
+// The CTA first copies, for every harmonic, the span of its source row that
+// all its threads need (starting at j B / H, a multiple of 256, so 16-byte
+// aligned) into shared memory with 16-byte cp.async copies, then each thread
+// reads its values with the widest aligned shared-memory loads and adds them
+// to its cells, in stage order, comparing each stage with its threshold.
+// ---------------------------------------------------------------------------
+template <class P, int H>
+struct Dedup {
+    using real = typename P::real;
+    static constexpr int R = 16;                                  // cells per thread
+    static constexpr int T = sizeof(real) == 2 ? 256 : 128;      // threads per CTA
+    static constexpr int CELLS = T * R;
+    static constexpr int EPV = 16 / (int)sizeof(real);
+    static constexpr int dmax(int j) { return ((R - 1) * j + H / 2) / H; }
+    static constexpr int len(int j) { return (R / H) * j * (T - 1) + dmax(j) + 1; }
+    static constexpr int padlen(int j) { return (len(j) + EPV - 1) / EPV * EPV; }
+    static constexpr int off(int j) { return j <= 1 ? 0 : off(j - 1) + padlen(j - 1); }
+    static constexpr int SMEM_ELEMS = off(H + 1);
+    // widest load (elements, power of two <= EPV) that the per-thread start
+    // (R/H) j t is always aligned to
+    static constexpr int width(int j) {
+        int w = 1;
+        while (w < EPV && (((R / H) * j) % (2 * w)) == 0) w *= 2;
+        return w;
+    }
+};
+
+// raw vector type of `bytes` bytes
+template <int BYTES>
+struct RawVec;
+template <>
+struct RawVec<2> { using type = unsigned short; };
+template <>
+struct RawVec<4> { using type = uint32_t; };
+template <>
+struct RawVec<8> { using type = uint2; };
+template <>
+struct RawVec<16> { using type = uint4; };
+
+// W consecutive stored values (W * sizeof(real) bytes, aligned) -> FP32
+template <class P, int W>
+struct VecLoad {
+    __device__ __forceinline__ static void run(const typename P::real *p, float *o) {
+        using R = typename P::real;
+        using V = typename RawVec<W * (int)sizeof(R)>::type;
+        const V u = *reinterpret_cast<const V *>(p);
+        R e[W];
+        static_assert(sizeof(e) == sizeof(u), "vector width");
+        memcpy(e, &u, sizeof(u));
+#pragma unroll
+        for (int k = 0; k < W; ++k) o[k] = P::ldr(e[k]);
+    }
+};
+
+template <class P, int H>
+struct DedupSteps {
+    using D = Dedup<P, H>;
+    using real = typename P::real;
+
+    // stage the spans of all harmonics (compile-time loop over j)
+    template <int J>
+    __device__ __forceinline__ static void copy(const real *__restrict__ plane, const int64_t *rowoff,
+                                                int64_t n_r, int64_t B, real *sm) {
+        if constexpr (J <= H) {
+            constexpr int NV = D::padlen(J) / D::EPV;
+            const int64_t c0 = (int64_t)J * B / H;
+            const int64_t maxsrc = ((n_r - 1) * J + H / 2) / H;
+            const real *g = plane + rowoff[J - 1] + c0;
+            real *d = sm + D::off(J);
+            for (int v = threadIdx.x; v < NV; v += D::T)
+                if (c0 + (int64_t)v * D::EPV <= maxsrc) cp_async16(d + v * D::EPV, g + v * D::EPV);
+            copy<J + 1>(plane, rowoff, n_r, B, sm);
+        }
+    }
+
+    // add harmonic j_at(H, IDX) to the thread's cells; stage(s, S) at the end
+    // of every stage
+    template <int IDX, class F>
+    __device__ __forceinline__ static void sums(const real *sm, int t, float2 (&S2)[D::R / 2],
+                                                F &&stage) {
+        if constexpr (IDX < H) {
+            constexpr int J = j_at(H, IDX);
+            constexpr int NVAL = D::dmax(J) + 1;
+            constexpr int W = D::width(J);
+            constexpr int NLD = (NVAL + W - 1) / W;
+            const real *p = sm + D::off(J) + (D::R / H) * J * t;
+            float val[NLD * W];
+#pragma unroll
+            for (int k = 0; k < NLD; ++k) VecLoad<P, W>::run(p + k * W, val + k * W);
+#pragma unroll
+            for (int c = 0; c < D::R / 2; ++c) {
+                const int d0 = ((2 * c) * J + H / 2) / H, d1 = ((2 * c + 1) * J + H / 2) / H;
+                S2[c] = cadd(S2[c], make_float2(val[d0], val[d1]));
+            }
+            if constexpr (((IDX + 1) & IDX) == 0) stage(ilog2h(IDX + 1), S2);
+            sums<IDX + 1>(sm, t, S2, stage);
+        }
+    }
+};
+
+template <class P, int H, bool kWriteSums>
+__global__ void __launch_bounds__(Dedup<P, H>::T)
+    harmonic_dedup_kernel(const typename P::real *__restrict__ plane, int64_t n_r, int n_z,
+                          int iz0, const TrialStats *__restrict__ st, uint32_t rank,
+                          CandRec *__restrict__ cand, unsigned long long *__restrict__ count,
+                          int64_t cap, float *__restrict__ sums_out) {
+    using D = Dedup<P, H>;
+    using real = typename P::real;
+    extern __shared__ __align__(16) unsigned char dd_smem[];
+    real *sm = reinterpret_cast<real *>(dd_smem);
+    __shared__ int64_t rowoff[H];
+    const int iz = blockIdx.y;
+    const int64_t B = (int64_t)blockIdx.x * D::CELLS;
+    const int t = threadIdx.x;
+    hs_row_offsets<H>(iz0, iz, n_r, rowoff);
+    DedupSteps<P, H>::template copy<1>(plane, rowoff, n_r, B, sm);
+    cp_async_wait_all_();
+    __syncthreads();
+    const int64_t b = B + (int64_t)D::R * t;   // first cell of this thread
+    if (b >= n_r) return;
+    const float inv = 1.0f / P::plane_scale;
+    float2 S2[D::R / 2];
+#pragma unroll
+    for (int c = 0; c < D::R / 2; ++c) S2[c] = make_float2(0.f, 0.f);
+    DedupSteps<P, H>::template sums<0>(sm, t, S2, [&](int s, float2 (&Sv)[D::R / 2]) {
+        if constexpr (kWriteSums) {
+#pragma unroll
+            for (int c = 0; c < D::R / 2; ++c) {
+                float *o = sums_out + ((int64_t)s * n_z + iz) * n_r + b + 2 * c;
+                o[0] = Sv[c].x * inv;
+                o[1] = Sv[c].y * inv;
+            }
+        } else {
+            const float th = st->thr[s];
+            float m = fmaxf(Sv[0].x, Sv[0].y);
+#pragma unroll
+            for (int c = 1; c < D::R / 2; ++c) m = fmaxf(m, fmaxf(Sv[c].x, Sv[c].y));
+            if (m * inv > th) {
+#pragma unroll
+                for (int i = 0; i < D::R; ++i) {
+                    const float val = ((i & 1) ? Sv[i / 2].y : Sv[i / 2].x) * inv;
+                    if (val > th) {
+                        const unsigned long long idx = atomicAdd(count, 1ull);
+                        if ((int64_t)idx < cap) {
+                            CandRec rec;
+                            rec.key = cand_key(rank, s, iz, (uint32_t)(b + i));
+                            rec.power = val;
+                            rec.pad = 0.f;
+                            cand[idx] = rec;
+                        }
+                    }
+                }
+            }
+        }
     });
 }
 
@@ -318,8 +519,23 @@ __global__ void finish_kernel(const CandRec *__restrict__ rec, int64_t n,
 }
 
 template <class P, int H, bool kWriteSums>
+fdas_status launch_dedup(Plan &p, const void *plane, const TrialStats *st, uint32_t rank,
+                         float *sums_out, cudaStream_t s) {
+    using D = Dedup<P, H>;
+    const size_t smem = sizeof(typename P::real) * (size_t)D::SMEM_ELEMS;
+    auto k = harmonic_dedup_kernel<P, H, kWriteSums>;
+    FDAS_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((unsigned)((p.n_r + D::CELLS - 1) / D::CELLS), p.n_z);
+    k<<<grid, D::T, smem, s>>>((const typename P::real *)plane, p.n_r, p.n_z, p.iz0, st, rank,
+                               p.cand, p.cand_count, p.max_cands, sums_out);
+    FDAS_CUDA_TRY(cudaGetLastError());
+    return FDAS_OK;
+}
+
+template <class P, int H, bool kWriteSums>
 fdas_status launch_hs(Plan &p, const void *plane, const TrialStats *st, uint32_t rank,
                       float *sums_out, cudaStream_t s) {
+    if constexpr (H <= 16) return launch_dedup<P, H, kWriteSums>(p, plane, st, rank, sums_out, s);
     // cells per thread: as many as the register budget allows (NC * H <= 64)
     // and as divide the row into whole CTAs (N/2 is a power of two >= 512)
     constexpr int NCMAX = H >= 32 ? 2 : 4;
