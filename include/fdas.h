@@ -165,6 +165,65 @@ fdas_status fdas_search(fdas_plan *plan, const fdas_series *batch,
                         int64_t capacity, int64_t *n_found, void *stream);
 
 /* ---------------------------------------------------------------------
+ * Candidate refinement with the Fourier-interpolated power.
+ *
+ * The search grid samples r in whole bins and z in steps of z_step; a
+ * signal between grid points loses power to the grid (the paper's §2.1
+ * matched filter evaluated off-grid).  For continuous (r, z), with k0 =
+ * floor(r + 1/2), delta = r - k0 and m = 32 + ceil(|z|/2) (at most 255):
+ *   F(r, z) = sum_{e=-m..m} X_{k0+e} conj(rho(delta - e, z)),   P = |F|^2,
+ * rho the unnormalised response above (so a signal c rho(r0 - k, z0) gives
+ * P(r0, z0) ~ |c|^2 at any z0), bins outside [0, N_r) counted as 0.  The
+ * integrals are Gauss-Legendre sums with 512 nodes, FP32 arithmetic.  The
+ * window is held fixed when differentiating.
+ * `spectrum` is always FP32 complex (N_r float pairs, device), e.g. the
+ * output of fdas_spectrum on an FP32 plan.
+ * --------------------------------------------------------------------- */
+typedef struct {
+    double r;           /* spectral bin (continuous)                       */
+    double z;           /* drift in bins over the observation               */
+    uint32_t trial_id;  /* echoed into the result                           */
+    uint32_t reserved;
+} fdas_seed;
+
+typedef struct {
+    double r, z;        /* refined location                                 */
+    float power;        /* P(r, z)                                          */
+    float dpdr, dpdz;   /* gradient at the refined location                 */
+    int32_t steps;      /* accepted ascent steps                            */
+    uint32_t trial_id;
+    uint32_t reserved;
+} fdas_refined;
+
+/* P at n points; rz: device double[n][2] (r, z); power: device float[n];
+ * grad_rz: device float[n][2] (dP/dr, dP/dz) or NULL.  Asynchronous. */
+fdas_status fdas_fourier_power(fdas_plan *plan, const float *spectrum,
+                               const double *rz, int32_t n, float *power,
+                               float *grad_rz, void *stream);
+
+/* Backward of fdas_fourier_power for an upstream gradient g_s = dL/dP_s
+ * (device float[n]): adds sum_s g_s * 2 F_s rho(r_s - k, z_s) to
+ * grad_spectrum[k] (device float[N_r][2], complex; the gradient of a real
+ * loss with respect to a complex input in the convention of PyTorch,
+ * dL/dRe + i dL/dIm), if not NULL, and writes g_s * (dP/dr, dP/dz) to grad_rz
+ * (device double[n][2]), if not NULL.  Asynchronous; atomically accumulating
+ * (the summation order of overlapping windows is not fixed). */
+fdas_status fdas_fourier_power_backward(fdas_plan *plan, const float *spectrum,
+                                        const double *rz, int32_t n,
+                                        const float *grad_power,
+                                        float *grad_spectrum, double *grad_rz,
+                                        void *stream);
+
+/* Refine n seeds by n_steps of gradient ascent on P(r, z) with
+ * backtracking (one point per CTA; steps along the gradient in the scaled
+ * coordinates (r, z/4), shortened fourfold on a decrease, lengthened 1.5
+ * times on an increase; stops early when no step increases P).  seeds and
+ * out may be host or device memory.  Blocking. */
+fdas_status fdas_refine(fdas_plan *plan, const float *spectrum,
+                        const fdas_seed *seeds, int32_t n, int32_t n_steps,
+                        fdas_refined *out, void *stream);
+
+/* ---------------------------------------------------------------------
  * Stage entry points: one step of the path each, on device buffers, so each
  * step can be checked on its own.  All are asynchronous on `stream`.
  * --------------------------------------------------------------------- */
@@ -269,8 +328,10 @@ fdas_status fdas_spectrum_static(const float *series, int64_t n_samples,
 
 /* ---------------------------------------------------------------------
  * Tracing: per-kernel-group launch counts (always kept) and CUDA-event
- * durations (kept while enabled).  Events are recorded on the stream each
- * group runs on, so overlapping groups are each timed as they ran.
+ * durations (kept while enabled).  While tracing is enabled fdas_search
+ * runs every group on the caller's stream (otherwise the harmonic sum of one
+ * series runs on a second stream beside the next series), so that each
+ * event interval holds one group's kernels only.
  * Groups: [0] R2C FFT + normalisation, [1] fused correlation/power,
  * [2] statistics + harmonic sum/threshold, [3] candidate ordering/output.
  * --------------------------------------------------------------------- */

@@ -34,6 +34,11 @@ paper and follows the stated readings):
                      (Gamma(h,1) tail at the Gaussian-equivalent false-alarm
                      probability of `sigma`), or T_h = h*mean + sigma*sqrt(h)*std.
 8. ``candidates``    every cell above threshold, sorted by (trial, h, iz, ir).
+9. ``fourier_power`` the off-grid power used to refine candidates:
+                     F(r, z) = sum_k X'_k conj(rho(r - k, z)) over the bins
+                     within 32 + ceil(|z|/2) of round(r), unnormalised rho,
+                     P = |F|^2 (gradients are checked by finite differences
+                     of this function in the tests).
 """
 from __future__ import annotations
 
@@ -390,6 +395,25 @@ def candidates(P: np.ndarray, geom: Geometry, mean: float, std: float,
     cands = np.sort(rec[is_cand], order=["trial", "harm", "iz", "ir"])
     guards = np.sort(rec[in_guard], order=["trial", "harm", "iz", "ir"])
     return cands, guards
+
+
+# --------------------------------------------------------------------------
+# Fourier-interpolated power for candidate refinement
+# --------------------------------------------------------------------------
+def refine_window(r: float, z: float, n_r: int) -> np.ndarray:
+    """Bins k with |k - round(r)| <= 32 + ceil(|z|/2), clipped to [0, N_r)."""
+    k0 = int(math.floor(r + 0.5))
+    m = 32 + math.ceil(abs(z) / 2.0 - 1e-12)
+    return np.arange(max(0, k0 - m), min(n_r, k0 + m + 1))
+
+
+def fourier_power(Xn: np.ndarray, r: float, z: float):
+    """(P, F) with F(r, z) = sum_k X'_k conj(rho(r - k, z)) over refine_window
+    and P = |F|^2, rho unnormalised (a signal X_k = c rho(r0 - k, z0) gives
+    P(r0, z0) ~ |c|^2, independent of z0)."""
+    k = refine_window(r, z, Xn.shape[0])
+    F = np.sum(Xn[k] * np.conj(rho(r - k, z)))
+    return float(abs(F) ** 2), complex(F)
 
 
 # --------------------------------------------------------------------------

@@ -39,7 +39,8 @@ FDAS_NORM_MEDIAN, FDAS_NORM_NONE = 0, 1
 EXPORTED = ["fdas_opts_default", "fdas_plan_create", "fdas_plan_destroy",
             "fdas_plan_get_info", "fdas_search", "fdas_spectrum", "fdas_power_plane",
             "fdas_harmonic_sums", "fdas_threshold", "fdas_template_bank",
-            "fdas_spectrum_static", "fdas_profile_enable", "fdas_profile_read",
+            "fdas_spectrum_static", "fdas_fourier_power", "fdas_fourier_power_backward",
+            "fdas_refine", "fdas_profile_enable", "fdas_profile_read",
             "fdas_last_error", "fdas_version"]
 
 
@@ -73,6 +74,23 @@ class fdas_plan_info(Structure):
                 ("tsamp", c_double), ("z_max", c_double), ("z_step", c_double),
                 ("threshold_sigma", c_double), ("stage_factor", c_double * 6),
                 ("workspace_bytes", c_int64)]
+
+
+class fdas_seed(Structure):
+    _fields_ = [("r", c_double), ("z", c_double), ("trial_id", c_uint32), ("reserved", c_uint32)]
+
+
+class fdas_refined(Structure):
+    _fields_ = [("r", c_double), ("z", c_double), ("power", c_float), ("dpdr", c_float),
+                ("dpdz", c_float), ("steps", c_int32), ("trial_id", c_uint32),
+                ("reserved", c_uint32)]
+
+
+SEED_DTYPE = np.dtype([("r", np.float64), ("z", np.float64), ("trial_id", np.uint32),
+                       ("reserved", np.uint32)])
+REFINED_DTYPE = np.dtype([("r", np.float64), ("z", np.float64), ("power", np.float32),
+                          ("dpdr", np.float32), ("dpdz", np.float32), ("steps", np.int32),
+                          ("trial_id", np.uint32), ("reserved", np.uint32)])
 
 
 class fdas_profile(Structure):
@@ -126,6 +144,15 @@ def lib() -> ctypes.CDLL:
         L.fdas_spectrum_static.argtypes = [c_void_p, c_int64, c_int32, c_int32, c_int32,
                                            c_void_p, c_void_p, c_void_p]
         L.fdas_spectrum_static.restype = c_int32
+        L.fdas_fourier_power.argtypes = [c_void_p, c_void_p, c_void_p, c_int32, c_void_p,
+                                         c_void_p, c_void_p]
+        L.fdas_fourier_power.restype = c_int32
+        L.fdas_fourier_power_backward.argtypes = [c_void_p, c_void_p, c_void_p, c_int32, c_void_p,
+                                                  c_void_p, c_void_p, c_void_p]
+        L.fdas_fourier_power_backward.restype = c_int32
+        L.fdas_refine.argtypes = [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_void_p,
+                                  c_void_p]
+        L.fdas_refine.restype = c_int32
         L.fdas_profile_enable.argtypes = [c_void_p, c_int32]
         L.fdas_profile_enable.restype = c_int32
         L.fdas_profile_read.argtypes = [c_void_p, POINTER(fdas_profile)]
@@ -209,6 +236,23 @@ def fdas_spectrum_static(series_ptr, n_samples, precision, norm_mode, norm_block
                          spectrum_ptr, medians_ptr=None, stream=None):
     _check(lib().fdas_spectrum_static(series_ptr, n_samples, precision, norm_mode, norm_block,
                                       spectrum_ptr, medians_ptr, stream), "fdas_spectrum_static")
+
+
+def fdas_fourier_power(plan, spectrum_ptr, rz_ptr, n, power_ptr, grad_ptr=None, stream=None):
+    _check(lib().fdas_fourier_power(plan, spectrum_ptr, rz_ptr, n, power_ptr, grad_ptr, stream),
+           "fdas_fourier_power")
+
+
+def fdas_fourier_power_backward(plan, spectrum_ptr, rz_ptr, n, grad_power_ptr,
+                                grad_spectrum_ptr=None, grad_rz_ptr=None, stream=None):
+    _check(lib().fdas_fourier_power_backward(plan, spectrum_ptr, rz_ptr, n, grad_power_ptr,
+                                             grad_spectrum_ptr, grad_rz_ptr, stream),
+           "fdas_fourier_power_backward")
+
+
+def fdas_refine(plan, spectrum_ptr, seeds_ptr, n, n_steps, out_ptr, stream=None):
+    _check(lib().fdas_refine(plan, spectrum_ptr, seeds_ptr, n, n_steps, out_ptr, stream),
+           "fdas_refine")
 
 
 def fdas_profile_enable(plan, on: bool) -> None:
@@ -337,6 +381,29 @@ class Plan:
                                 out.ctypes.data_as(c_void_p), capacity, _stream_ptr(stream))
         return st, out[:min(nf, capacity)], nf
 
+    # -- refinement (spectrum: complex64 device tensor of N_r bins) ------------
+    def fourier_power(self, spectrum, rz, stream=None):
+        """(P float32[n], grad float32[n, 2]) at rz (float64 device tensor [n, 2])."""
+        import torch
+        sp = torch.view_as_real(spectrum.contiguous())
+        rz = rz.contiguous()
+        n = rz.shape[0]
+        P = torch.empty(n, dtype=torch.float32, device=rz.device)
+        g = torch.empty((n, 2), dtype=torch.float32, device=rz.device)
+        fdas_fourier_power(self.handle, c_void_p(sp.data_ptr()), c_void_p(rz.data_ptr()), n,
+                           c_void_p(P.data_ptr()), c_void_p(g.data_ptr()), _stream_ptr(stream))
+        return P, g
+
+    def refine(self, spectrum, seeds, n_steps=50, stream=None):
+        """seeds: numpy SEED_DTYPE array (host); returns a REFINED_DTYPE array."""
+        import torch
+        sp = torch.view_as_real(spectrum.contiguous())
+        seeds = np.ascontiguousarray(seeds, dtype=SEED_DTYPE)
+        out = np.zeros(seeds.shape[0], dtype=REFINED_DTYPE)
+        fdas_refine(self.handle, c_void_p(sp.data_ptr()), seeds.ctypes.data_as(c_void_p),
+                    seeds.shape[0], n_steps, out.ctypes.data_as(c_void_p), _stream_ptr(stream))
+        return out
+
     def template_bank(self):
         """(taps list per z of complex128 arrays, energies)."""
         info = self.info
@@ -353,3 +420,50 @@ class Plan:
             out.append(c[acc:acc + 2 * mm + 1])
             acc += 2 * mm + 1
         return out, energy
+
+
+def _fourier_power_function():
+    import torch
+
+    class FourierPower(torch.autograd.Function):
+        """P(r, z) of a complex64 spectrum at float64 points rz [n, 2]; the
+        backward pass runs the library's backward kernel."""
+
+        @staticmethod
+        def forward(ctx, plan, spectrum, rz):
+            P, _ = plan.fourier_power(spectrum, rz)
+            ctx.plan = plan
+            ctx.save_for_backward(spectrum, rz)
+            return P
+
+        @staticmethod
+        def backward(ctx, gP):
+            spectrum, rz = ctx.saved_tensors
+            plan = ctx.plan
+            gP = gP.contiguous().to(torch.float32)
+            g_spec = g_rz = None
+            want_s, want_rz = ctx.needs_input_grad[1], ctx.needs_input_grad[2]
+            sp = torch.view_as_real(spectrum.contiguous())
+            if want_s:
+                g_spec = torch.zeros_like(spectrum)
+            if want_rz:
+                g_rz = torch.empty_like(rz)
+            fdas_fourier_power_backward(
+                plan.handle, c_void_p(sp.data_ptr()), c_void_p(rz.contiguous().data_ptr()),
+                rz.shape[0], c_void_p(gP.data_ptr()),
+                c_void_p(torch.view_as_real(g_spec).data_ptr()) if want_s else None,
+                c_void_p(g_rz.data_ptr()) if want_rz else None, _stream_ptr(None))
+            return None, g_spec, g_rz
+
+    return FourierPower
+
+
+_FP = None
+
+
+def FourierPower():
+    """The torch.autograd.Function for P(r, z) (built on first use)."""
+    global _FP
+    if _FP is None:
+        _FP = _fourier_power_function()
+    return _FP

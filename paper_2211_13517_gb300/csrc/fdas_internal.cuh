@@ -132,6 +132,10 @@ struct Plan {
     fdas_candidate *out_stage = nullptr;   // [max_cands] ordered output
     float *stage = nullptr;         // [n_samples] device copy of a host series
     unsigned long long *host_small = nullptr;  // pinned: {count, flags}
+    float2 *gl_nodes = nullptr;     // Gauss-Legendre (u, w) on [0, 1] for P(r, z)
+    fdas_seed *ref_seeds = nullptr;        // device staging of refine seeds
+    fdas_refined *ref_out = nullptr;       // device staging of refine results
+    int64_t ref_cap = 0;
     int64_t ws_bytes = 0;
     // tracing
     bool profiling = false;
@@ -164,5 +168,14 @@ fdas_status launch_harmonic_sums(Plan &p, const void *plane, float *out,
                                  cudaStream_t s);
 fdas_status launch_candidates_finish(Plan &p, int64_t n, fdas_candidate *out_dev,
                                      cudaStream_t s);
+std::vector<float2> gauss_legendre_01(int n);
+int refine_nodes();
+fdas_status launch_fourier_power(Plan &p, const float2 *X, const double2 *rz, int n, float *power,
+                                 float2 *grad, cudaStream_t s);
+fdas_status launch_fourier_power_backward(Plan &p, const float2 *X, const double2 *rz, int n,
+                                          const float *gP, float2 *grad_X, double2 *grad_rz,
+                                          cudaStream_t s);
+fdas_status launch_refine(Plan &p, const float2 *X, const fdas_seed *seeds, int n, int n_steps,
+                          fdas_refined *out, cudaStream_t s);
 
 }  // namespace fdas

@@ -87,6 +87,9 @@ static void free_plan_memory(Plan *p) {
     cudaFree(p->flags);
     cudaFree(p->out_stage);
     cudaFree(p->stage);
+    cudaFree(p->gl_nodes);
+    cudaFree(p->ref_seeds);
+    cudaFree(p->ref_out);
     if (p->host_small) cudaFreeHost(p->host_small);
     for (cudaEvent_t e : p->events) cudaEventDestroy(e);
     if (p->aux) cudaStreamDestroy(p->aux);
@@ -286,6 +289,12 @@ static fdas_status create(Plan *&out, int64_t n_samples, double tsamp, double z_
     PLAN_CUDA(cudaMallocHost((void **)&p.host_small, 4 * sizeof(unsigned long long)));
     PLAN_CUDA(cudaStreamCreateWithFlags(&p.aux, cudaStreamNonBlocking));
 
+    {
+        const std::vector<float2> gl = gauss_legendre_01(refine_nodes());
+        PLAN_TRY(dalloc(p, &p.gl_nodes, sizeof(float2) * gl.size()));
+        PLAN_CUDA(cudaMemcpy(p.gl_nodes, gl.data(), sizeof(float2) * gl.size(),
+                             cudaMemcpyHostToDevice));
+    }
     PLAN_CUDA(cudaMemset(p.spec_pad, 0, cb * pad_elems));
     PLAN_CUDA(cudaMemcpy(p.tap_off, off.data(), sizeof(int64_t) * p.n_z, cudaMemcpyHostToDevice));
     PLAN_CUDA(cudaMemcpy(p.tap_m, m.data(), sizeof(int32_t) * p.n_z, cudaMemcpyHostToDevice));
@@ -420,7 +429,7 @@ static fdas_status search(Plan &p, const fdas_series *batch, int32_t n_series,
     void *spec = (char *)p.spec_pad + cb * (size_t)p.m_ov;
     std::vector<Interval> iv;
     if (p.profiling) {
-        FDAS_TRY(events_reserve(p, 6 * (size_t)n_series + 2));
+        FDAS_TRY(events_reserve(p, 7 * (size_t)n_series + 2));
         iv.reserve(3 * (size_t)n_series + 1);
     }
     size_t ev = 0;
@@ -430,6 +439,9 @@ static fdas_status search(Plan &p, const fdas_series *batch, int32_t n_series,
         return e;
     };
     const int spectrum_launches = (p.fft_m1 == 1 ? 1 : 2) + 1;
+    // while tracing, every group runs on the caller's stream, so that each
+    // event interval holds the kernels of one group and nothing else
+    cudaStream_t hs = p.profiling ? s : p.aux;
     for (int32_t t = 0; t < n_series; ++t) {
         const int b = t & 1;
         const float *x = batch[t].data;
@@ -438,20 +450,25 @@ static fdas_status search(Plan &p, const fdas_series *batch, int32_t n_series,
                                           cudaMemcpyHostToDevice, s));
             x = p.stage;
         }
-        if (t >= 2) FDAS_CUDA_TRY(cudaStreamWaitEvent(s, p.ev_hsum[b], 0));
         cudaEvent_t e0 = p.profiling ? mark(s) : nullptr;
         FDAS_TRY(launch_spectrum(p, x, spec, nullptr, s));
         cudaEvent_t e1 = p.profiling ? mark(s) : nullptr;
+        // plane[b] and partials[b] are free once the harmonic sum of series t-2
+        // is done; only the correlation writes them
+        if (t >= 2) {
+            FDAS_CUDA_TRY(cudaStreamWaitEvent(s, p.ev_hsum[b], 0));
+            if (p.profiling) e1 = mark(s);
+        }
         FDAS_TRY(launch_correlate(p, p.spec_pad, p.plane[b], p.partials[b], s));
         cudaEvent_t e2 = p.profiling ? mark(s) : nullptr;
         FDAS_CUDA_TRY(cudaEventRecord(p.ev_conv[b], s));
-        FDAS_CUDA_TRY(cudaStreamWaitEvent(p.aux, p.ev_conv[b], 0));
-        cudaEvent_t e3 = p.profiling ? mark(p.aux) : nullptr;
+        FDAS_CUDA_TRY(cudaStreamWaitEvent(hs, p.ev_conv[b], 0));
+        cudaEvent_t e3 = p.profiling ? mark(hs) : nullptr;
         TrialStats *ts = p.stats + rank[t];
-        FDAS_TRY(launch_finalize_stats(p, p.partials[b], correlate_ctas(p), nullptr, ts, p.aux));
-        FDAS_TRY(launch_harmonic_threshold(p, p.plane[b], ts, (uint32_t)rank[t], p.aux));
-        cudaEvent_t e4 = p.profiling ? mark(p.aux) : nullptr;
-        FDAS_CUDA_TRY(cudaEventRecord(p.ev_hsum[b], p.aux));
+        FDAS_TRY(launch_finalize_stats(p, p.partials[b], correlate_ctas(p), nullptr, ts, hs));
+        FDAS_TRY(launch_harmonic_threshold(p, p.plane[b], ts, (uint32_t)rank[t], hs));
+        cudaEvent_t e4 = p.profiling ? mark(hs) : nullptr;
+        FDAS_CUDA_TRY(cudaEventRecord(p.ev_hsum[b], hs));
         p.launches[FDAS_PROF_SPECTRUM] += spectrum_launches;
         p.launches[FDAS_PROF_CORRELATE] += 1;
         p.launches[FDAS_PROF_HARMONIC] += 2;
@@ -625,6 +642,56 @@ fdas_status fdas_template_bank(fdas_plan *plan, double *taps_out, double *energy
     if (bank_out)
         FDAS_CUDA_TRY(cudaMemcpyAsync(bank_out, p.bank, cpx_bytes(p.prec) * (size_t)p.n_z * p.L,
                                       cudaMemcpyDeviceToDevice, s));
+    FDAS_CUDA_TRY(cudaStreamSynchronize(s));
+    return FDAS_OK;
+}
+
+fdas_status fdas_fourier_power(fdas_plan *plan, const float *spectrum, const double *rz, int32_t n,
+                               float *power, float *grad_rz, void *stream) {
+    if (!plan || !spectrum || (n > 0 && (!rz || !power))) return arg_error("NULL argument");
+    if (n < 0) return arg_error("n < 0");
+    Plan &p = *reinterpret_cast<Plan *>(plan);
+    DeviceGuard guard(p.device);
+    return launch_fourier_power(p, (const float2 *)spectrum, (const double2 *)rz, n, power,
+                                (float2 *)grad_rz, (cudaStream_t)stream);
+}
+
+fdas_status fdas_fourier_power_backward(fdas_plan *plan, const float *spectrum, const double *rz,
+                                        int32_t n, const float *grad_power, float *grad_spectrum,
+                                        double *grad_rz, void *stream) {
+    if (!plan || !spectrum || (n > 0 && (!rz || !grad_power))) return arg_error("NULL argument");
+    if (n < 0) return arg_error("n < 0");
+    Plan &p = *reinterpret_cast<Plan *>(plan);
+    DeviceGuard guard(p.device);
+    return launch_fourier_power_backward(p, (const float2 *)spectrum, (const double2 *)rz, n,
+                                         grad_power, (float2 *)grad_spectrum, (double2 *)grad_rz,
+                                         (cudaStream_t)stream);
+}
+
+fdas_status fdas_refine(fdas_plan *plan, const float *spectrum, const fdas_seed *seeds, int32_t n,
+                        int32_t n_steps, fdas_refined *out, void *stream) {
+    if (!plan || !spectrum || (n > 0 && (!seeds || !out))) return arg_error("NULL argument");
+    if (n < 0 || n_steps < 0) return arg_error("n and n_steps must be >= 0");
+    Plan &p = *reinterpret_cast<Plan *>(plan);
+    DeviceGuard guard(p.device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n == 0) return FDAS_OK;
+    if (n > p.ref_cap) {
+        FDAS_CUDA_TRY(cudaStreamSynchronize(s));
+        cudaFree(p.ref_seeds);
+        cudaFree(p.ref_out);
+        p.ref_seeds = nullptr;
+        p.ref_out = nullptr;
+        p.ref_cap = 0;
+        FDAS_TRY(dalloc(p, &p.ref_seeds, sizeof(fdas_seed) * (size_t)n));
+        FDAS_TRY(dalloc(p, &p.ref_out, sizeof(fdas_refined) * (size_t)n));
+        p.ref_cap = n;
+    }
+    FDAS_CUDA_TRY(cudaMemcpyAsync(p.ref_seeds, seeds, sizeof(fdas_seed) * (size_t)n,
+                                  cudaMemcpyDefault, s));
+    FDAS_TRY(launch_refine(p, (const float2 *)spectrum, p.ref_seeds, n, n_steps, p.ref_out, s));
+    FDAS_CUDA_TRY(cudaMemcpyAsync(out, p.ref_out, sizeof(fdas_refined) * (size_t)n,
+                                  cudaMemcpyDefault, s));
     FDAS_CUDA_TRY(cudaStreamSynchronize(s));
     return FDAS_OK;
 }

@@ -350,3 +350,28 @@ def test_noise_only_false_alarms_are_rare():
     x = S.white_noise(1 << 17, 99)
     r = O.search(x, 16.0, 2.0, 4)
     assert len(r["candidates"]) <= 3
+
+
+# --------------------------------------------------------------------------
+# Fourier-interpolated power (refinement)
+# --------------------------------------------------------------------------
+def test_fourier_power_integer_r_zero_z_is_the_bin():
+    X = O.spectrum(S.white_noise(4096, 8))
+    for r in (10, 500, 1999):
+        P, F = O.fourier_power(X, float(r), 0.0)
+        assert abs(F - X[r]) < 1e-10 * abs(X[r])
+
+
+@pytest.mark.parametrize("r0,z0", [(1000.37, 12.6), (1500.81, -33.2)])
+def test_fourier_power_peak_of_an_injection(r0, z0):
+    n_r = 4096
+    k = np.arange(n_r)
+    c = 2.0 + 1.0j
+    X = c * rho_fresnel(r0 - k, z0)
+    P, F = O.fourier_power(X, r0, z0)
+    w = O.refine_window(r0, z0, n_r)
+    E = np.sum(np.abs(rho_fresnel(r0 - w, z0)) ** 2)
+    assert abs(F - c * E) < 1e-10 * abs(c)          # F = c sum |rho|^2 on the window
+    assert 0.99 < E < 1.0
+    for dr, dz in ((0.03, 0), (-0.03, 0), (0, 0.3), (0, -0.3)):
+        assert O.fourier_power(X, r0 + dr, z0 + dz)[0] < P
