@@ -282,6 +282,20 @@ def run_gpu(args, rank, world, local_rank, dist):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
+    def timed_stream(plan, inputs, steps, warmup, stream):
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                plan.search(inputs, capacity=1 << 16, stream=stream)
+            barrier()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            for _ in range(steps):
+                plan.search(inputs, capacity=1 << 16, stream=stream)
+            ev1.record(stream)
+        barrier()
+        return max_over_ranks(ev0.elapsed_time(ev1))
+
     def timed(plan, inputs, steps, warmup, profile=False, energy=None, clocks=None):
         for _ in range(warmup):
             plan.search(inputs, capacity=1 << 16)
@@ -329,6 +343,10 @@ def run_gpu(args, rank, world, local_rank, dist):
                                                  energy)
         plan32.close()
 
+    # --- uneven batch: full-length and decimated series in one call, graph ---
+    uneven = None
+    if not args.no_uneven:
+        uneven = run_uneven(args, dev, capi, S, timed_uneven=timed_stream)
     trials = args.batch * args.steps * world
     value = trials / (ms_bf16 / 1000.0)
     if rank != 0:
@@ -395,9 +413,37 @@ def run_gpu(args, rank, world, local_rank, dist):
                         "hbm_alg_frac": wm32["alg_bytes"] * args.batch * args.steps
                         / (ms_fp32 / 1000.0) / 1e9 / peak_hbm}
         line["bf16_speedup_vs_fp32"] = value / v32
+    if uneven is not None:
+        line["uneven_batch"] = uneven
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
+
+
+def run_uneven(args, dev, capi, S, timed_uneven):
+    """The uneven persistent-batch case: series at full length and decimated
+    by 2, 4 and 8 in the proportions 3050 : 959 : 958 : 958, one fdas_search
+    per step replayed as one CUDA graph, BF16 storage."""
+    import torch
+    B = args.uneven_batch
+    counts = [round(B * c / 5925) for c in (3050, 959, 958, 958)]
+    counts[0] += B - sum(counts)
+    xs = []
+    for d, c in enumerate(counts):
+        if c:
+            part, _ = S.torch_batch_series(c, N_SAMPLES >> d, base_seed=5000 + 1000 * d, device=dev)
+            xs += part
+    torch.cuda.synchronize()
+    plan = capi.Plan(N_SAMPLES, TSAMP, Z_MAX, Z_STEP, SEG_LEN, N_HARM, precision=capi.FDAS_BF16,
+                     use_graph=True)
+    side = torch.cuda.Stream(device=dev)
+    ms = timed_uneven(plan, xs, args.steps, args.warmup, side)
+    plan.close()
+    equiv = sum(c / (1 << d) for d, c in enumerate(counts))
+    return {"series_per_step": B, "split_full_div2_div4_div8": counts,
+            "value": B * args.steps / (ms / 1000.0), "unit": "series/s",
+            "full_length_equiv_per_s": equiv * args.steps / (ms / 1000.0),
+            "ms_per_step": ms / args.steps, "use_graph": True, "precision": "bf16"}
 
 
 def _ncu_traffic(kernel_group, prec):
@@ -424,6 +470,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-uneven", action="store_true")
+    ap.add_argument("--uneven-batch", type=int, default=64)
     ap.add_argument("--n-log2", type=int, default=23,
                     help="series length 2^n (smaller only for profiling captures)")
     args = ap.parse_args()

@@ -63,17 +63,23 @@ typedef struct {
     int32_t norm_mode;       /* FDAS_NORM_MEDIAN (default)                          */
     int32_t norm_block;      /* bins per median block, power of 2 in [16, 8192]; 2048 */
     int64_t max_candidates;  /* device candidate store per search call; 1<<20     */
-    int32_t autotune;        /* reserved, must be 0                                 */
-    int32_t reserved;
+    int32_t autotune;        /* 1: pick seg_len (among 2048, 4096, 8192 and the one
+                                asked for) and the template chunking by timing the
+                                correlation at plan creation; 0 (default): as given */
+    int32_t use_graph;       /* 1: fdas_search captures each batch's launches into
+                                one CUDA graph and replays it (device or pinned
+                                series, a non-default stream); 0 (default): direct */
 } fdas_opts;
 
 /* One dedispersed time series (one DM trial).  `data` points to n_samples
  * FP32 values (16-byte aligned) in device memory, or in host memory (pinned
  * or pageable), which the search copies to the device itself; it is only
- * read. */
+ * read.  n_samples may be the plan's length or that length divided by a
+ * power of two (a series decimated in time: same observation, so the same
+ * z grid and templates, half the bins per halving), down to 2^10. */
 typedef struct {
     const float *data;
-    int64_t n_samples;   /* must equal the plan's n_samples                 */
+    int64_t n_samples;   /* plan's n_samples / 2^d, d >= 0, at least 2^10   */
     int32_t decimation;  /* informational (1 = full time resolution)        */
     uint32_t trial_id;   /* caller's DM-trial id, echoed into candidates    */
 } fdas_series;
@@ -99,6 +105,9 @@ typedef struct {
     double tsamp, z_max, z_step, threshold_sigma;
     double stage_factor[6];   /* G_h = Q^-1(h, Phibar(sigma)) per stage h = 2^s */
     int64_t workspace_bytes;  /* device memory the plan holds                  */
+    int32_t z_chunks;         /* template chunks per segment in the correlation */
+    int32_t use_graph;
+    double tuned_ms;          /* autotune: correlation time per series (ms), else 0 */
 } fdas_plan_info;
 
 typedef struct fdas_plan fdas_plan;

@@ -48,7 +48,7 @@ class fdas_opts(Structure):
     _fields_ = [("precision", c_int32), ("threshold_sigma", c_double),
                 ("threshold_mode", c_int32), ("norm_mode", c_int32),
                 ("norm_block", c_int32), ("max_candidates", c_int64),
-                ("autotune", c_int32), ("reserved", c_int32)]
+                ("autotune", c_int32), ("use_graph", c_int32)]
 
 
 class fdas_series(Structure):
@@ -73,7 +73,8 @@ class fdas_plan_info(Structure):
                 ("norm_block", c_int32), ("threshold_mode", c_int32),
                 ("tsamp", c_double), ("z_max", c_double), ("z_step", c_double),
                 ("threshold_sigma", c_double), ("stage_factor", c_double * 6),
-                ("workspace_bytes", c_int64)]
+                ("workspace_bytes", c_int64), ("z_chunks", c_int32), ("use_graph", c_int32),
+                ("tuned_ms", c_double)]
 
 
 class fdas_seed(Structure):
@@ -289,7 +290,7 @@ class Plan:
     def __init__(self, n_samples, tsamp=64e-6, z_max=96.0, z_step=1.0, seg_len=8192,
                  n_harm=16, precision=FDAS_FP32, threshold_sigma=6.0,
                  threshold_mode=FDAS_THRESH_GAMMA_TAIL, norm_mode=FDAS_NORM_MEDIAN,
-                 norm_block=2048, max_candidates=1 << 20):
+                 norm_block=2048, max_candidates=1 << 20, autotune=False, use_graph=False):
         o = fdas_opts_default()
         o.precision = precision
         o.threshold_sigma = threshold_sigma
@@ -297,6 +298,8 @@ class Plan:
         o.norm_mode = norm_mode
         o.norm_block = norm_block
         o.max_candidates = max_candidates
+        o.autotune = 1 if autotune else 0
+        o.use_graph = 1 if use_graph else 0
         self.handle = fdas_plan_create(n_samples, tsamp, z_max, z_step, seg_len, n_harm, o)
         self.info = fdas_plan_get_info(self.handle)
 

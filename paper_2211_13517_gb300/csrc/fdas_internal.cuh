@@ -110,6 +110,10 @@ struct Plan {
     int device;
     int n_zchunk;           // z chunks per segment in the correlation grid
     int n_sms = 1;          // streaming multiprocessors of the device
+    int64_t partials_cap = 0;   // double2 entries of each partials buffer
+    bool use_graph = false;
+    cudaGraphExec_t graph_exec = nullptr;   // last captured batch
+    double tuned_ms = 0.0;
     // FFT split of the N/2-point complex FFT in the spectrum stage
     int fft_m1, fft_m2;     // M = m1 * m2 (m1 = 1: single pass)
     // device memory

@@ -93,6 +93,7 @@ static void free_plan_memory(Plan *p) {
     if (p->host_small) cudaFreeHost(p->host_small);
     for (cudaEvent_t e : p->events) cudaEventDestroy(e);
     if (p->aux) cudaStreamDestroy(p->aux);
+    if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
 }
 
 template <class T>
@@ -149,6 +150,31 @@ static int choose_zchunks(const Plan &p, int slots) {
     return best;
 }
 
+// geometry of a series of n samples (the plan's length or a power-of-two
+// fraction of it) on the plan's z grid and segment length
+static void set_length(Plan &p, int64_t n) {
+    p.n_samples = n;
+    p.n_r = n / 2;
+    p.n_seg = (int)((p.n_r + p.V - 1) / p.V);
+    const int lm = ilog2(p.n_r);
+    if (p.n_r <= 8192) {
+        p.fft_m1 = 1;
+        p.fft_m2 = (int)p.n_r;
+    } else {
+        p.fft_m1 = 1 << (lm / 2);
+        p.fft_m2 = 1 << (lm - lm / 2);
+    }
+}
+
+// the plan's buffers with the geometry of a shorter series
+static Plan plan_view(const Plan &p, int64_t n) {
+    Plan v = p;
+    set_length(v, n);
+    v.n_zchunk = choose_zchunks(v, v.n_sms);
+    while (v.n_zchunk > 1 && (int64_t)v.n_seg * v.n_zchunk > p.partials_cap) --v.n_zchunk;
+    return v;
+}
+
 static fdas_status create(Plan *&out, int64_t n_samples, double tsamp, double z_max, double z_step,
                           int32_t seg_len, int32_t n_harm, const fdas_opts *o) {
     if (!is_pow2(n_samples) || n_samples < (1 << 10) || n_samples > (1 << 24))
@@ -177,7 +203,8 @@ static fdas_status create(Plan *&out, int64_t n_samples, double tsamp, double z_
         return arg_error("threshold_sigma must be in (0, 37]");
     if (o->max_candidates < 1 || o->max_candidates > (int64_t(1) << 26))
         return arg_error("max_candidates must be in [1, 2^26]");
-    if (o->autotune != 0) return arg_error("autotune is reserved and must be 0");
+    if (o->autotune != 0 && o->autotune != 1) return arg_error("autotune must be 0 or 1");
+    if (o->use_graph != 0 && o->use_graph != 1) return arg_error("use_graph must be 0 or 1");
 
     Plan *pp = new (std::nothrow) Plan();
     if (!pp) return arg_error("out of host memory");
@@ -225,15 +252,8 @@ static fdas_status create(Plan *&out, int64_t n_samples, double tsamp, double z_
         return FDAS_ERR_UNSUPPORTED;
     }
     p.V = p.L - 2 * p.m_ov;
-    p.n_seg = (int)((p.n_r + p.V - 1) / p.V);
-    const int lm = ilog2(p.n_r);
-    if (p.n_r <= 8192) {
-        p.fft_m1 = 1;
-        p.fft_m2 = (int)p.n_r;
-    } else {
-        p.fft_m1 = 1 << (lm / 2);
-        p.fft_m2 = 1 << (lm - lm / 2);
-    }
+    set_length(p, n_samples);
+    p.use_graph = o->use_graph != 0;
 
     cudaError_t ce = cudaGetDevice(&p.device);
     if (ce != cudaSuccess) {
@@ -244,6 +264,14 @@ static fdas_status create(Plan *&out, int64_t n_samples, double tsamp, double z_
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device);
     p.n_sms = std::max(1, sms);
     p.n_zchunk = choose_zchunks(p, p.n_sms);
+    // partials serve every length the plan accepts (N, N/2, ..., 2^10) and
+    // any template chunking up to 32
+    p.partials_cap = (int64_t)p.n_seg * 32;
+    for (int64_t n = n_samples; n >= (1 << 10); n /= 2) {
+        Plan v = p;
+        set_length(v, n);
+        p.partials_cap = std::max<int64_t>(p.partials_cap, (int64_t)v.n_seg * 32);
+    }
 
     fdas_status st = FDAS_OK;
     auto fail = [&](fdas_status s) {
@@ -275,7 +303,7 @@ static fdas_status create(Plan *&out, int64_t n_samples, double tsamp, double z_
     PLAN_TRY(dalloc(p, &p.spec_pad, cb * pad_elems));
     for (int b = 0; b < 2; ++b) {
         PLAN_TRY(dalloc(p, &p.plane[b], rb * (size_t)p.n_z * (size_t)p.n_r));
-        PLAN_TRY(dalloc(p, &p.partials[b], sizeof(double2) * (size_t)correlate_ctas(p)));
+        PLAN_TRY(dalloc(p, &p.partials[b], sizeof(double2) * (size_t)p.partials_cap));
         PLAN_CUDA(cudaEventCreateWithFlags(&p.ev_conv[b], cudaEventDisableTiming));
         PLAN_CUDA(cudaEventCreateWithFlags(&p.ev_hsum[b], cudaEventDisableTiming));
     }
@@ -391,6 +419,116 @@ static void accumulate(Plan &p, const std::vector<Interval> &iv) {
     }
 }
 
+static bool is_pinned_or_device(const void *ptr) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged ||
+           a.type == cudaMemoryTypeHost;
+}
+
+// the per-series work of a batch, queued on s (and the plan's second
+// stream); returns the intervals to time when tracing
+static fdas_status enqueue_batch(Plan &p, const fdas_series *batch, int32_t n_series,
+                                 const std::vector<int32_t> &rank, cudaStream_t s,
+                                 std::vector<Interval> &iv, size_t &ev) {
+    const size_t cb = cpx_bytes(p.prec);
+    void *spec = (char *)p.spec_pad + cb * (size_t)p.m_ov;
+    auto mark = [&](cudaStream_t st) -> cudaEvent_t {
+        cudaEvent_t e = p.events[ev++];
+        cudaEventRecord(e, st);
+        return e;
+    };
+    // while tracing, every group runs on the caller's stream, so that each
+    // event interval holds the kernels of one group and nothing else
+    cudaStream_t hs = p.profiling ? s : p.aux;
+    for (int32_t t = 0; t < n_series; ++t) {
+        const int b = t & 1;
+        Plan v = batch[t].n_samples == p.n_samples ? p : plan_view(p, batch[t].n_samples);
+        const float *x = batch[t].data;
+        if (!is_device_ptr(x)) {
+            FDAS_CUDA_TRY(cudaMemcpyAsync(p.stage, x, sizeof(float) * (size_t)v.n_samples,
+                                          cudaMemcpyHostToDevice, s));
+            x = p.stage;
+        }
+        if (v.n_r < p.n_r) {
+            // a shorter series: the bins past its end must read as 0 again
+            const size_t tail = (size_t)v.n_seg * v.V + 2 * (size_t)v.m_ov - ((size_t)v.m_ov + v.n_r);
+            FDAS_CUDA_TRY(cudaMemsetAsync((char *)spec + cb * (size_t)v.n_r, 0, cb * tail, s));
+        }
+        cudaEvent_t e0 = p.profiling ? mark(s) : nullptr;
+        FDAS_TRY(launch_spectrum(v, x, spec, nullptr, s));
+        cudaEvent_t e1 = p.profiling ? mark(s) : nullptr;
+        // plane[b] and partials[b] are free once the harmonic sum of series t-2
+        // is done; only the correlation writes them
+        if (t >= 2) {
+            FDAS_CUDA_TRY(cudaStreamWaitEvent(s, p.ev_hsum[b], 0));
+            if (p.profiling) e1 = mark(s);
+        }
+        FDAS_TRY(launch_correlate(v, p.spec_pad, p.plane[b], p.partials[b], s));
+        cudaEvent_t e2 = p.profiling ? mark(s) : nullptr;
+        FDAS_CUDA_TRY(cudaEventRecord(p.ev_conv[b], s));
+        FDAS_CUDA_TRY(cudaStreamWaitEvent(hs, p.ev_conv[b], 0));
+        cudaEvent_t e3 = p.profiling ? mark(hs) : nullptr;
+        TrialStats *ts = p.stats + rank[t];
+        FDAS_TRY(launch_finalize_stats(v, p.partials[b], correlate_ctas(v), nullptr, ts, hs));
+        FDAS_TRY(launch_harmonic_threshold(v, p.plane[b], ts, (uint32_t)rank[t], hs));
+        cudaEvent_t e4 = p.profiling ? mark(hs) : nullptr;
+        FDAS_CUDA_TRY(cudaEventRecord(p.ev_hsum[b], hs));
+        p.launches[FDAS_PROF_SPECTRUM] += (v.fft_m1 == 1 ? 1 : 2) + 1;
+        p.launches[FDAS_PROF_CORRELATE] += 1;
+        p.launches[FDAS_PROF_HARMONIC] += 2;
+        if (p.profiling) {
+            iv.push_back({FDAS_PROF_SPECTRUM, e0, e1});
+            iv.push_back({FDAS_PROF_CORRELATE, e1, e2});
+            iv.push_back({FDAS_PROF_HARMONIC, e3, e4});
+        }
+    }
+    for (int b = 0; b < 2 && b < n_series; ++b)
+        FDAS_CUDA_TRY(cudaStreamWaitEvent(s, p.ev_hsum[(n_series - 1 - b) & 1], 0));
+    return FDAS_OK;
+}
+
+// capture the batch into one CUDA graph (updating the previous executable
+// when the launch sequence has the same shape) and launch it
+static fdas_status run_as_graph(Plan &p, const fdas_series *batch, int32_t n_series,
+                                const std::vector<int32_t> &rank, cudaStream_t s) {
+    std::vector<Interval> iv;
+    size_t ev = 0;
+    FDAS_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    fdas_status st = enqueue_batch(p, batch, n_series, rank, s, iv, ev);
+    cudaGraph_t g = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(s, &g);
+    if (st != FDAS_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    FDAS_CUDA_TRY(ce);
+    bool updated = false;
+    if (p.graph_exec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(p.graph_exec, g, &info) == cudaSuccess) updated = true;
+        else {
+            cudaGetLastError();
+            cudaGraphExecDestroy(p.graph_exec);
+            p.graph_exec = nullptr;
+        }
+    }
+    if (!updated) {
+        ce = cudaGraphInstantiate(&p.graph_exec, g, 0);
+        if (ce != cudaSuccess) {
+            cudaGraphDestroy(g);
+            p.graph_exec = nullptr;
+            return cuda_status(ce, "cudaGraphInstantiate");
+        }
+    }
+    cudaGraphDestroy(g);
+    FDAS_CUDA_TRY(cudaGraphLaunch(p.graph_exec, s));
+    return FDAS_OK;
+}
+
 static fdas_status search(Plan &p, const fdas_series *batch, int32_t n_series,
                           fdas_candidate *cands, int64_t capacity, int64_t *n_found,
                           cudaStream_t s) {
@@ -399,12 +537,17 @@ static fdas_status search(Plan &p, const fdas_series *batch, int32_t n_series,
     if (n_series > 0 && batch == nullptr) return arg_error("batch is NULL");
     if (n_found == nullptr) return arg_error("n_found is NULL");
     if (capacity < 0 || (capacity > 0 && cands == nullptr)) return arg_error("bad cands/capacity");
+    bool graphable = p.use_graph && !p.profiling && s != nullptr && s != cudaStreamLegacy &&
+                     s != cudaStreamPerThread;
     for (int32_t i = 0; i < n_series; ++i) {
+        const int64_t n = batch[i].n_samples;
         if (batch[i].data == nullptr) return arg_error("series " + std::to_string(i) + " has NULL data");
-        if (batch[i].n_samples != p.n_samples)
-            return arg_error("series " + std::to_string(i) + " length differs from the plan");
+        if (!is_pow2(n) || n > p.n_samples || n < (1 << 10))
+            return arg_error("series " + std::to_string(i) +
+                             " must hold the plan's n_samples / 2^d samples, at least 2^10");
         if (((uintptr_t)batch[i].data & 15u) != 0)
             return arg_error("series " + std::to_string(i) + " is not 16-byte aligned");
+        if (graphable && !is_pinned_or_device(batch[i].data)) graphable = false;
     }
     *n_found = 0;
     DeviceGuard guard(p.device);
@@ -425,71 +568,119 @@ static fdas_status search(Plan &p, const fdas_series *batch, int32_t n_series,
                                       cudaMemcpyHostToDevice, s));
     FDAS_CUDA_TRY(cudaMemsetAsync(p.cand_count, 0, sizeof(unsigned long long), s));
     FDAS_CUDA_TRY(cudaMemsetAsync(p.flags, 0, sizeof(unsigned int), s));
-    const size_t cb = cpx_bytes(p.prec);
-    void *spec = (char *)p.spec_pad + cb * (size_t)p.m_ov;
     std::vector<Interval> iv;
+    size_t ev = 0;
     if (p.profiling) {
         FDAS_TRY(events_reserve(p, 7 * (size_t)n_series + 2));
         iv.reserve(3 * (size_t)n_series + 1);
     }
-    size_t ev = 0;
-    auto mark = [&](cudaStream_t st) -> cudaEvent_t {
-        cudaEvent_t e = p.events[ev++];
-        cudaEventRecord(e, st);
-        return e;
-    };
-    const int spectrum_launches = (p.fft_m1 == 1 ? 1 : 2) + 1;
-    // while tracing, every group runs on the caller's stream, so that each
-    // event interval holds the kernels of one group and nothing else
-    cudaStream_t hs = p.profiling ? s : p.aux;
-    for (int32_t t = 0; t < n_series; ++t) {
-        const int b = t & 1;
-        const float *x = batch[t].data;
-        if (!is_device_ptr(x)) {
-            FDAS_CUDA_TRY(cudaMemcpyAsync(p.stage, x, sizeof(float) * (size_t)p.n_samples,
-                                          cudaMemcpyHostToDevice, s));
-            x = p.stage;
-        }
-        cudaEvent_t e0 = p.profiling ? mark(s) : nullptr;
-        FDAS_TRY(launch_spectrum(p, x, spec, nullptr, s));
-        cudaEvent_t e1 = p.profiling ? mark(s) : nullptr;
-        // plane[b] and partials[b] are free once the harmonic sum of series t-2
-        // is done; only the correlation writes them
-        if (t >= 2) {
-            FDAS_CUDA_TRY(cudaStreamWaitEvent(s, p.ev_hsum[b], 0));
-            if (p.profiling) e1 = mark(s);
-        }
-        FDAS_TRY(launch_correlate(p, p.spec_pad, p.plane[b], p.partials[b], s));
-        cudaEvent_t e2 = p.profiling ? mark(s) : nullptr;
-        FDAS_CUDA_TRY(cudaEventRecord(p.ev_conv[b], s));
-        FDAS_CUDA_TRY(cudaStreamWaitEvent(hs, p.ev_conv[b], 0));
-        cudaEvent_t e3 = p.profiling ? mark(hs) : nullptr;
-        TrialStats *ts = p.stats + rank[t];
-        FDAS_TRY(launch_finalize_stats(p, p.partials[b], correlate_ctas(p), nullptr, ts, hs));
-        FDAS_TRY(launch_harmonic_threshold(p, p.plane[b], ts, (uint32_t)rank[t], hs));
-        cudaEvent_t e4 = p.profiling ? mark(hs) : nullptr;
-        FDAS_CUDA_TRY(cudaEventRecord(p.ev_hsum[b], hs));
-        p.launches[FDAS_PROF_SPECTRUM] += spectrum_launches;
-        p.launches[FDAS_PROF_CORRELATE] += 1;
-        p.launches[FDAS_PROF_HARMONIC] += 2;
-        if (p.profiling) {
-            iv.push_back({FDAS_PROF_SPECTRUM, e0, e1});
-            iv.push_back({FDAS_PROF_CORRELATE, e1, e2});
-            iv.push_back({FDAS_PROF_HARMONIC, e3, e4});
-        }
+    if (graphable && n_series > 0) {
+        FDAS_TRY(run_as_graph(p, batch, n_series, rank, s));
+    } else {
+        FDAS_TRY(enqueue_batch(p, batch, n_series, rank, s, iv, ev));
     }
     p.prof_trials += n_series;
-    for (int b = 0; b < 2 && b < n_series; ++b)
-        FDAS_CUDA_TRY(cudaStreamWaitEvent(s, p.ev_hsum[(n_series - 1 - b) & 1], 0));
-    cudaEvent_t f0 = p.profiling ? mark(s) : nullptr;
+    cudaEvent_t f0 = nullptr;
+    if (p.profiling) {
+        f0 = p.events[ev++];
+        cudaEventRecord(f0, s);
+    }
     fdas_status st = collect(p, cands, capacity, n_found, s);
     if (p.profiling) {
-        cudaEvent_t f1 = mark(s);
+        cudaEvent_t f1 = p.events[ev++];
+        cudaEventRecord(f1, s);
         cudaEventSynchronize(f1);
         iv.push_back({FDAS_PROF_FINISH, f0, f1});
         accumulate(p, iv);
     }
     return st;
+}
+
+// time the correlation of one full-length series on a plan (synthetic unit
+// spectrum), median of a few runs, in ms
+static fdas_status time_correlation(Plan &p, double &ms) {
+    const size_t cb = cpx_bytes(p.prec);
+    cudaStream_t s = p.aux;
+    // any finite spectrum will do for timing: the plan's own zero-padded
+    // buffer with its interior set to a constant pattern
+    FDAS_CUDA_TRY(cudaMemsetAsync((char *)p.spec_pad + cb * (size_t)p.m_ov, 0x3c, cb * (size_t)p.n_r, s));
+    cudaEvent_t a, b;
+    FDAS_CUDA_TRY(cudaEventCreate(&a));
+    FDAS_CUDA_TRY(cudaEventCreate(&b));
+    std::vector<float> t;
+    fdas_status st = FDAS_OK;
+    for (int rep = 0; rep < 4 && st == FDAS_OK; ++rep) {
+        cudaEventRecord(a, s);
+        st = launch_correlate(p, p.spec_pad, p.plane[0], p.partials[0], s);
+        cudaEventRecord(b, s);
+        if (cudaEventSynchronize(b) != cudaSuccess) st = cuda_status(cudaGetLastError(), "autotune");
+        float x = 0.f;
+        cudaEventElapsedTime(&x, a, b);
+        if (rep > 0) t.push_back(x);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (st != FDAS_OK) return st;
+    std::sort(t.begin(), t.end());
+    ms = t[t.size() / 2];
+    return FDAS_OK;
+}
+
+// autotune: the segment length among {2048, 4096, 8192} and the one asked
+// for, then the template chunking of the fastest, by timing the correlation
+static fdas_status create_tuned(Plan *&out, int64_t n_samples, double tsamp, double z_max,
+                                double z_step, int32_t seg_len, int32_t n_harm, fdas_opts o) {
+    o.autotune = 0;
+    std::vector<int32_t> cand = {2048, 4096, 8192};
+    if (std::find(cand.begin(), cand.end(), seg_len) == cand.end()) cand.push_back(seg_len);
+    Plan *best = nullptr;
+    double best_ms = 1e300;
+    std::string first_error;
+    fdas_status first_status = FDAS_OK;
+    for (int32_t L : cand) {
+        Plan *p = nullptr;
+        fdas_status s = create(p, n_samples, tsamp, z_max, z_step, L, n_harm, &o);
+        if (s != FDAS_OK) {
+            if (first_status == FDAS_OK) {
+                first_status = s;
+                first_error = g_last_error;
+            }
+            continue;
+        }
+        double ms = 0.0;
+        s = time_correlation(*p, ms);
+        if (s == FDAS_OK && ms < best_ms) {
+            if (best) {
+                free_plan_memory(best);
+                delete best;
+            }
+            best = p;
+            best_ms = ms;
+        } else {
+            free_plan_memory(p);
+            delete p;
+        }
+    }
+    if (!best) {
+        set_error(first_error.empty() ? "autotune: no segment length fits" : first_error);
+        return first_status == FDAS_OK ? FDAS_ERR_ARG : first_status;
+    }
+    // template chunking of the chosen length
+    const int base = best->n_zchunk;
+    int best_c = base;
+    for (int c : {1, 2, 3, 4, 6, 8, 12, 16}) {
+        if (c == base || c > best->n_z || (int64_t)best->n_seg * c > best->partials_cap) continue;
+        best->n_zchunk = c;
+        double ms = 0.0;
+        if (time_correlation(*best, ms) == FDAS_OK && ms < best_ms) {
+            best_ms = ms;
+            best_c = c;
+        }
+    }
+    best->n_zchunk = best_c;
+    best->tuned_ms = best_ms;
+    out = best;
+    return FDAS_OK;
 }
 
 }  // namespace fdas
@@ -508,6 +699,7 @@ void fdas_opts_default(fdas_opts *o) {
     o->norm_block = 2048;
     o->max_candidates = int64_t(1) << 20;
     o->autotune = 0;
+    o->use_graph = 0;
 }
 
 fdas_status fdas_plan_create(fdas_plan **out, int64_t n_samples, double tsamp, double z_max,
@@ -519,7 +711,9 @@ fdas_status fdas_plan_create(fdas_plan **out, int64_t n_samples, double tsamp, d
         fdas_opts_default(&o);
         if (opts) o = *opts;
         Plan *p = nullptr;
-        fdas_status s = create(p, n_samples, tsamp, z_max, z_step, seg_len, n_harm, &o);
+        fdas_status s = o.autotune ? create_tuned(p, n_samples, tsamp, z_max, z_step, seg_len,
+                                                  n_harm, o)
+                                   : create(p, n_samples, tsamp, z_max, z_step, seg_len, n_harm, &o);
         if (s == FDAS_OK) *out = reinterpret_cast<fdas_plan *>(p);
         return s;
     } catch (...) {
@@ -561,6 +755,9 @@ fdas_status fdas_plan_get_info(const fdas_plan *plan, fdas_plan_info *info) {
     info->threshold_sigma = p.sigma;
     for (int s = 0; s < 6; ++s) info->stage_factor[s] = p.G[s];
     info->workspace_bytes = p.ws_bytes;
+    info->z_chunks = p.n_zchunk;
+    info->use_graph = p.use_graph ? 1 : 0;
+    info->tuned_ms = p.tuned_ms;
     return FDAS_OK;
 }
 

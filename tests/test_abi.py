@@ -46,7 +46,7 @@ def test_struct_layouts(capi):
     assert ctypes.sizeof(capi.fdas_candidate) == 20
     assert ctypes.sizeof(capi.fdas_series) == 24
     assert ctypes.sizeof(capi.fdas_opts) == 48
-    assert ctypes.sizeof(capi.fdas_plan_info) == 152
+    assert ctypes.sizeof(capi.fdas_plan_info) == 168
     assert capi.CANDIDATE_DTYPE.itemsize == 20
     assert ctypes.sizeof(capi.fdas_seed) == capi.SEED_DTYPE.itemsize == 24
     assert ctypes.sizeof(capi.fdas_refined) == capi.REFINED_DTYPE.itemsize == 40
