@@ -135,6 +135,11 @@ struct Plan {
     uint32_t *rank_ids = nullptr;   // [stats_cap] trial id per rank
     fdas_candidate *out_stage = nullptr;   // [max_cands] ordered output
     float *stage = nullptr;         // [n_samples] device copy of a host series
+    float *stage2 = nullptr;        // second staging buffer (copies alternate)
+    cudaStream_t cpy = nullptr;     // host-to-device copies of host series
+    cudaEvent_t ev_copied[2] = {nullptr, nullptr};
+    cudaEvent_t ev_consumed[2] = {nullptr, nullptr};
+    cudaEvent_t ev_start = nullptr;         // orders the copy stream after the caller's
     unsigned long long *host_small = nullptr;  // pinned: {count, flags}
     float2 *gl_nodes = nullptr;     // Gauss-Legendre (u, w) on [0, 1] for P(r, z)
     fdas_seed *ref_seeds = nullptr;        // device staging of refine seeds

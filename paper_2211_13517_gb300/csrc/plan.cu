@@ -87,6 +87,13 @@ static void free_plan_memory(Plan *p) {
     cudaFree(p->flags);
     cudaFree(p->out_stage);
     cudaFree(p->stage);
+    cudaFree(p->stage2);
+    for (int b = 0; b < 2; ++b) {
+        if (p->ev_copied[b]) cudaEventDestroy(p->ev_copied[b]);
+        if (p->ev_consumed[b]) cudaEventDestroy(p->ev_consumed[b]);
+    }
+    if (p->cpy) cudaStreamDestroy(p->cpy);
+    if (p->ev_start) cudaEventDestroy(p->ev_start);
     cudaFree(p->gl_nodes);
     cudaFree(p->ref_seeds);
     cudaFree(p->ref_out);
@@ -314,6 +321,13 @@ static fdas_status create(Plan *&out, int64_t n_samples, double tsamp, double z_
     PLAN_TRY(dalloc(p, &p.flags, sizeof(unsigned int)));
     PLAN_TRY(dalloc(p, &p.out_stage, sizeof(fdas_candidate) * (size_t)p.max_cands));
     PLAN_TRY(dalloc(p, &p.stage, sizeof(float) * (size_t)p.n_samples));
+    PLAN_TRY(dalloc(p, &p.stage2, sizeof(float) * (size_t)p.n_samples));
+    PLAN_CUDA(cudaStreamCreateWithFlags(&p.cpy, cudaStreamNonBlocking));
+    PLAN_CUDA(cudaEventCreateWithFlags(&p.ev_start, cudaEventDisableTiming));
+    for (int b = 0; b < 2; ++b) {
+        PLAN_CUDA(cudaEventCreateWithFlags(&p.ev_copied[b], cudaEventDisableTiming));
+        PLAN_CUDA(cudaEventCreateWithFlags(&p.ev_consumed[b], cudaEventDisableTiming));
+    }
     PLAN_CUDA(cudaMallocHost((void **)&p.host_small, 4 * sizeof(unsigned long long)));
     PLAN_CUDA(cudaStreamCreateWithFlags(&p.aux, cudaStreamNonBlocking));
 
@@ -444,14 +458,54 @@ static fdas_status enqueue_batch(Plan &p, const fdas_series *batch, int32_t n_se
     // while tracing, every group runs on the caller's stream, so that each
     // event interval holds the kernels of one group and nothing else
     cudaStream_t hs = p.profiling ? s : p.aux;
+    // series in host memory are copied on their own stream into two
+    // alternating staging buffers, so that the copy of the next series
+    // overlaps the work on this one
+    std::vector<char> on_host(n_series);
+    int n_host = 0;
+    for (int32_t t = 0; t < n_series; ++t) n_host += on_host[t] = !is_device_ptr(batch[t].data);
+    float *stages[2] = {p.stage, p.stage2};
+    int copied = 0;   // host series queued for copy so far
+    auto queue_copy = [&](int32_t t, int slot) -> fdas_status {
+        // the slot is free once the spectrum of the series two copies back read it
+        if (copied >= 2) FDAS_CUDA_TRY(cudaStreamWaitEvent(p.cpy, p.ev_consumed[slot], 0));
+        FDAS_CUDA_TRY(cudaMemcpyAsync(stages[slot], batch[t].data,
+                                      sizeof(float) * (size_t)batch[t].n_samples,
+                                      cudaMemcpyHostToDevice, p.cpy));
+        FDAS_CUDA_TRY(cudaEventRecord(p.ev_copied[slot], p.cpy));
+        ++copied;
+        return FDAS_OK;
+    };
+    if (n_host > 0) {
+        // the copy stream starts after the work already queued on the
+        // caller's stream (and joins a graph capture of it)
+        FDAS_CUDA_TRY(cudaEventRecord(p.ev_start, s));
+        FDAS_CUDA_TRY(cudaStreamWaitEvent(p.cpy, p.ev_start, 0));
+    }
+    int host_seen = 0;
+    int32_t next_host = 0;   // next host series whose copy is not queued yet
+    auto queue_next = [&]() -> fdas_status {
+        while (next_host < n_series && !on_host[next_host]) ++next_host;
+        if (next_host < n_series) {
+            FDAS_TRY(queue_copy(next_host, copied & 1));
+            ++next_host;
+        }
+        return FDAS_OK;
+    };
+    if (n_host > 0) {
+        FDAS_TRY(queue_next());
+        FDAS_TRY(queue_next());
+    }
     for (int32_t t = 0; t < n_series; ++t) {
         const int b = t & 1;
         Plan v = batch[t].n_samples == p.n_samples ? p : plan_view(p, batch[t].n_samples);
         const float *x = batch[t].data;
-        if (!is_device_ptr(x)) {
-            FDAS_CUDA_TRY(cudaMemcpyAsync(p.stage, x, sizeof(float) * (size_t)v.n_samples,
-                                          cudaMemcpyHostToDevice, s));
-            x = p.stage;
+        int slot = -1;
+        if (on_host[t]) {
+            slot = host_seen & 1;
+            ++host_seen;
+            FDAS_CUDA_TRY(cudaStreamWaitEvent(s, p.ev_copied[slot], 0));
+            x = stages[slot];
         }
         if (v.n_r < p.n_r) {
             // a shorter series: the bins past its end must read as 0 again
@@ -461,6 +515,10 @@ static fdas_status enqueue_batch(Plan &p, const fdas_series *batch, int32_t n_se
         cudaEvent_t e0 = p.profiling ? mark(s) : nullptr;
         FDAS_TRY(launch_spectrum(v, x, spec, nullptr, s));
         cudaEvent_t e1 = p.profiling ? mark(s) : nullptr;
+        if (slot >= 0) {
+            FDAS_CUDA_TRY(cudaEventRecord(p.ev_consumed[slot], s));
+            FDAS_TRY(queue_next());
+        }
         // plane[b] and partials[b] are free once the harmonic sum of series t-2
         // is done; only the correlation writes them
         if (t >= 2) {
