@@ -23,6 +23,7 @@
 #include "fdas_internal.cuh"
 #include "fft_cta.cuh"
 #include "fft8k.cuh"
+#include "tma.cuh"
 
 namespace fdas {
 namespace {
@@ -114,28 +115,58 @@ __global__ void __launch_bounds__(L / 16, 1)
 }
 
 // The same correlation for L = 8192 with 256 threads x 32 points (fft8k.cuh):
-// two shared-memory exchanges per inverse transform instead of three.
+// two shared-memory exchanges per inverse transform instead of three.  The
+// segment window and the template spectra reach shared memory by bulk
+// asynchronous copies (cp.async.bulk + mbarrier): the spectrum of template
+// z + 1 is in flight while the inverse FFT of template z runs.  A bounded
+// wait that gives up sets bit 1 of `flags` and the CTA returns.
 template <class P>
 __global__ void __launch_bounds__(256, 1)
     correlate8k_kernel(const typename P::cpx *__restrict__ spec_pad,
                        const typename P::cpx *__restrict__ bank, typename P::real *__restrict__ plane,
                        double2 *__restrict__ partials, int64_t n_r, int n_z, int V, int m_ov,
-                       int z_per_cta, float bank_scale) {
+                       int z_per_cta, float bank_scale, unsigned int *__restrict__ flags) {
     using Fw = Fft8k<-1>;
     using Iv = Fft8k<+1>;
+    using cpx = typename P::cpx;
     constexpr int L = 8192;
-    extern __shared__ float2 buf[];
+    constexpr unsigned kBytes = L * sizeof(cpx);
+    extern __shared__ __align__(16) float2 buf[];
+    cpx *const hb0 = reinterpret_cast<cpx *>(buf + Fw::SMEM_ELEMS);   // two template slots
+    cpx *const hb1 = hb0 + L;
+    __shared__ __align__(8) uint64_t bars[3];   // segment, template slot 0, slot 1
     __shared__ double red[2][8];
     const int t = threadIdx.x;
     const int64_t seg0 = (int64_t)blockIdx.x * V;
     const int iz_begin = blockIdx.y * z_per_cta;
     const int iz_end = min(n_z, iz_begin + z_per_cta);
 
+    if (t == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_init(&bars[2], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (t == 0) {
+        mbar_arrive_expect_tx(&bars[0], kBytes);
+        bulk_copy_g2s(hb1, spec_pad + seg0, kBytes, &bars[0]);
+        if (iz_begin < iz_end) {
+            mbar_arrive_expect_tx(&bars[1], kBytes);
+            bulk_copy_g2s(hb0, bank + (int64_t)iz_begin * L, kBytes, &bars[1]);
+        }
+    }
+    bool ok = mbar_wait(&bars[0], 0);
+    if (__syncthreads_or(!ok)) {
+        if (t == 0) atomicOr(flags, 2u);
+        return;
+    }
+
     float2 v[32], S[32], o[32], w1, w2;
 #pragma unroll
     for (int b = 0; b < 2; ++b)
 #pragma unroll
-        for (int r = 0; r < 16; ++r) v[16 * b + r] = P::ld(spec_pad[seg0 + t + 256 * b + 512 * r]);
+        for (int r = 0; r < 16; ++r) v[16 * b + r] = P::ld(hb1[t + 256 * b + 512 * r]);
     Fw::make_twiddles(t, w1, w2);
     Fw::pass0(v, buf, t);
     __syncthreads();
@@ -151,6 +182,13 @@ __global__ void __launch_bounds__(256, 1)
         for (int r = 0; r < 16; ++r)
             S[16 * b + r] = cscale(buf[fft_pad(t + 256 * b + 512 * r)], bank_scale);
     Iv::make_twiddles(t, w1, w2);
+    // the segment copy in slot 1 has been read by every thread: refill it with
+    // the second template
+    if (t == 0 && iz_begin + 1 < iz_end) {
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&bars[2], kBytes);
+        bulk_copy_g2s(hb1, bank + (int64_t)(iz_begin + 1) * L, kBytes, &bars[2]);
+    }
     // CTA-uniform: every output but r = 0 and r = 31 is kept, and those two
     // by a per-thread test, unless the overlap is wide or this is the last
     // segment (then every output is tested)
@@ -159,16 +197,31 @@ __global__ void __launch_bounds__(256, 1)
     const bool keep31 = t + 256 * 31 < m_ov + V;
 
     Kahan sp, sq;
-    for (int iz = iz_begin; iz < iz_end; ++iz) {
+    unsigned phase0 = 0u, phase1 = 0u;   // next phase of each template slot
+    for (int iz = iz_begin, k = 0; iz < iz_end; ++iz, ++k) {
+        const int slot = k & 1;
         __syncthreads();   // the previous pass 2 has read buf
-        const typename P::cpx *h = bank + (int64_t)iz * L;
+        ok = mbar_wait(&bars[1 + slot], slot ? phase1 : phase0);
+        if (__syncthreads_or(!ok)) {
+            if (t == 0) atomicOr(flags, 2u);
+            return;
+        }
+        if (slot) phase1 ^= 1u;
+        else phase0 ^= 1u;
+        const cpx *h = hb0 + slot * L;
 #pragma unroll
         for (int b = 0; b < 2; ++b)
 #pragma unroll
             for (int r = 0; r < 16; ++r)
-                v[16 * b + r] = cmul(S[16 * b + r], P::ld(__ldg(h + t + 256 * b + 512 * r)));
+                v[16 * b + r] = cmul(S[16 * b + r], P::ld(h[t + 256 * b + 512 * r]));
         Iv::pass0(v, buf, t);
         __syncthreads();
+        // every thread has read template iz: its slot takes template iz + 2
+        if (t == 0 && iz + 2 < iz_end) {
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&bars[1 + slot], kBytes);
+            bulk_copy_g2s(hb0 + slot * L, bank + (int64_t)(iz + 2) * L, kBytes, &bars[1 + slot]);
+        }
         Iv::pass1(buf, t, w1);
         Iv::pass2(buf, t, w2, o);
         typename P::real *row = plane + (seg0 - m_ov) + (int64_t)iz * n_r + t;
@@ -224,7 +277,7 @@ __global__ void __launch_bounds__(256, 1)
 template <class P>
 fdas_status launch_8k(Plan &p, const void *spec_padded, void *plane, double2 *partials,
                       cudaStream_t s) {
-    const size_t smem = sizeof(float2) * Fft8k<1>::SMEM_ELEMS;
+    const size_t smem = sizeof(float2) * Fft8k<1>::SMEM_ELEMS + 2 * 8192 * sizeof(typename P::cpx);
     auto k = correlate8k_kernel<P>;
     FDAS_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int zper = (p.n_z + p.n_zchunk - 1) / p.n_zchunk;
@@ -232,7 +285,7 @@ fdas_status launch_8k(Plan &p, const void *spec_padded, void *plane, double2 *pa
     const float bank_scale = P::id == FDAS_FP16 ? 1.0f / (float)p.L : 1.0f;
     k<<<grid, 256, smem, s>>>((const typename P::cpx *)spec_padded, (const typename P::cpx *)p.bank,
                               (typename P::real *)plane, partials, p.n_r, p.n_z, p.V, p.m_ov, zper,
-                              bank_scale);
+                              bank_scale, p.flags);
     FDAS_CUDA_TRY(cudaGetLastError());
     return FDAS_OK;
 }

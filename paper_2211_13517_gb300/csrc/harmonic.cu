@@ -15,6 +15,7 @@
 // (trial rank, stage, iz, ir), so the list does not depend on scheduling.
 #include "fdas_internal.cuh"
 #include "fft_cta.cuh"   // cadd
+#include "tma.cuh"
 
 #include <cstring>
 
@@ -235,7 +236,8 @@ __global__ void __launch_bounds__(kHsThreads)
 // j (B + 16 t)/H, and which of them each cell adds is a compile-time index.
 // The CTA first copies, for every harmonic, the span of its source row that
 // all its threads need (starting at j B / H, a multiple of 256, so 16-byte
-// aligned) into shared memory with 16-byte cp.async copies, then each thread
+// aligned) into shared memory with one bulk asynchronous copy per harmonic
+// (cp.async.bulk completing on an mbarrier, bounded wait), then each thread
 // reads its values with the widest aligned shared-memory loads and adds them
 // to its cells, in stage order, comparing each stage with its threshold.
 // ---------------------------------------------------------------------------
@@ -292,19 +294,31 @@ struct DedupSteps {
     using D = Dedup<P, H>;
     using real = typename P::real;
 
-    // stage the spans of all harmonics (compile-time loop over j)
+    // bytes of the span of harmonic J: from j B / H (16-byte aligned) up to
+    // the last bin of the row the CTA's cells can read, rounded up to 16 bytes
+    template <int J>
+    __device__ __forceinline__ static unsigned span_bytes(int64_t n_r, int64_t B) {
+        const int64_t c0 = (int64_t)J * B / H;
+        const int64_t maxsrc = ((n_r - 1) * J + H / 2) / H;
+        if (maxsrc < c0) return 0u;
+        int64_t n = (maxsrc - c0 + 1 + D::EPV - 1) / D::EPV * D::EPV;
+        if (n > D::padlen(J)) n = D::padlen(J);
+        return (unsigned)(n * (int64_t)sizeof(real));
+    }
+    template <int J>
+    __device__ __forceinline__ static unsigned total_bytes(int64_t n_r, int64_t B) {
+        if constexpr (J <= H) return span_bytes<J>(n_r, B) + total_bytes<J + 1>(n_r, B);
+        else return 0u;
+    }
+    // one thread: bulk-copy the span of every harmonic into shared memory
     template <int J>
     __device__ __forceinline__ static void copy(const real *__restrict__ plane, const int64_t *rowoff,
-                                                int64_t n_r, int64_t B, real *sm) {
+                                                int64_t n_r, int64_t B, real *sm, uint64_t *bar) {
         if constexpr (J <= H) {
-            constexpr int NV = D::padlen(J) / D::EPV;
-            const int64_t c0 = (int64_t)J * B / H;
-            const int64_t maxsrc = ((n_r - 1) * J + H / 2) / H;
-            const real *g = plane + rowoff[J - 1] + c0;
-            real *d = sm + D::off(J);
-            for (int v = threadIdx.x; v < NV; v += D::T)
-                if (c0 + (int64_t)v * D::EPV <= maxsrc) cp_async16(d + v * D::EPV, g + v * D::EPV);
-            copy<J + 1>(plane, rowoff, n_r, B, sm);
+            const unsigned bytes = span_bytes<J>(n_r, B);
+            if (bytes)
+                bulk_copy_g2s(sm + D::off(J), plane + rowoff[J - 1] + (int64_t)J * B / H, bytes, bar);
+            copy<J + 1>(plane, rowoff, n_r, B, sm, bar);
         }
     }
 
@@ -338,19 +352,31 @@ __global__ void __launch_bounds__(Dedup<P, H>::T)
     harmonic_dedup_kernel(const typename P::real *__restrict__ plane, int64_t n_r, int n_z,
                           int iz0, const TrialStats *__restrict__ st, uint32_t rank,
                           CandRec *__restrict__ cand, unsigned long long *__restrict__ count,
-                          int64_t cap, float *__restrict__ sums_out) {
+                          int64_t cap, float *__restrict__ sums_out,
+                          unsigned int *__restrict__ flags) {
     using D = Dedup<P, H>;
     using real = typename P::real;
     extern __shared__ __align__(16) unsigned char dd_smem[];
     real *sm = reinterpret_cast<real *>(dd_smem);
     __shared__ int64_t rowoff[H];
+    __shared__ __align__(8) uint64_t bar;
     const int iz = blockIdx.y;
     const int64_t B = (int64_t)blockIdx.x * D::CELLS;
     const int t = threadIdx.x;
-    hs_row_offsets<H>(iz0, iz, n_r, rowoff);
-    DedupSteps<P, H>::template copy<1>(plane, rowoff, n_r, B, sm);
-    cp_async_wait_all_();
-    __syncthreads();
+    if (t == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+    }
+    hs_row_offsets<H>(iz0, iz, n_r, rowoff);   // ends with __syncthreads
+    if (t == 0) {
+        mbar_arrive_expect_tx(&bar, DedupSteps<P, H>::template total_bytes<1>(n_r, B));
+        DedupSteps<P, H>::template copy<1>(plane, rowoff, n_r, B, sm, &bar);
+    }
+    const bool ok = mbar_wait(&bar, 0);
+    if (__syncthreads_or(!ok)) {
+        if (t == 0) atomicOr(flags, 2u);
+        return;
+    }
     const int64_t b = B + (int64_t)D::R * t;   // first cell of this thread
     if (b >= n_r) return;
     const float inv = 1.0f / P::plane_scale;
@@ -527,7 +553,7 @@ fdas_status launch_dedup(Plan &p, const void *plane, const TrialStats *st, uint3
     FDAS_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((unsigned)((p.n_r + D::CELLS - 1) / D::CELLS), p.n_z);
     k<<<grid, D::T, smem, s>>>((const typename P::real *)plane, p.n_r, p.n_z, p.iz0, st, rank,
-                               p.cand, p.cand_count, p.max_cands, sums_out);
+                               p.cand, p.cand_count, p.max_cands, sums_out, p.flags);
     FDAS_CUDA_TRY(cudaGetLastError());
     return FDAS_OK;
 }

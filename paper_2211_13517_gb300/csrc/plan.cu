@@ -369,6 +369,11 @@ static fdas_status collect(Plan &p, fdas_candidate *cands, int64_t capacity, int
     FDAS_CUDA_TRY(cudaStreamSynchronize(s));
     const int64_t total = (int64_t)p.host_small[0];
     const unsigned int flags = (unsigned int)(p.host_small[1] & 0xffffffffu);
+    if (flags & 2u) {
+        *n_found = 0;
+        set_error("a bounded wait for an asynchronous copy gave up");
+        return FDAS_ERR_TIMEOUT;
+    }
     if (flags & 1u) {
         *n_found = 0;
         set_error("non-finite values in an input series");
