@@ -58,6 +58,25 @@ struct PrecBF16 {
     __device__ __forceinline__ static cpx st(float2 v) { return __float22bfloat162_rn(v); }
     __device__ __forceinline__ static float ldr(real v) { return __bfloat162float(v); }
     __device__ __forceinline__ static real str(float v) { return __float2bfloat16_rn(v); }
+    // s + (value stored in the low / high half of w, or in h), one FP32
+    // rounding: the mixed-precision add converts the 16-bit operand exactly
+    __device__ __forceinline__ static float acc_lo(float s, uint32_t w) {
+        float d;
+        asm("{\n .reg .b16 l, u;\n mov.b32 {l, u}, %1;\n add.rn.f32.bf16 %0, l, %2;\n}\n"
+            : "=f"(d) : "r"(w), "f"(s));
+        return d;
+    }
+    __device__ __forceinline__ static float acc_hi(float s, uint32_t w) {
+        float d;
+        asm("{\n .reg .b16 l, u;\n mov.b32 {l, u}, %1;\n add.rn.f32.bf16 %0, u, %2;\n}\n"
+            : "=f"(d) : "r"(w), "f"(s));
+        return d;
+    }
+    __device__ __forceinline__ static float acc16(float s, unsigned short h) {
+        float d;
+        asm("add.rn.f32.bf16 %0, %1, %2;\n" : "=f"(d) : "h"(h), "f"(s));
+        return d;
+    }
 };
 
 struct PrecF16 {
@@ -69,6 +88,23 @@ struct PrecF16 {
     __device__ __forceinline__ static cpx st(float2 v) { return __float22half2_rn(v); }
     __device__ __forceinline__ static float ldr(real v) { return __half2float(v); }
     __device__ __forceinline__ static real str(float v) { return __float2half_rn(v); }
+    __device__ __forceinline__ static float acc_lo(float s, uint32_t w) {
+        float d;
+        asm("{\n .reg .b16 l, u;\n mov.b32 {l, u}, %1;\n add.rn.f32.f16 %0, l, %2;\n}\n"
+            : "=f"(d) : "r"(w), "f"(s));
+        return d;
+    }
+    __device__ __forceinline__ static float acc_hi(float s, uint32_t w) {
+        float d;
+        asm("{\n .reg .b16 l, u;\n mov.b32 {l, u}, %1;\n add.rn.f32.f16 %0, u, %2;\n}\n"
+            : "=f"(d) : "r"(w), "f"(s));
+        return d;
+    }
+    __device__ __forceinline__ static float acc16(float s, unsigned short h) {
+        float d;
+        asm("add.rn.f32.f16 %0, %1, %2;\n" : "=f"(d) : "h"(h), "f"(s));
+        return d;
+    }
 };
 
 inline size_t cpx_bytes(int prec) { return prec == FDAS_FP32 ? 8 : 4; }

@@ -333,13 +333,44 @@ struct DedupSteps {
             constexpr int W = D::width(J);
             constexpr int NLD = (NVAL + W - 1) / W;
             const real *p = sm + D::off(J) + (D::R / H) * J * t;
-            float val[NLD * W];
+            if constexpr (sizeof(real) == 2) {
+                // 16-bit values: keep them packed as loaded and add each to
+                // its cell with one mixed-precision add (no conversions)
+                if constexpr (W == 1) {
+                    unsigned short h[NLD];
 #pragma unroll
-            for (int k = 0; k < NLD; ++k) VecLoad<P, W>::run(p + k * W, val + k * W);
+                    for (int k = 0; k < NLD; ++k) h[k] = reinterpret_cast<const unsigned short *>(p)[k];
 #pragma unroll
-            for (int c = 0; c < D::R / 2; ++c) {
-                const int d0 = ((2 * c) * J + H / 2) / H, d1 = ((2 * c + 1) * J + H / 2) / H;
-                S2[c] = cadd(S2[c], make_float2(val[d0], val[d1]));
+                    for (int i = 0; i < D::R; ++i) {
+                        const int d = (i * J + H / 2) / H;
+                        float &s = (i & 1) ? S2[i / 2].y : S2[i / 2].x;
+                        s = P::acc16(s, h[d]);
+                    }
+                } else {
+                    constexpr int WPL = W / 2;                 // 32-bit words per load
+                    using V = typename RawVec<W * 2>::type;
+                    uint32_t w[NLD * WPL];
+#pragma unroll
+                    for (int k = 0; k < NLD; ++k) {
+                        const V u = reinterpret_cast<const V *>(p)[k];
+                        memcpy(w + k * WPL, &u, sizeof(u));
+                    }
+#pragma unroll
+                    for (int i = 0; i < D::R; ++i) {
+                        const int d = (i * J + H / 2) / H;
+                        float &s = (i & 1) ? S2[i / 2].y : S2[i / 2].x;
+                        s = (d & 1) ? P::acc_hi(s, w[d / 2]) : P::acc_lo(s, w[d / 2]);
+                    }
+                }
+            } else {
+                float val[NLD * W];
+#pragma unroll
+                for (int k = 0; k < NLD; ++k) VecLoad<P, W>::run(p + k * W, val + k * W);
+#pragma unroll
+                for (int c = 0; c < D::R / 2; ++c) {
+                    const int d0 = ((2 * c) * J + H / 2) / H, d1 = ((2 * c + 1) * J + H / 2) / H;
+                    S2[c] = cadd(S2[c], make_float2(val[d0], val[d1]));
+                }
             }
             if constexpr (((IDX + 1) & IDX) == 0) stage(ilog2h(IDX + 1), S2);
             sums<IDX + 1>(sm, t, S2, stage);
