@@ -257,7 +257,7 @@ def run_gpu(args, rank, world, local_rank, dist):
     import torch
 
     import paper_2211_13517_gb300 as pkg
-    from paper_2211_13517_gb300 import capi
+    from paper_2211_13517_gb300 import capi, shard
     import synthetic as S
 
     pkg.build()
@@ -265,7 +265,10 @@ def run_gpu(args, rank, world, local_rank, dist):
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream()
 
-    xs, _ = S.torch_batch_series(args.batch, N_SAMPLES, base_seed=1000 + rank * args.batch,
+    # this rank's block of the job's DM trials, numbered globally
+    t_start, t_stop = shard.trial_block(args.batch * world, rank, world)
+    ids = list(range(t_start, t_stop))
+    xs, _ = S.torch_batch_series(t_stop - t_start, N_SAMPLES, base_seed=1000 + t_start,
                                  device=dev)
     torch.cuda.synchronize()
     peak_hbm, peak_src = _peaks()
@@ -276,11 +279,7 @@ def run_gpu(args, rank, world, local_rank, dist):
         torch.cuda.synchronize()
 
     def max_over_ranks(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return shard.max_over_ranks(v, dist, dev)
 
     def timed_stream(plan, inputs, steps, warmup, stream):
         with torch.cuda.stream(stream):
@@ -298,7 +297,7 @@ def run_gpu(args, rank, world, local_rank, dist):
 
     def timed(plan, inputs, steps, warmup, profile=False, energy=None, clocks=None):
         for _ in range(warmup):
-            plan.search(inputs, capacity=1 << 16)
+            plan.search(inputs, trial_ids=ids, capacity=1 << 16)
         if profile:
             plan.profile(True)
         barrier()
@@ -310,7 +309,7 @@ def run_gpu(args, rank, world, local_rank, dist):
         ev0.record(stream)
         nfound = 0
         for _ in range(steps):
-            st, c, nf = plan.search(inputs, capacity=1 << 16)
+            st, c, nf = plan.search(inputs, trial_ids=ids, capacity=1 << 16)
             nfound += nf
         ev1.record(stream)
         barrier()
@@ -348,7 +347,7 @@ def run_gpu(args, rank, world, local_rank, dist):
     if not args.no_uneven:
         uneven = run_uneven(args, dev, capi, S, timed_uneven=timed_stream)
     trials = args.batch * args.steps * world
-    value = trials / (ms_bf16 / 1000.0)
+    value = shard.weak_scaling_throughput(args.batch * args.steps, world, ms_bf16)
     if rank != 0:
         return
     wm = work_model(info, 2)
