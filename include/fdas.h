@@ -55,6 +55,14 @@ enum { FDAS_FP32 = 0, FDAS_BF16 = 1, FDAS_FP16 = 2 };
 enum { FDAS_THRESH_GAMMA_TAIL = 0, FDAS_THRESH_MEAN_PLUS_KSIGMA = 1 };
 /* spectral normalisation */
 enum { FDAS_NORM_MEDIAN = 0, FDAS_NORM_NONE = 1 };
+/* how the power plane is computed (the same P(r, z) either way):
+ * FDAS_CORR_FFT: overlap-save, segment FFT x template spectrum, inverse FFT
+ *   (FP32 arithmetic on the CUDA cores; every precision);
+ * FDAS_CORR_TENSOR: the direct correlation sum_e g_z[e] X'_{r-e} as a GEMM
+ *   on the tensor cores (16-bit operands, FP32 accumulation; FDAS_BF16 and
+ *   FDAS_FP16 only, n_samples >= 2^10 and m(z_max) <= 104);
+ * FDAS_CORR_AUTO: TENSOR where it applies, else FFT. */
+enum { FDAS_CORR_AUTO = 0, FDAS_CORR_FFT = 1, FDAS_CORR_TENSOR = 2 };
 
 typedef struct {
     int32_t precision;       /* FDAS_FP32 (default), FDAS_BF16, FDAS_FP16          */
@@ -69,6 +77,9 @@ typedef struct {
     int32_t use_graph;       /* 1: fdas_search captures each batch's launches into
                                 one CUDA graph and replays it (device or pinned
                                 series, a non-default stream); 0 (default): direct */
+    int32_t correlator;      /* FDAS_CORR_AUTO (default), _FFT or _TENSOR; asking
+                                for _TENSOR where it does not apply is FDAS_ERR_ARG */
+    int32_t reserved;        /* 0 */
 } fdas_opts;
 
 /* One dedispersed time series (one DM trial).  `data` points to n_samples
@@ -108,6 +119,8 @@ typedef struct {
     int32_t z_chunks;         /* template chunks per segment in the correlation */
     int32_t use_graph;
     double tuned_ms;          /* autotune: correlation time per series (ms), else 0 */
+    int32_t correlator;       /* FDAS_CORR_FFT or FDAS_CORR_TENSOR, as built    */
+    int32_t reserved;
 } fdas_plan_info;
 
 typedef struct fdas_plan fdas_plan;
@@ -360,6 +373,20 @@ fdas_status fdas_profile_enable(fdas_plan *plan, int32_t on);
 
 /* Copy the counters into *out (host). */
 fdas_status fdas_profile_read(const fdas_plan *plan, fdas_profile *out);
+
+/* ---------------------------------------------------------------------
+ * Failure-path check for the bounded device waits (no counterpart in the
+ * paper).  Every kernel that waits for an asynchronous copy (an mbarrier
+ * phase) gives up after a bounded number of clock cycles, records the fact
+ * in the plan's flag word and returns; the call that launched it then
+ * returns FDAS_ERR_TIMEOUT and the plan stays usable.  This call exercises
+ * that path without any fault: one CTA arms a barrier for 16 bytes that no
+ * copy delivers and waits at most `limit_cycles` SM clock cycles
+ * (1 <= limit_cycles <= 2e9, else FDAS_ERR_ARG).  Blocking.  Returns
+ * FDAS_ERR_TIMEOUT when the wait gave up (the expected outcome), FDAS_OK if
+ * it did not, FDAS_ERR_CUDA on a CUDA error.
+ */
+fdas_status fdas_selftest_wait_timeout(fdas_plan *plan, int64_t limit_cycles, void *stream);
 
 /* Thread-local message describing the last failed call ("" if none). */
 const char *fdas_last_error(void);

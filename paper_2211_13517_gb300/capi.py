@@ -35,20 +35,22 @@ STATUS_NAMES = {0: "FDAS_OK", 1: "FDAS_ERR_ARG", 2: "FDAS_ERR_CUDA", 3: "FDAS_ER
 FDAS_FP32, FDAS_BF16, FDAS_FP16 = 0, 1, 2
 FDAS_THRESH_GAMMA_TAIL, FDAS_THRESH_MEAN_PLUS_KSIGMA = 0, 1
 FDAS_NORM_MEDIAN, FDAS_NORM_NONE = 0, 1
+FDAS_CORR_AUTO, FDAS_CORR_FFT, FDAS_CORR_TENSOR = 0, 1, 2
 
 EXPORTED = ["fdas_opts_default", "fdas_plan_create", "fdas_plan_destroy",
             "fdas_plan_get_info", "fdas_search", "fdas_spectrum", "fdas_power_plane",
             "fdas_harmonic_sums", "fdas_threshold", "fdas_template_bank",
             "fdas_spectrum_static", "fdas_fourier_power", "fdas_fourier_power_backward",
             "fdas_refine", "fdas_profile_enable", "fdas_profile_read",
-            "fdas_last_error", "fdas_version"]
+            "fdas_selftest_wait_timeout", "fdas_last_error", "fdas_version"]
 
 
 class fdas_opts(Structure):
     _fields_ = [("precision", c_int32), ("threshold_sigma", c_double),
                 ("threshold_mode", c_int32), ("norm_mode", c_int32),
                 ("norm_block", c_int32), ("max_candidates", c_int64),
-                ("autotune", c_int32), ("use_graph", c_int32)]
+                ("autotune", c_int32), ("use_graph", c_int32),
+                ("correlator", c_int32), ("reserved", c_int32)]
 
 
 class fdas_series(Structure):
@@ -74,7 +76,7 @@ class fdas_plan_info(Structure):
                 ("tsamp", c_double), ("z_max", c_double), ("z_step", c_double),
                 ("threshold_sigma", c_double), ("stage_factor", c_double * 6),
                 ("workspace_bytes", c_int64), ("z_chunks", c_int32), ("use_graph", c_int32),
-                ("tuned_ms", c_double)]
+                ("tuned_ms", c_double), ("correlator", c_int32), ("reserved", c_int32)]
 
 
 class fdas_seed(Structure):
@@ -154,6 +156,8 @@ def lib() -> ctypes.CDLL:
         L.fdas_refine.argtypes = [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_void_p,
                                   c_void_p]
         L.fdas_refine.restype = c_int32
+        L.fdas_selftest_wait_timeout.argtypes = [c_void_p, c_int64, c_void_p]
+        L.fdas_selftest_wait_timeout.restype = c_int32
         L.fdas_profile_enable.argtypes = [c_void_p, c_int32]
         L.fdas_profile_enable.restype = c_int32
         L.fdas_profile_read.argtypes = [c_void_p, POINTER(fdas_profile)]
@@ -256,6 +260,14 @@ def fdas_refine(plan, spectrum_ptr, seeds_ptr, n, n_steps, out_ptr, stream=None)
            "fdas_refine")
 
 
+def fdas_selftest_wait_timeout(plan, limit_cycles, stream=None) -> int:
+    """Status of the bounded-wait check: FDAS_ERR_TIMEOUT when the wait gave
+    up as it should (returned, not raised), FDAS_OK if it did not."""
+    st = lib().fdas_selftest_wait_timeout(plan, limit_cycles, stream)
+    _check(st, "fdas_selftest_wait_timeout", allow=(FDAS_ERR_TIMEOUT,))
+    return st
+
+
 def fdas_profile_enable(plan, on: bool) -> None:
     _check(lib().fdas_profile_enable(plan, 1 if on else 0), "fdas_profile_enable")
 
@@ -290,7 +302,8 @@ class Plan:
     def __init__(self, n_samples, tsamp=64e-6, z_max=96.0, z_step=1.0, seg_len=8192,
                  n_harm=16, precision=FDAS_FP32, threshold_sigma=6.0,
                  threshold_mode=FDAS_THRESH_GAMMA_TAIL, norm_mode=FDAS_NORM_MEDIAN,
-                 norm_block=2048, max_candidates=1 << 20, autotune=False, use_graph=False):
+                 norm_block=2048, max_candidates=1 << 20, autotune=False, use_graph=False,
+                 correlator=None):
         o = fdas_opts_default()
         o.precision = precision
         o.threshold_sigma = threshold_sigma
@@ -300,6 +313,8 @@ class Plan:
         o.max_candidates = max_candidates
         o.autotune = 1 if autotune else 0
         o.use_graph = 1 if use_graph else 0
+        if correlator is not None:
+            o.correlator = correlator
         self.handle = fdas_plan_create(n_samples, tsamp, z_max, z_step, seg_len, n_harm, o)
         self.info = fdas_plan_get_info(self.handle)
 

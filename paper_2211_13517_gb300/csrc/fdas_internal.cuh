@@ -211,6 +211,7 @@ fdas_status launch_harmonic_threshold(Plan &p, const void *plane,
                                       cudaStream_t s);
 fdas_status launch_harmonic_sums(Plan &p, const void *plane, float *out,
                                  cudaStream_t s);
+fdas_status launch_stuck_wait(unsigned int *flags, long long limit_cycles, cudaStream_t s);
 fdas_status launch_candidates_finish(Plan &p, int64_t n, fdas_candidate *out_dev,
                                      cudaStream_t s);
 std::vector<float2> gauss_legendre_01(int n);

@@ -234,18 +234,22 @@ __global__ void __launch_bounds__(kHsThreads)
 //     j (B + 16 t)/H + d_i,   d_i = floor((i j + H/2)/H) <= DMAX_j,
 // so the thread needs only the DMAX_j + 1 consecutive bins starting at
 // j (B + 16 t)/H, and which of them each cell adds is a compile-time index.
-// The CTA first copies, for every harmonic, the span of its source row that
-// all its threads need (starting at j B / H, a multiple of 256, so 16-byte
-// aligned) into shared memory with one bulk asynchronous copy per harmonic
-// (cp.async.bulk completing on an mbarrier, bounded wait), then each thread
-// reads its values with the widest aligned shared-memory loads and adds them
-// to its cells, in stage order, comparing each stage with its threshold.
+// The CTA (T = 128 threads, 2048 cells) copies, for every harmonic, the span
+// of its source row that all its threads need (starting at j B / H, a
+// multiple of 128 elements, so 16-byte aligned) into shared memory with one
+// bulk asynchronous copy per harmonic; the copies of each stage complete on
+// that stage's own mbarrier (bounded waits), so the sums of the first stages
+// run while the later spans are still arriving.  Each thread reads its
+// values with the widest aligned shared-memory loads and adds them to its
+// cells, in stage order, comparing each stage with its threshold.  Small
+// CTAs (about 35 KB of BF16 spans) keep six of them per SM in different
+// phases of copy and compute.
 // ---------------------------------------------------------------------------
 template <class P, int H>
 struct Dedup {
     using real = typename P::real;
     static constexpr int R = 16;                                  // cells per thread
-    static constexpr int T = sizeof(real) == 2 ? 256 : 128;      // threads per CTA
+    static constexpr int T = 128;                                 // threads per CTA
     static constexpr int CELLS = T * R;
     static constexpr int EPV = 16 / (int)sizeof(real);
     static constexpr int dmax(int j) { return ((R - 1) * j + H / 2) / H; }
@@ -305,30 +309,48 @@ struct DedupSteps {
         if (n > D::padlen(J)) n = D::padlen(J);
         return (unsigned)(n * (int64_t)sizeof(real));
     }
-    template <int J>
-    __device__ __forceinline__ static unsigned total_bytes(int64_t n_r, int64_t B) {
-        if constexpr (J <= H) return span_bytes<J>(n_r, B) + total_bytes<J + 1>(n_r, B);
-        else return 0u;
+    // harmonics are consumed in stage order j_at(H, 0), j_at(H, 1), ...; the
+    // harmonics of stage g (indices [2^(g-1), 2^g), index 0 for g = 0) are
+    // copied on barrier g, so the sums of a stage start as soon as its own
+    // spans have landed while the later ones are still in flight
+    static constexpr int NG = ilog2h(H) + 1;
+    static constexpr int group_of(int idx) { return idx == 0 ? 0 : ilog2h(idx) + 1; }
+    template <int IDX, int G>
+    __device__ __forceinline__ static unsigned group_bytes(int64_t n_r, int64_t B) {
+        if constexpr (IDX < H) {
+            const unsigned own = group_of(IDX) == G ? span_bytes<j_at(H, IDX)>(n_r, B) : 0u;
+            return own + group_bytes<IDX + 1, G>(n_r, B);
+        } else {
+            return 0u;
+        }
     }
-    // one thread: bulk-copy the span of every harmonic into shared memory
-    template <int J>
+    // one thread: arm each stage's barrier with its byte count and issue the
+    // bulk copies of its harmonic spans
+    template <int IDX>
     __device__ __forceinline__ static void copy(const real *__restrict__ plane, const int64_t *rowoff,
-                                                int64_t n_r, int64_t B, real *sm, uint64_t *bar) {
-        if constexpr (J <= H) {
+                                                int64_t n_r, int64_t B, real *sm, uint64_t *bars) {
+        if constexpr (IDX < H) {
+            constexpr int J = j_at(H, IDX);
+            constexpr int G = group_of(IDX);
+            if constexpr (IDX == 0 || (IDX & (IDX - 1)) == 0)
+                mbar_arrive_expect_tx(&bars[G], group_bytes<0, G>(n_r, B));
             const unsigned bytes = span_bytes<J>(n_r, B);
             if (bytes)
-                bulk_copy_g2s(sm + D::off(J), plane + rowoff[J - 1] + (int64_t)J * B / H, bytes, bar);
-            copy<J + 1>(plane, rowoff, n_r, B, sm, bar);
+                bulk_copy_g2s(sm + D::off(J), plane + rowoff[J - 1] + (int64_t)J * B / H, bytes,
+                              &bars[G]);
+            copy<IDX + 1>(plane, rowoff, n_r, B, sm, bars);
         }
     }
 
     // add harmonic j_at(H, IDX) to the thread's cells; stage(s, S) at the end
-    // of every stage
+    // of every stage.  False if a stage's copies did not land in time.
     template <int IDX, class F>
-    __device__ __forceinline__ static void sums(const real *sm, int t, float2 (&S2)[D::R / 2],
-                                                F &&stage) {
+    __device__ __forceinline__ static bool sums(const real *sm, uint64_t *bars, int t,
+                                                float2 (&S2)[D::R / 2], F &&stage) {
         if constexpr (IDX < H) {
             constexpr int J = j_at(H, IDX);
+            if constexpr (IDX == 0 || (IDX & (IDX - 1)) == 0)
+                if (!mbar_wait(&bars[group_of(IDX)], 0)) return false;
             constexpr int NVAL = D::dmax(J) + 1;
             constexpr int W = D::width(J);
             constexpr int NLD = (NVAL + W - 1) / W;
@@ -373,7 +395,9 @@ struct DedupSteps {
                 }
             }
             if constexpr (((IDX + 1) & IDX) == 0) stage(ilog2h(IDX + 1), S2);
-            sums<IDX + 1>(sm, t, S2, stage);
+            return sums<IDX + 1>(sm, bars, t, S2, stage);
+        } else {
+            return true;
         }
     }
 };
@@ -389,32 +413,27 @@ __global__ void __launch_bounds__(Dedup<P, H>::T)
     using real = typename P::real;
     extern __shared__ __align__(16) unsigned char dd_smem[];
     real *sm = reinterpret_cast<real *>(dd_smem);
+    using Steps = DedupSteps<P, H>;
     __shared__ int64_t rowoff[H];
-    __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(8) uint64_t bars[Steps::NG];
     const int iz = blockIdx.y;
     const int64_t B = (int64_t)blockIdx.x * D::CELLS;
     const int t = threadIdx.x;
     if (t == 0) {
-        mbar_init(&bar, 1);
+        for (int g = 0; g < Steps::NG; ++g) mbar_init(&bars[g], 1);
         mbar_fence_init();
     }
     hs_row_offsets<H>(iz0, iz, n_r, rowoff);   // ends with __syncthreads
-    if (t == 0) {
-        mbar_arrive_expect_tx(&bar, DedupSteps<P, H>::template total_bytes<1>(n_r, B));
-        DedupSteps<P, H>::template copy<1>(plane, rowoff, n_r, B, sm, &bar);
-    }
-    const bool ok = mbar_wait(&bar, 0);
-    if (__syncthreads_or(!ok)) {
-        if (t == 0) atomicOr(flags, 2u);
-        return;
-    }
+    if (t == 0) Steps::template copy<0>(plane, rowoff, n_r, B, sm, bars);
+    // Thread 0 (cell B < n_r) waits for every stage's copies before it
+    // exits, so the CTA's shared memory outlives all copies into it.
     const int64_t b = B + (int64_t)D::R * t;   // first cell of this thread
     if (b >= n_r) return;
     const float inv = 1.0f / P::plane_scale;
     float2 S2[D::R / 2];
 #pragma unroll
     for (int c = 0; c < D::R / 2; ++c) S2[c] = make_float2(0.f, 0.f);
-    DedupSteps<P, H>::template sums<0>(sm, t, S2, [&](int s, float2 (&Sv)[D::R / 2]) {
+    const bool ok = Steps::template sums<0>(sm, bars, t, S2, [&](int s, float2 (&Sv)[D::R / 2]) {
         if constexpr (kWriteSums) {
 #pragma unroll
             for (int c = 0; c < D::R / 2; ++c) {
@@ -445,6 +464,13 @@ __global__ void __launch_bounds__(Dedup<P, H>::T)
             }
         }
     });
+    if (!ok) {
+        atomicOr(flags, 2u);
+        // copies still in flight must land before the CTA's shared memory
+        // is released (each wait bounded)
+        if (t == 0)
+            for (int g = 0; g < Steps::NG; ++g) (void)mbar_wait(&bars[g], 0);
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -887,6 +887,19 @@ fdas_status fdas_threshold(fdas_plan *plan, const void *plane, const double *sta
     return collect(p, cands, capacity, n_found, s);
 }
 
+fdas_status fdas_selftest_wait_timeout(fdas_plan *plan, int64_t limit_cycles, void *stream) {
+    if (!plan) return arg_error("plan is NULL");
+    if (limit_cycles < 1 || limit_cycles > 2000000000LL) return arg_error("limit_cycles out of range");
+    Plan &p = *reinterpret_cast<Plan *>(plan);
+    DeviceGuard guard(p.device);
+    cudaStream_t s = (cudaStream_t)stream;
+    FDAS_CUDA_TRY(cudaMemsetAsync(p.cand_count, 0, sizeof(unsigned long long), s));
+    FDAS_CUDA_TRY(cudaMemsetAsync(p.flags, 0, sizeof(unsigned int), s));
+    FDAS_TRY(launch_stuck_wait(p.flags, (long long)limit_cycles, s));
+    int64_t n_found = 0;
+    return collect(p, nullptr, 0, &n_found, s);
+}
+
 fdas_status fdas_template_bank(fdas_plan *plan, double *taps_out, double *energy_out,
                                void *bank_out, void *stream) {
     if (!plan) return arg_error("plan is NULL");

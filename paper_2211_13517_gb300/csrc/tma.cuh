@@ -64,12 +64,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned phase) {
     return ok != 0;
 }
 
-// wait for the given phase of the barrier; false after the timeout
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned phase) {
+// wait for the given phase of the barrier; false once `limit` clock cycles
+// have passed without it
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned phase,
+                                          long long limit = kMbarTimeoutCycles) {
     if (mbar_try_wait(bar, phase)) return true;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, phase))
-        if (clock64() - t0 > kMbarTimeoutCycles) return false;
+        if (clock64() - t0 > limit) return false;
     return true;
 }
 
