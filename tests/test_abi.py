@@ -45,8 +45,8 @@ def test_every_declared_symbol_is_exported(capi):
 def test_struct_layouts(capi):
     assert ctypes.sizeof(capi.fdas_candidate) == 20
     assert ctypes.sizeof(capi.fdas_series) == 24
-    assert ctypes.sizeof(capi.fdas_opts) == 48
-    assert ctypes.sizeof(capi.fdas_plan_info) == 168
+    assert ctypes.sizeof(capi.fdas_opts) == 56
+    assert ctypes.sizeof(capi.fdas_plan_info) == 176
     assert capi.CANDIDATE_DTYPE.itemsize == 20
     assert ctypes.sizeof(capi.fdas_seed) == capi.SEED_DTYPE.itemsize == 24
     assert ctypes.sizeof(capi.fdas_refined) == capi.REFINED_DTYPE.itemsize == 40
@@ -95,3 +95,5 @@ def test_null_arguments_rejected(capi):
     assert lib.fdas_plan_get_info(None, None) == capi.FDAS_ERR_ARG
     assert "NULL" in capi.fdas_last_error() or "plan" in capi.fdas_last_error()
     lib.fdas_plan_destroy(None)   # ignored
+    assert lib.fdas_selftest_wait_timeout(None, 1000, None) == capi.FDAS_ERR_ARG
+    assert lib.fdas_refine(None, None, None, 0, 0, None, None) == capi.FDAS_ERR_ARG
