@@ -60,7 +60,7 @@ enum { FDAS_NORM_MEDIAN = 0, FDAS_NORM_NONE = 1 };
  *   (FP32 arithmetic on the CUDA cores; every precision);
  * FDAS_CORR_TENSOR: the direct correlation sum_e g_z[e] X'_{r-e} as a GEMM
  *   on the tensor cores (16-bit operands, FP32 accumulation; FDAS_BF16 and
- *   FDAS_FP16 only, n_samples >= 2^10 and m(z_max) <= 104);
+ *   FDAS_FP16 only, with m_overlap <= 112, i.e. z_max <= 208);
  * FDAS_CORR_AUTO: TENSOR where it applies, else FFT. */
 enum { FDAS_CORR_AUTO = 0, FDAS_CORR_FFT = 1, FDAS_CORR_TENSOR = 2 };
 

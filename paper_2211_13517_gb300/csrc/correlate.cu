@@ -321,10 +321,14 @@ fdas_status launch_P(Plan &p, const void *spec, void *plane, double2 *partials, 
 
 }  // namespace
 
-int correlate_ctas(const Plan &p) { return p.n_seg * p.n_zchunk; }
+int correlate_ctas(const Plan &p) {
+    return p.correlator == FDAS_CORR_TENSOR ? correlate_tc_ctas(p) : p.n_seg * p.n_zchunk;
+}
 
 fdas_status launch_correlate(Plan &p, const void *spec_padded, void *plane, double2 *partials,
                              cudaStream_t s) {
+    if (p.correlator == FDAS_CORR_TENSOR)
+        return launch_correlate_tc(p, spec_padded, plane, partials, s);
     switch (p.prec) {
         case FDAS_FP32: return launch_P<PrecF32>(p, spec_padded, plane, partials, s);
         case FDAS_BF16: return launch_P<PrecBF16>(p, spec_padded, plane, partials, s);

@@ -1,0 +1,476 @@
+// The power plane on the tensor cores: the direct correlation as a GEMM.
+//
+// The matched filter of paper §2.1, F(r, z) = sum_{|e| <= m(z)} g_z[e] X'_{r-e},
+// P = |F|^2, is a product of two dense matrices once the spectrum is read as a
+// Hankel matrix.  For a tile of 512 bins starting at r_b and a chunk of 28
+// templates:
+//
+//   row i (0..127) of A holds the spectrum window X'_{r_b - W0 + 4i + q},
+//   q = kofs .. (complex, as interleaved 16-bit (re, im) pairs along K);
+//   column n = (zz, p, c) of B holds, at K position (q, re/im), the tap
+//   g_z[e] with e = p + W0 - kofs - q arranged so that the dot product gives
+//   Re F (c = 0) or Im F (c = 1) at r = r_b + 4i + p, p = 0..3.
+//
+// Row i + 1 of A is row i moved by 4 complex values = 16 bytes, so A needs no
+// copy at all: the window itself, described to the tensor core as a K-major
+// operand whose 8-row core matrices are 16 bytes apart along K (LBO = 16) and
+// 128 bytes apart along M (SBO = 128), *is* the Hankel matrix.  The four
+// phases p live in the template operand instead (B columns shifted by p taps),
+// so one accumulator row holds four consecutive bins of every template.
+//
+// One persistent CTA per SM takes a weighted contiguous run of (chunk, tile)
+// items.  Warp 0 (one thread) bulk-copies the chunk's template image (B, up to
+// 208 KB, once per chunk) and the spectrum windows (A, a ring of 4) into shared
+// memory; warp 1 (one thread) issues the tcgen05 MMAs (M = 128, N = 224, K = 16
+// each, BF16 or FP16 operands, FP32 accumulators) into one of two TMEM
+// accumulators; warps 2..9 read the finished accumulator (tcgen05.ld), form
+// P = re^2 + im^2, store 4 consecutive bins per template as one 8-byte store,
+// and sum P and P^2 for the plane statistics (FP32 per tile, FP64 across
+// tiles).  All waits are bounded; a wait that gives up sets flag bit 2.
+//
+// Unit template energy (noise cells distributed as Exp(1)) is kept for the
+// taps as rounded to 16 bits: P is |F|^2 / E'_z with E'_z = sum_e |g'_z[e]|^2
+// of the rounded taps g', one FP32 factor per template.
+#include <algorithm>
+
+#include "fdas_internal.cuh"
+#include "tcgen05.cuh"
+#include "tma.cuh"
+
+namespace fdas {
+
+namespace {
+
+constexpr int kTcRows = 128;                     // GEMM rows = TMEM lanes per tile
+constexpr int kTcPhases = 4;                     // r = r_b + 4 i + p
+constexpr int kTcTile = kTcRows * kTcPhases;     // bins per tile
+constexpr int kTcZ = 28;                         // templates per chunk
+constexpr int kTcN = kTcZ * kTcPhases * 2;       // GEMM columns (224)
+constexpr int kTcSlab = kTcN / 8 * 256;          // bytes of B per K step of 16
+constexpr int kTcStages = 4;                     // spectrum-window ring
+constexpr int kTcEpiWarps = 8;
+constexpr int kTcThreads = 32 * (2 + kTcEpiWarps);
+constexpr int kTcTmemCols = 512;
+constexpr int kTcAccStride = 256;                // TMEM column of accumulator 1
+constexpr int kTcEpiWeight = 6;                  // epilogue cost of a tile, in K steps
+constexpr size_t kTcMinSmem = 120 * 1024;        // keeps one CTA (and one TMEM owner) per SM
+
+// The (chunk, tile) items of CTA k of G: items are ordered chunk-major with
+// weight ks + kTcEpiWeight each, and CTA k takes those whose starting weight
+// falls in [k W / G, (k + 1) W / G).
+struct TcSchedule {
+    const TcChunk *ch;
+    int n_ch;
+    int64_t n_tiles, lo, hi, base, t;
+    int c;
+    __device__ TcSchedule(const TcChunk *chunks, int n_ch_, int64_t n_tiles_, int k, int G)
+        : ch(chunks), n_ch(n_ch_), n_tiles(n_tiles_), base(0), t(-1), c(0) {
+        int64_t w = 0;
+        for (int i = 0; i < n_ch; ++i) w += chunks[i].ks + kTcEpiWeight;
+        const int64_t total = w * n_tiles;
+        lo = total * k / G;
+        hi = total * (k + 1) / G;
+    }
+    __device__ bool next(int &oc, int64_t &ot) {
+        while (c < n_ch) {
+            const int64_t w = ch[c].ks + kTcEpiWeight;
+            if (base >= hi) break;
+            if (t < 0) t = lo > base ? (lo - base + w - 1) / w : 0;
+            if (t < n_tiles && base + t * w < hi) {
+                oc = c;
+                ot = t++;
+                return true;
+            }
+            base += n_tiles * w;
+            ++c;
+            t = -1;
+        }
+        c = n_ch;
+        return false;
+    }
+};
+
+template <class P>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    correlate_tc_kernel(const typename P::cpx *__restrict__ spec_pad,
+                        const unsigned char *__restrict__ bank_img,
+                        const TcChunk *__restrict__ chunks, int n_ch,
+                        const float *__restrict__ inv_energy,
+                        typename P::real *__restrict__ plane, double2 *__restrict__ partials,
+                        int64_t n_r, int win_bytes, int b_bytes_max, unsigned int *flags) {
+    extern __shared__ __align__(128) unsigned char tc_smem[];
+    unsigned char *const sB = tc_smem;
+    unsigned char *const sA = tc_smem + b_bytes_max;
+    __shared__ __align__(8) uint64_t a_full[kTcStages], a_empty[kTcStages];
+    __shared__ __align__(8) uint64_t b_full, b_empty, acc_full[2], acc_empty[2], drain;
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ double red[2][kTcEpiWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t n_tiles = n_r / kTcTile;
+    constexpr bool kBF16 = P::id == FDAS_BF16;
+    constexpr uint32_t kIdesc = idesc_f16<kBF16>(kTcRows, kTcN);
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kTcStages; ++i) {
+            mbar_init(&a_full[i], 1);
+            mbar_init(&a_empty[i], 1);
+        }
+        mbar_init(&b_full, 1);
+        mbar_init(&b_empty, 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&acc_full[i], 1);
+            mbar_init(&acc_empty[i], kTcEpiWarps);
+        }
+        mbar_init(&drain, 1);
+        mbar_fence_init();
+    }
+    if (warp == 1) {
+        __syncwarp();
+        tmem_alloc(&tmem_base_sh, kTcTmemCols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_sh;
+    bool ok = true;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // producer: template image per chunk, spectrum window per tile
+            TcSchedule sch(chunks, n_ch, n_tiles, blockIdx.x, gridDim.x);
+            int c, cur = -1, run = -1;
+            int64_t t;
+            int j = 0;
+            while (sch.next(c, t)) {
+                if (c != cur) {
+                    ++run;
+                    if (run > 0 && !mbar_wait(&b_empty, (run - 1) & 1)) {
+                        ok = false;
+                        break;
+                    }
+                    const unsigned bytes = (unsigned)chunks[c].ks * kTcSlab;
+                    mbar_arrive_expect_tx(&b_full, bytes);
+                    bulk_copy_g2s(sB, bank_img + chunks[c].b_off, bytes, &b_full);
+                    cur = c;
+                }
+                const int s = j % kTcStages;
+                if (j >= kTcStages && !mbar_wait(&a_empty[s], ((j / kTcStages) - 1) & 1)) {
+                    ok = false;
+                    break;
+                }
+                mbar_arrive_expect_tx(&a_full[s], (unsigned)win_bytes);
+                bulk_copy_g2s(sA + s * win_bytes, spec_pad + t * kTcTile, (unsigned)win_bytes,
+                              &a_full[s]);
+                ++j;
+            }
+            // every copy issued lands before the CTA can exit (bounded)
+            for (int s = 0; s < kTcStages && s < j; ++s) {
+                const int uses = (j - 1 - s) / kTcStages + 1;
+                (void)mbar_wait(&a_full[s], (uses - 1) & 1);
+            }
+            if (run >= 0) (void)mbar_wait(&b_full, run & 1);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // MMA issuer
+            TcSchedule sch(chunks, n_ch, n_tiles, blockIdx.x, gridDim.x);
+            int c, cur = -1, run = -1, ks = 0, kofs = 0;
+            int64_t t;
+            int j = 0;
+            const uint64_t bdesc0 = smem_desc(smem_u32(sB), 128, 256);
+            while (sch.next(c, t)) {
+                if (c != cur) {
+                    if (cur >= 0) tc_commit(&b_empty);   // the old template image is free
+                    ++run;
+                    cur = c;
+                    if (!mbar_wait(&b_full, run & 1)) {
+                        ok = false;
+                        break;
+                    }
+                    ks = chunks[c].ks;
+                    kofs = chunks[c].kofs;
+                }
+                const int s = j % kTcStages, b = j & 1;
+                if (!mbar_wait(&a_full[s], (j / kTcStages) & 1)) {
+                    ok = false;
+                    break;
+                }
+                if (j >= 2 && !mbar_wait(&acc_empty[b], ((j >> 1) - 1) & 1)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(b * kTcAccStride);
+                const uint64_t adesc = smem_desc(smem_u32(sA + s * win_bytes) + 4u * kofs, 16, 128);
+                for (int k = 0; k < ks; ++k)
+                    tc_mma_f16(d, adesc + 2ull * k, bdesc0 + (uint64_t)(kTcSlab >> 4) * k, kIdesc,
+                               k > 0 ? 1u : 0u);
+                tc_commit(&acc_full[b]);
+                tc_commit(&a_empty[s]);
+                ++j;
+            }
+            // every MMA issued has completed before TMEM is released (bounded)
+            tc_commit(&drain);
+            (void)mbar_wait(&drain, 0);
+        }
+    } else {
+        // epilogue: TMEM lanes 32 (warp % 4) .. + 31, column half (warp - 2) / 4
+        const int quarter = warp & 3;
+        const int half = (warp - 2) >> 2;
+        const int row = 32 * quarter + lane;
+        const uint32_t tlane = tmem + ((uint32_t)(32 * quarter) << 16);
+        TcSchedule sch(chunks, n_ch, n_tiles, blockIdx.x, gridDim.x);
+        int c;
+        int64_t t;
+        int j = 0;
+        double s1 = 0.0, s2 = 0.0;
+        while (sch.next(c, t)) {
+            const int b = j & 1;
+            const bool got = mbar_wait(&acc_full[b], (j >> 1) & 1);
+            if (!__all_sync(0xffffffffu, got)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const int z0 = chunks[c].z_begin, nzc = chunks[c].n_zc;
+            const int64_t r0 = t * kTcTile + 4 * row;
+            float f1 = 0.f, f2 = 0.f;
+#pragma unroll 1
+            for (int u = 0; u < kTcZ / 4; ++u) {
+                uint32_t v[16];
+                const int col = half * (kTcN / 2) + 16 * u;
+                tmem_ld16(tlane + (uint32_t)(b * kTcAccStride + col), v);
+                tmem_ld_wait();
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int zz = half * (kTcZ / 2) + 2 * u + h;
+                    const float sc = zz < nzc ? __ldg(inv_energy + z0 + zz) : 0.f;
+                    float pw[4];
+#pragma unroll
+                    for (int p = 0; p < 4; ++p) {
+                        const float re = __uint_as_float(v[8 * h + 2 * p]);
+                        const float im = __uint_as_float(v[8 * h + 2 * p + 1]);
+                        pw[p] = fmaf(re, re, im * im) * sc;
+                        f1 += pw[p];
+                        f2 = fmaf(pw[p], pw[p], f2);
+                    }
+                    if (zz < nzc) {
+                        const typename P::cpx lo =
+                            P::st(make_float2(pw[0] * P::plane_scale, pw[1] * P::plane_scale));
+                        const typename P::cpx hi =
+                            P::st(make_float2(pw[2] * P::plane_scale, pw[3] * P::plane_scale));
+                        uint2 o;
+                        memcpy(&o.x, &lo, 4);
+                        memcpy(&o.y, &hi, 4);
+                        *reinterpret_cast<uint2 *>(plane + (int64_t)(z0 + zz) * n_r + r0) = o;
+                    }
+                }
+            }
+            s1 += (double)f1;
+            s2 += (double)f2;
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[b]);
+            ++j;
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            s1 += __shfl_down_sync(0xffffffffu, s1, off);
+            s2 += __shfl_down_sync(0xffffffffu, s2, off);
+        }
+        if (lane == 0) {
+            red[0][warp - 2] = s1;
+            red[1][warp - 2] = s2;
+        }
+    }
+    if (!ok) atomicOr(flags, 2u);
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, q = 0.0;
+        for (int w = 0; w < kTcEpiWarps; ++w) {
+            a += red[0][w];
+            q += red[1][w];
+        }
+        partials[blockIdx.x] = make_double2(a, q);
+    }
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc(tmem, kTcTmemCols);
+    }
+}
+
+// The template operand of every chunk, laid out exactly as the kernel's
+// shared-memory image: per K step a slab of [n-block 28][K core 2][row 8][8
+// values]; column n = 8 zz + 2 p + c, K element kk of step k is complex tap
+// q = 8 k + kk / 2, component kk % 2 (re, im).
+template <class P>
+__global__ void tc_bank_kernel(uint16_t *__restrict__ img, const TcChunk *__restrict__ chunks,
+                               const double *__restrict__ taps, const int64_t *__restrict__ off,
+                               const int32_t *__restrict__ m, int W0) {
+    const TcChunk ch = chunks[blockIdx.y];
+    const int64_t n_el = (int64_t)ch.ks * (kTcSlab / 2);
+    uint16_t *out = img + ch.b_off / 2;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_el;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(i / (kTcSlab / 2));
+        const int e_lin = (int)(i % (kTcSlab / 2));
+        const int nb = e_lin / 128, cb = (e_lin / 64) & 1, rw = (e_lin / 8) & 7, kk8 = e_lin & 7;
+        const int zz = nb, p = rw >> 1, c = rw & 1;
+        const int kk = 8 * cb + kk8;
+        const int q = 8 * k + kk / 2, comp = kk & 1;
+        double v = 0.0;
+        if (zz < ch.n_zc) {
+            const int iz = ch.z_begin + zz;
+            const int e = p + W0 - ch.kofs - q;
+            const int mz = m[iz];
+            if (e >= -mz && e <= mz) {
+                const int64_t ti = off[iz] + e + mz;
+                const double gr = taps[2 * ti], gi = taps[2 * ti + 1];
+                v = c == 0 ? (comp == 0 ? gr : -gi) : (comp == 0 ? gi : gr);
+            }
+        }
+        const typename P::real r = P::str((float)v);
+        uint16_t bits;
+        memcpy(&bits, &r, 2);
+        out[i] = bits;
+    }
+}
+
+// 1 / E'_z, E'_z = sum_e |g'_z[e]|^2 of the taps as rounded to the plan's
+// 16-bit type (one block per template, FP64 sum in a fixed order)
+template <class P>
+__global__ void tc_energy_kernel(float *__restrict__ inv_energy, const double *__restrict__ taps,
+                                 const int64_t *__restrict__ off, const int32_t *__restrict__ m) {
+    __shared__ double sh[128];
+    const int iz = blockIdx.x;
+    const int n = 2 * m[iz] + 1;
+    double a = 0.0;
+    for (int e = threadIdx.x; e < n; e += 128) {
+        const int64_t ti = off[iz] + e;
+        const float gr = P::ldr(P::str((float)taps[2 * ti]));
+        const float gi = P::ldr(P::str((float)taps[2 * ti + 1]));
+        a += (double)gr * gr + (double)gi * gi;
+    }
+    sh[threadIdx.x] = a;
+    __syncthreads();
+    for (int w = 64; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) inv_energy[iz] = sh[0] > 0.0 ? (float)(1.0 / sh[0]) : 0.f;
+}
+
+size_t tc_smem_bytes(int max_ks, int win) {
+    const size_t need = (size_t)max_ks * kTcSlab + (size_t)kTcStages * win * 4;
+    return std::max(need, kTcMinSmem);
+}
+
+template <class P>
+fdas_status launch_tc_P(Plan &p, const void *spec_padded, void *plane, double2 *partials,
+                        cudaStream_t s) {
+    const size_t smem = tc_smem_bytes(p.tc_max_ks, p.tc_win);
+    auto k = correlate_tc_kernel<P>;
+    FDAS_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int grid = correlate_tc_ctas(p);
+    k<<<grid, kTcThreads, smem, s>>>((const typename P::cpx *)spec_padded,
+                                      (const unsigned char *)p.tc_bank, p.tc_chunks, p.tc_n_ch,
+                                      p.tc_inv_energy, (typename P::real *)plane, partials, p.n_r,
+                                      p.tc_win * 4,
+                                      p.tc_max_ks * kTcSlab, p.flags);
+    FDAS_CUDA_TRY(cudaGetLastError());
+    return FDAS_OK;
+}
+
+}  // namespace
+
+std::vector<TcChunk> tc_chunk_table(const Plan &p, const std::vector<int32_t> &m, int *win,
+                                    int *max_ks) {
+    const int W0 = p.m_ov;
+    std::vector<TcChunk> out;
+    int64_t b_off = 0;
+    int wmax = 0, kmax = 0;
+    for (int z0 = 0; z0 < p.n_z; z0 += kTcZ) {
+        TcChunk c;
+        c.z_begin = z0;
+        c.n_zc = std::min(kTcZ, p.n_z - z0);
+        int mc = 0;
+        for (int iz = z0; iz < z0 + c.n_zc; ++iz) mc = std::max(mc, m[iz]);
+        c.kofs = (W0 - mc) & ~3;
+        const int kc = (W0 - c.kofs + mc + 4 + 7) / 8 * 8;   // complex taps q in [0, kc)
+        c.ks = kc / 8;
+        c.b_off = b_off;
+        b_off += (int64_t)c.ks * kTcSlab;
+        wmax = std::max(wmax, c.kofs + kc);
+        kmax = std::max(kmax, c.ks);
+        out.push_back(c);
+    }
+    *win = (4 * (kTcRows - 1) + wmax + 3) / 4 * 4;
+    *max_ks = kmax;
+    return out;
+}
+
+bool tc_applicable(const Plan &p, std::string *why) {
+    if (p.prec == FDAS_FP32) {
+        if (why) *why = "the tensor-core correlation takes 16-bit storage (FDAS_BF16/FDAS_FP16)";
+        return false;
+    }
+    if (p.n_r % kTcTile != 0) {
+        if (why) *why = "the tensor-core correlation needs n_samples >= 1024";
+        return false;
+    }
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        cudaGetLastError();
+        optin = 0;
+    }
+    if (tc_smem_bytes(p.tc_max_ks, p.tc_win) + 1024 > (size_t)optin) {
+        if (why) *why = "the widest template chunk does not fit in shared memory (z_max too large)";
+        return false;
+    }
+    return true;
+}
+
+int correlate_tc_ctas(const Plan &p) {
+    const int64_t items = (p.n_r / kTcTile) * (int64_t)p.tc_n_ch;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(p.n_sms, items));
+}
+
+fdas_status launch_tc_bank(Plan &p, cudaStream_t s) {
+    dim3 grid(64, p.tc_n_ch);
+    switch (p.prec) {
+        case FDAS_BF16:
+            tc_bank_kernel<PrecBF16><<<grid, 256, 0, s>>>((uint16_t *)p.tc_bank, p.tc_chunks, p.taps,
+                                                          p.tap_off, p.tap_m, p.m_ov);
+            tc_energy_kernel<PrecBF16><<<p.n_z, 128, 0, s>>>(p.tc_inv_energy, p.taps, p.tap_off,
+                                                             p.tap_m);
+            break;
+        case FDAS_FP16:
+            tc_bank_kernel<PrecF16><<<grid, 256, 0, s>>>((uint16_t *)p.tc_bank, p.tc_chunks, p.taps,
+                                                         p.tap_off, p.tap_m, p.m_ov);
+            tc_energy_kernel<PrecF16><<<p.n_z, 128, 0, s>>>(p.tc_inv_energy, p.taps, p.tap_off,
+                                                            p.tap_m);
+            break;
+        default:
+            set_error("tensor-core correlation: 16-bit precisions only");
+            return FDAS_ERR_UNSUPPORTED;
+    }
+    FDAS_CUDA_TRY(cudaGetLastError());
+    return FDAS_OK;
+}
+
+fdas_status launch_correlate_tc(Plan &p, const void *spec_padded, void *plane, double2 *partials,
+                                cudaStream_t s) {
+    switch (p.prec) {
+        case FDAS_BF16: return launch_tc_P<PrecBF16>(p, spec_padded, plane, partials, s);
+        case FDAS_FP16: return launch_tc_P<PrecF16>(p, spec_padded, plane, partials, s);
+        default:
+            set_error("tensor-core correlation: 16-bit precisions only");
+            return FDAS_ERR_UNSUPPORTED;
+    }
+}
+
+}  // namespace fdas

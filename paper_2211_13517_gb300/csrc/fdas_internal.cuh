@@ -132,6 +132,16 @@ struct TrialStats {
     float thr[8];   // T_h per stage (FP32, compared against FP32 sums)
 };
 
+// one chunk of templates of the tensor-core correlation: its templates, the
+// K range it reads of each spectrum window and where its operand image lives
+struct TcChunk {
+    int32_t z_begin;   // first template index of the chunk
+    int32_t n_zc;      // templates in the chunk (the rest of the 28 columns are 0)
+    int32_t kofs;      // first complex element of the window it reads (multiple of 4)
+    int32_t ks;        // K steps of 8 complex taps (16 real elements)
+    int64_t b_off;     // byte offset of the chunk's template image in tc_bank
+};
+
 // ---------------------------------------------------------------------------
 // plan
 // ---------------------------------------------------------------------------
@@ -150,6 +160,13 @@ struct Plan {
     bool use_graph = false;
     cudaGraphExec_t graph_exec = nullptr;   // last captured batch
     double tuned_ms = 0.0;
+    int correlator = FDAS_CORR_FFT;   // FDAS_CORR_FFT or FDAS_CORR_TENSOR
+    // tensor-core correlation: template chunks, their operand images and the
+    // spectrum window each GEMM tile reads (complex elements)
+    TcChunk *tc_chunks = nullptr;
+    void *tc_bank = nullptr;
+    float *tc_inv_energy = nullptr;   // [n_z] 1 / energy of the 16-bit taps
+    int tc_n_ch = 0, tc_max_ks = 0, tc_win = 0;
     // FFT split of the N/2-point complex FFT in the spectrum stage
     int fft_m1, fft_m2;     // M = m1 * m2 (m1 = 1: single pass)
     // device memory
@@ -203,6 +220,15 @@ fdas_status launch_spectrum(Plan &p, const float *x, void *spec_out_padded,
 fdas_status launch_correlate(Plan &p, const void *spec_padded, void *plane,
                              double2 *partials, cudaStream_t s);
 int correlate_ctas(const Plan &p);
+// tensor-core correlation: whether it applies to the plan's geometry, the
+// host-side chunk table, the operand images (from the FP64 taps) and launch
+bool tc_applicable(const Plan &p, std::string *why);
+std::vector<TcChunk> tc_chunk_table(const Plan &p, const std::vector<int32_t> &m, int *win,
+                                    int *max_ks);
+fdas_status launch_tc_bank(Plan &p, cudaStream_t s);
+fdas_status launch_correlate_tc(Plan &p, const void *spec_padded, void *plane, double2 *partials,
+                                cudaStream_t s);
+int correlate_tc_ctas(const Plan &p);
 fdas_status launch_finalize_stats(Plan &p, const double2 *partials, int n_partials,
                                   const double *given_stats, TrialStats *out,
                                   cudaStream_t s);

@@ -74,6 +74,9 @@ static void free_plan_memory(Plan *p) {
     cudaFree(p->fft_a);
     cudaFree(p->fft_b);
     cudaFree(p->spec_pad);
+    cudaFree(p->tc_chunks);
+    cudaFree(p->tc_bank);
+    cudaFree(p->tc_inv_energy);
     for (int b = 0; b < 2; ++b) {
         cudaFree(p->plane[b]);
         cudaFree(p->partials[b]);
@@ -212,6 +215,9 @@ static fdas_status create(Plan *&out, int64_t n_samples, double tsamp, double z_
         return arg_error("max_candidates must be in [1, 2^26]");
     if (o->autotune != 0 && o->autotune != 1) return arg_error("autotune must be 0 or 1");
     if (o->use_graph != 0 && o->use_graph != 1) return arg_error("use_graph must be 0 or 1");
+    if (o->correlator != FDAS_CORR_AUTO && o->correlator != FDAS_CORR_FFT &&
+        o->correlator != FDAS_CORR_TENSOR)
+        return arg_error("unknown correlator");
 
     Plan *pp = new (std::nothrow) Plan();
     if (!pp) return arg_error("out of host memory");
@@ -273,11 +279,31 @@ static fdas_status create(Plan *&out, int64_t n_samples, double tsamp, double z_
     p.n_zchunk = choose_zchunks(p, p.n_sms);
     // partials serve every length the plan accepts (N, N/2, ..., 2^10) and
     // any template chunking up to 32
-    p.partials_cap = (int64_t)p.n_seg * 32;
+    p.partials_cap = std::max<int64_t>((int64_t)p.n_seg * 32, p.n_sms);
     for (int64_t n = n_samples; n >= (1 << 10); n /= 2) {
         Plan v = p;
         set_length(v, n);
         p.partials_cap = std::max<int64_t>(p.partials_cap, (int64_t)v.n_seg * 32);
+    }
+    // the correlator: the tensor-core GEMM where it applies (16-bit storage,
+    // template chunks that fit in shared memory), else overlap-save FFTs
+    std::vector<TcChunk> tc_table;
+    if (o->correlator != FDAS_CORR_FFT && p.prec != FDAS_FP32) {
+        tc_table = tc_chunk_table(p, m, &p.tc_win, &p.tc_max_ks);
+        p.tc_n_ch = (int)tc_table.size();
+    }
+    {
+        std::string why = "the tensor-core correlation takes 16-bit storage (FDAS_BF16/FDAS_FP16)";
+        const bool tc_ok = !tc_table.empty() && tc_applicable(p, &why);
+        if (o->correlator == FDAS_CORR_TENSOR && !tc_ok) {
+            delete pp;
+            return arg_error("correlator FDAS_CORR_TENSOR: " + why);
+        }
+        p.correlator = (o->correlator != FDAS_CORR_FFT && tc_ok) ? FDAS_CORR_TENSOR : FDAS_CORR_FFT;
+        if (p.correlator != FDAS_CORR_TENSOR) {
+            tc_table.clear();
+            p.tc_n_ch = 0;
+        }
     }
 
     fdas_status st = FDAS_OK;
@@ -306,7 +332,9 @@ static fdas_status create(Plan *&out, int64_t n_samples, double tsamp, double z_
     PLAN_TRY(dalloc(p, &p.tap_m, sizeof(int32_t) * p.n_z));
     if (p.fft_m1 > 1) PLAN_TRY(dalloc(p, &p.fft_a, sizeof(float2) * (size_t)p.n_r));
     PLAN_TRY(dalloc(p, &p.fft_b, sizeof(float2) * (size_t)p.n_r));
-    const size_t pad_elems = (size_t)p.n_seg * p.V + 2 * (size_t)p.m_ov;
+    // 64 elements past the last segment: the tensor-core windows of the last
+    // tile read up to 16 elements beyond the zero tail
+    const size_t pad_elems = (size_t)p.n_seg * p.V + 2 * (size_t)p.m_ov + 64;
     PLAN_TRY(dalloc(p, &p.spec_pad, cb * pad_elems));
     for (int b = 0; b < 2; ++b) {
         PLAN_TRY(dalloc(p, &p.plane[b], rb * (size_t)p.n_z * (size_t)p.n_r));
@@ -341,6 +369,16 @@ static fdas_status create(Plan *&out, int64_t n_samples, double tsamp, double z_
     PLAN_CUDA(cudaMemcpy(p.tap_off, off.data(), sizeof(int64_t) * p.n_z, cudaMemcpyHostToDevice));
     PLAN_CUDA(cudaMemcpy(p.tap_m, m.data(), sizeof(int32_t) * p.n_z, cudaMemcpyHostToDevice));
     PLAN_TRY(launch_template_bank(p, p.aux));
+    if (p.correlator == FDAS_CORR_TENSOR) {
+        int64_t img = 0;
+        for (const TcChunk &c : tc_table) img = std::max<int64_t>(img, c.b_off + (int64_t)c.ks * 7168);
+        PLAN_TRY(dalloc(p, &p.tc_chunks, sizeof(TcChunk) * tc_table.size()));
+        PLAN_TRY(dalloc(p, &p.tc_bank, (size_t)img));
+        PLAN_TRY(dalloc(p, &p.tc_inv_energy, sizeof(float) * (size_t)p.n_z));
+        PLAN_CUDA(cudaMemcpyAsync(p.tc_chunks, tc_table.data(), sizeof(TcChunk) * tc_table.size(),
+                                  cudaMemcpyHostToDevice, p.aux));
+        PLAN_TRY(launch_tc_bank(p, p.aux));
+    }
     PLAN_CUDA(cudaStreamSynchronize(p.aux));
     PLAN_CUDA(cudaDeviceSynchronize());
 #undef PLAN_TRY
@@ -689,20 +727,31 @@ static fdas_status time_correlation(Plan &p, double &ms) {
     return FDAS_OK;
 }
 
-// autotune: the segment length among {2048, 4096, 8192} and the one asked
-// for, then the template chunking of the fastest, by timing the correlation
+// autotune: the correlator (the tensor-core GEMM, where it applies and was
+// not excluded, against overlap-save FFTs), the segment length among {2048,
+// 4096, 8192} and the one asked for, then the template chunking of the
+// fastest FFT plan, by timing the correlation
 static fdas_status create_tuned(Plan *&out, int64_t n_samples, double tsamp, double z_max,
                                 double z_step, int32_t seg_len, int32_t n_harm, fdas_opts o) {
     o.autotune = 0;
-    std::vector<int32_t> cand = {2048, 4096, 8192};
-    if (std::find(cand.begin(), cand.end(), seg_len) == cand.end()) cand.push_back(seg_len);
+    std::vector<std::pair<int32_t, int32_t>> cand;   // (seg_len, correlator)
+    if (o.correlator != FDAS_CORR_TENSOR) {
+        std::vector<int32_t> lens = {2048, 4096, 8192};
+        if (std::find(lens.begin(), lens.end(), seg_len) == lens.end()) lens.push_back(seg_len);
+        for (int32_t L : lens) cand.push_back({L, FDAS_CORR_FFT});
+    }
+    if (o.correlator != FDAS_CORR_FFT && o.precision != FDAS_FP32)
+        cand.push_back({seg_len, FDAS_CORR_TENSOR});
     Plan *best = nullptr;
     double best_ms = 1e300;
     std::string first_error;
     fdas_status first_status = FDAS_OK;
-    for (int32_t L : cand) {
+    for (const auto &lc : cand) {
+        const int32_t L = lc.first;
         Plan *p = nullptr;
-        fdas_status s = create(p, n_samples, tsamp, z_max, z_step, L, n_harm, &o);
+        fdas_opts oc = o;
+        oc.correlator = lc.second;
+        fdas_status s = create(p, n_samples, tsamp, z_max, z_step, L, n_harm, &oc);
         if (s != FDAS_OK) {
             if (first_status == FDAS_OK) {
                 first_status = s;
@@ -732,6 +781,7 @@ static fdas_status create_tuned(Plan *&out, int64_t n_samples, double tsamp, dou
     const int base = best->n_zchunk;
     int best_c = base;
     for (int c : {1, 2, 3, 4, 6, 8, 12, 16}) {
+        if (best->correlator != FDAS_CORR_FFT) break;
         if (c == base || c > best->n_z || (int64_t)best->n_seg * c > best->partials_cap) continue;
         best->n_zchunk = c;
         double ms = 0.0;
@@ -821,6 +871,8 @@ fdas_status fdas_plan_get_info(const fdas_plan *plan, fdas_plan_info *info) {
     info->z_chunks = p.n_zchunk;
     info->use_graph = p.use_graph ? 1 : 0;
     info->tuned_ms = p.tuned_ms;
+    info->correlator = p.correlator;
+    info->reserved = 0;
     return FDAS_OK;
 }
 

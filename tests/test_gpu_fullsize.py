@@ -79,10 +79,12 @@ def test_fullsize_fp32_plane_and_candidates(capi, pulsar_case):
     plan.close()
 
 
+@pytest.mark.parametrize("corr", [1, 2])
 @pytest.mark.parametrize("prec", [1, 2])
-def test_fullsize_low_precision_power_error(capi, pulsar_case, prec):
+def test_fullsize_low_precision_power_error(capi, pulsar_case, prec, corr):
     x, params, ref = pulsar_case
-    plan = capi.Plan(N, 64e-6, Z_MAX, Z_STEP, L, H, precision=prec)
+    plan = capi.Plan(N, 64e-6, Z_MAX, Z_STEP, L, H, precision=prec, correlator=corr)
+    assert plan.info.correlator == corr
     st, cands, nf = plan.search([torch.from_numpy(x).cuda()], capacity=1 << 18)
     assert st == capi.FDAS_OK and nf > 0
     g, r = _keyset(cands, "trial_id"), _keyset(ref["candidates"], "trial")

@@ -101,11 +101,13 @@ def test_spectrum_without_normalisation(capi):
 # ---------------------------------------------------------------------------
 # a3-a6: correlation / power plane / statistics
 # ---------------------------------------------------------------------------
-def _plane_case(capi, n, z_max, z_step, L, seed=7, prec=0):
+def _plane_case(capi, n, z_max, z_step, L, seed=7, prec=0, corr=None):
     x = S.sinusoid_series(n=n, seed=seed, r0=0.3 * n / 2 + 0.4, z0=z_max * 0.45, amp=0.1)
     g = O.geometry(n, z_max, z_step, 4)
     Xn, _ = O.normalise(O.spectrum(x), 2048)
-    plan = _plan(capi, n, z_max, z_step, L, 4, precision=prec)
+    plan = _plan(capi, n, z_max, z_step, L, 4, precision=prec, correlator=corr)
+    if corr is not None:
+        assert plan.info.correlator == corr
     il = np.empty(2 * Xn.shape[0], dtype=np.float32)
     il[0::2], il[1::2] = Xn.real, Xn.imag
     spec = torch.from_numpy(il).cuda().to(plan.spec_dtype)
@@ -136,16 +138,59 @@ def test_power_plane_fp32_matches_direct_correlation(capi, n, z_max, z_step, L):
     plan.close()
 
 
+@pytest.mark.parametrize("corr", [1, 2])
 @pytest.mark.parametrize("prec", [1, 2])
-def test_power_plane_low_precision_storage(capi, prec):
-    plan, plane, stats, P, g = _plane_case(capi, 1 << 17, 16.0, 2.0, 2048, prec=prec)
+def test_power_plane_low_precision_storage(capi, prec, corr):
+    """Both correlators (overlap-save FFTs, tensor-core GEMM) at BF16/FP16:
+    every cell within 3% of max(P, mean), statistics within 1e-3."""
+    plan, plane, stats, P, g = _plane_case(capi, 1 << 17, 16.0, 2.0, 2048, prec=prec, corr=corr)
     got = plane.float().cpu().numpy().astype(np.float64)
     if prec == 2:
         got *= 16.0          # FP16 planes hold P/16
-    mean, _ = O.plane_stats(P)
+    mean, std = O.plane_stats(P)
     rel = np.abs(got - P) / np.maximum(P, mean)
     assert rel.max() < 0.03, rel.max()
+    s = stats.cpu().numpy()
+    assert abs(s[0] / mean - 1) < 1e-3 and abs(s[1] / std - 1) < 1e-3, (s, mean, std)
     plan.close()
+
+
+@pytest.mark.parametrize("n,z_max,z_step", [
+    (1 << 10, 2.0, 1.0),        # one 512-bin tile
+    (1 << 12, 0.0, 1.0),        # a single template (z = 0)
+    (1 << 14, 7.5, 0.5),        # half-step grid, ragged last chunk (31 templates)
+    (1 << 16, 96.0, 1.0),       # the 193-template grid: 7 chunks of 28
+    (1 << 15, 200.0, 4.0),      # widest templates (m = 108), 101 templates
+])
+@pytest.mark.parametrize("prec", [1, 2])
+def test_tensor_plane_matches_direct_correlation(capi, n, z_max, z_step, prec):
+    """The tensor-core correlation against the FP64 direct sum over the whole
+    plane (every tile, chunk and phase), on the spectrum exactly as stored:
+    within 3% of max(P, mean) (16-bit taps and plane, FP32 sums)."""
+    plan, plane, stats, P, g = _plane_case(capi, n, z_max, z_step, 1024 if z_max < 100 else 2048,
+                                           prec=prec, corr=capi.FDAS_CORR_TENSOR)
+    got = plane.float().cpu().numpy().astype(np.float64)
+    if prec == 2:
+        got *= 16.0
+    mean, std = O.plane_stats(P)
+    rel = np.abs(got - P) / np.maximum(P, mean)
+    assert rel.max() < 0.03, (rel.max(), np.unravel_index(np.argmax(rel), rel.shape))
+    s = stats.cpu().numpy()
+    assert abs(s[0] / mean - 1) < 1e-3 and abs(s[1] / std - 1) < 1e-3, (s, mean, std)
+    plan.close()
+
+
+def test_tensor_correlator_is_refused_where_it_does_not_apply(capi):
+    with pytest.raises(capi.FdasError) as ei:
+        _plan(capi, 1 << 14, 16.0, 2.0, 2048, 4, precision=capi.FDAS_FP32,
+              correlator=capi.FDAS_CORR_TENSOR)
+    assert ei.value.status == capi.FDAS_ERR_ARG
+    auto32 = _plan(capi, 1 << 14, 16.0, 2.0, 2048, 4)
+    assert auto32.info.correlator == capi.FDAS_CORR_FFT
+    auto16 = _plan(capi, 1 << 14, 16.0, 2.0, 2048, 4, precision=capi.FDAS_BF16)
+    assert auto16.info.correlator == capi.FDAS_CORR_TENSOR
+    auto32.close()
+    auto16.close()
 
 
 # ---------------------------------------------------------------------------
@@ -253,11 +298,12 @@ def test_search_sinusoid_workload_fp32(capi):
     plan.close()
 
 
+@pytest.mark.parametrize("corr", [1, 2])
 @pytest.mark.parametrize("prec", [1, 2])
-def test_search_low_precision_within_three_percent(capi, prec):
+def test_search_low_precision_within_three_percent(capi, prec, corr):
     x = S.sinusoid_series()
     ref = O.search(x, 16.0, 2.0, 4, guard=0.03)
-    plan = _plan(capi, 1 << 17, 16.0, 2.0, 2048, 4, precision=prec)
+    plan = _plan(capi, 1 << 17, 16.0, 2.0, 2048, 4, precision=prec, correlator=corr)
     st, cands, nf = plan.search([torch.from_numpy(x).cuda()])
     assert st == capi.FDAS_OK and nf > 0
     gk, rk = _compare_cands(cands, ref["candidates"], ref["guard"], rel_power=0.03)
