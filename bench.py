@@ -61,6 +61,17 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def _bf16_peak():
+    """Dense BF16 tensor peak in TFLOP/s for a kernel timed inside a long
+    step (the sustained figure), and its source."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["bf16_tflops_sustained"]), "measured bf16_tflops_sustained"
+    except Exception:
+        return 1700.0, "fallback (sustained bf16)"
+
+
 # ---------------------------------------------------------------------------
 # clocks and energy (read-only)
 # ---------------------------------------------------------------------------
@@ -158,6 +169,11 @@ def work_model(info, prec_bytes):
         # FFT flop model per (segment, template): 4.25 L log2 L + 9 L
         "correlate_flops": (4.25 * L * math.log2(L) + 9 * L) * info.n_seg * n_z,
         "correlate_bytes": b_s * n_r + plane,
+        # direct correlation (tensor cores): 8 real flops per complex tap
+        # product, sum over templates of (2 m(z) + 1) taps per bin
+        "correlate_tc_flops": 8.0 * n_r * sum(
+            2 * (8 + math.ceil(abs(i - info.iz0) * info.z_step / 2.0 - 1e-9)) + 1
+            for i in range(n_z)),
         # harmonic gathers: unique cells of stream j are (j/H)^2 of the plane
         "harmonic_bytes": plane * gather,
         "alg_bytes": 4 * n + 2 * b_s * n_r + plane * (1 + gather),
@@ -353,7 +369,7 @@ def run_gpu(args, rank, world, local_rank, dist):
     wm = work_model(info, 2)
     groups = capi.PROFILE_GROUPS
 
-    def group_stats(prof, wmod):
+    def group_stats(prof, wmod, tensor=False):
         res = {}
         for g in groups:
             launches, timed_n, ms = prof[g]
@@ -363,26 +379,41 @@ def run_gpu(args, rank, world, local_rank, dist):
         t_co = res["correlate"]["ms_per_trial"] / 1e3
         t_hs = res["harmonic"]["ms_per_trial"] / 1e3
         res["spectrum"]["gbs"] = wmod["spectrum_bytes"] / t_sp / 1e9 if t_sp else None
-        res["correlate"]["tflops"] = wmod["correlate_flops"] / t_co / 1e12 if t_co else None
+        flops = wmod["correlate_tc_flops"] if tensor else wmod["correlate_flops"]
+        res["correlate"]["tflops"] = flops / t_co / 1e12 if t_co else None
         res["correlate"]["gbs"] = wmod["correlate_bytes"] / t_co / 1e9 if t_co else None
         res["harmonic"]["gbs"] = wmod["harmonic_bytes"] / t_hs / 1e9 if t_hs else None
         return res
 
-    k_bf16 = group_stats(prof_bf16, wm)
-    # dominant kernel by summed event time
-    dom = max(("correlate", "harmonic"), key=lambda g: k_bf16[g]["ms_total"])
-    traffic = _ncu_traffic(dom, "bf16")
-    if dom == "harmonic":
-        roof = {"kernel": "harmonic_threshold_kernel (bf16 plane)", "bound": "hbm",
-                "achieved": k_bf16["harmonic"]["gbs"], "peak": peak_hbm, "unit": "GB/s",
-                "frac": k_bf16["harmonic"]["gbs"] / peak_hbm, "traffic": traffic,
-                "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)"}
-    else:
+    tensor = info.correlator == capi.FDAS_CORR_TENSOR
+    k_bf16 = group_stats(prof_bf16, wm, tensor)
+    peak_tc, peak_tc_src = _bf16_peak()
+
+    def roof_of(group):
+        traffic = _ncu_traffic(group, "bf16")
+        if group == "harmonic":
+            return {"kernel": "harmonic_dedup_kernel<BF16,16>", "bound": "hbm",
+                    "achieved": k_bf16["harmonic"]["gbs"], "peak": peak_hbm, "unit": "GB/s",
+                    "frac": k_bf16["harmonic"]["gbs"] / peak_hbm, "traffic": traffic,
+                    "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)",
+                    "work": "plane x sum_j (j/H)^2 = 5.84 planes of BF16 reads per trial"}
         a = k_bf16["correlate"]["tflops"]
-        roof = {"kernel": "correlate_kernel<8192> (bf16)", "bound": "alu", "achieved": a,
+        if tensor:
+            return {"kernel": "correlate_tc_kernel<BF16> (tcgen05)", "bound": "tensor",
+                    "achieved": a, "peak": peak_tc, "unit": "TFLOP/s", "frac": a / peak_tc,
+                    "traffic": traffic, "peak_source": f"{peak_tc_src} (MEASURED_PEAKS.json)",
+                    "work": "8 flops x N_r x sum_z (2 m(z) + 1) per trial (useful taps only)",
+                    "plane_write_gbs": k_bf16["correlate"]["gbs"],
+                    "plane_write_frac": k_bf16["correlate"]["gbs"] / peak_hbm}
+        return {"kernel": "correlate8k_kernel<BF16> (FFT)", "bound": "alu", "achieved": a,
                 "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": a / FP32_ALU_PEAK_TFLOPS,
                 "traffic": traffic,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
+
+    # dominant kernel by summed event time
+    dom = max(("correlate", "harmonic"), key=lambda g: k_bf16[g]["ms_total"])
+    roof = roof_of(dom)
+    other = roof_of("harmonic" if dom == "correlate" else "correlate")
     alg_gbs = wm["alg_bytes"] * args.batch * args.steps / (ms_bf16 / 1000.0) / 1e9
     launches = sum(prof_bf16[g][0] for g in groups)
     line = {
@@ -391,6 +422,7 @@ def run_gpu(args, rank, world, local_rank, dist):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "storage": "bf16",
         "data": "synthetic", "config": _config(args, "bf16 storage, fp32 arithmetic"),
         "roofline": roof,
+        "roofline_other": other,
         "hbm_alg": {"bytes_per_trial": wm["alg_bytes"], "achieved_gbs": alg_gbs,
                     "peak_gbs": peak_hbm, "frac": alg_gbs / peak_hbm,
                     "note": f"B_alg of the whole path / step time, {peak_src} peak"},
@@ -407,7 +439,7 @@ def run_gpu(args, rank, world, local_rank, dist):
         v32 = trials / (ms_fp32 / 1000.0)
         wm32 = work_model(info, 4)
         line["fp32"] = {"value": v32, "ms_per_step": ms_fp32 / args.steps,
-                        "kernels": group_stats(prof_fp32, wm32),
+                        "kernels": group_stats(prof_fp32, wm32, False),
                         "joules_per_trial": (j_fp32 / (args.batch * args.steps)) if j_fp32 else None,
                         "hbm_alg_frac": wm32["alg_bytes"] * args.batch * args.steps
                         / (ms_fp32 / 1000.0) / 1e9 / peak_hbm}

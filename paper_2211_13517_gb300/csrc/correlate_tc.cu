@@ -7,7 +7,7 @@
 //
 //   row i (0..127) of A holds the spectrum window X'_{r_b - W0 + 4i + q},
 //   q = kofs .. (complex, as interleaved 16-bit (re, im) pairs along K);
-//   column n = (zz, p, c) of B holds, at K position (q, re/im), the tap
+//   column n = 8 zz + 4 c + p of B holds, at K position (q, re/im), the tap
 //   g_z[e] with e = p + W0 - kofs - q arranged so that the dot product gives
 //   Re F (c = 0) or Im F (c = 1) at r = r_b + 4i + p, p = 0..3.
 //
@@ -23,10 +23,13 @@
 // 208 KB, once per chunk) and the spectrum windows (A, a ring of 4) into shared
 // memory; warp 1 (one thread) issues the tcgen05 MMAs (M = 128, N = 224, K = 16
 // each, BF16 or FP16 operands, FP32 accumulators) into one of two TMEM
-// accumulators; warps 2..9 read the finished accumulator (tcgen05.ld), form
-// P = re^2 + im^2, store 4 consecutive bins per template as one 8-byte store,
-// and sum P and P^2 for the plane statistics (FP32 per tile, FP64 across
-// tiles).  All waits are bounded; a wait that gives up sets flag bit 2.
+// accumulators; warps 2..17 read the finished accumulator (tcgen05.ld, all
+// loads of a tile before one wait, then release the accumulator at once),
+// form P = re^2 + im^2 with packed FP32x2 arithmetic (the column order puts
+// the re and the im parts of the 4 phases side by side), store 4 consecutive
+// bins per template as one 8-byte store, and sum P and P^2 for the plane
+// statistics (FP32 per tile, FP64 across tiles).  All waits are bounded; a
+// wait that gives up sets flag bit 2.
 //
 // Unit template energy (noise cells distributed as Exp(1)) is kept for the
 // taps as rounded to 16 bits: P is |F|^2 / E'_z with E'_z = sum_e |g'_z[e]|^2
@@ -48,16 +51,19 @@ constexpr int kTcZ = 28;                         // templates per chunk
 constexpr int kTcN = kTcZ * kTcPhases * 2;       // GEMM columns (224)
 constexpr int kTcSlab = kTcN / 8 * 256;          // bytes of B per K step of 16
 constexpr int kTcStages = 4;                     // spectrum-window ring
-constexpr int kTcEpiWarps = 8;
+constexpr int kTcEpiWarps = 16;
+constexpr int kTcZpt = kTcZ / (kTcEpiWarps / 4);   // templates per epilogue thread
+static_assert(kTcZ % (kTcEpiWarps / 4) == 0, "epilogue split");
 constexpr int kTcThreads = 32 * (2 + kTcEpiWarps);
 constexpr int kTcTmemCols = 512;
 constexpr int kTcAccStride = 256;                // TMEM column of accumulator 1
-constexpr int kTcEpiWeight = 6;                  // epilogue cost of a tile, in K steps
+constexpr int kTcEpiSteps = 11;                  // epilogue time of a tile, in MMA K steps
 constexpr size_t kTcMinSmem = 120 * 1024;        // keeps one CTA (and one TMEM owner) per SM
 
 // The (chunk, tile) items of CTA k of G: items are ordered chunk-major with
-// weight ks + kTcEpiWeight each, and CTA k takes those whose starting weight
-// falls in [k W / G, (k + 1) W / G).
+// weight max(ks, kTcEpiSteps) each (the MMAs of a tile overlap the epilogue
+// of the previous one, so a tile costs the longer of the two), and CTA k
+// takes those whose starting weight falls in [k W / G, (k + 1) W / G).
 struct TcSchedule {
     const TcChunk *ch;
     int n_ch;
@@ -66,14 +72,14 @@ struct TcSchedule {
     __device__ TcSchedule(const TcChunk *chunks, int n_ch_, int64_t n_tiles_, int k, int G)
         : ch(chunks), n_ch(n_ch_), n_tiles(n_tiles_), base(0), t(-1), c(0) {
         int64_t w = 0;
-        for (int i = 0; i < n_ch; ++i) w += chunks[i].ks + kTcEpiWeight;
+        for (int i = 0; i < n_ch; ++i) w += max(chunks[i].ks, kTcEpiSteps);
         const int64_t total = w * n_tiles;
         lo = total * k / G;
         hi = total * (k + 1) / G;
     }
     __device__ bool next(int &oc, int64_t &ot) {
         while (c < n_ch) {
-            const int64_t w = ch[c].ks + kTcEpiWeight;
+            const int64_t w = max(ch[c].ks, kTcEpiSteps);
             if (base >= hi) break;
             if (t < 0) t = lo > base ? (lo - base + w - 1) / w : 0;
             if (t < n_tiles && base + t * w < hi) {
@@ -215,17 +221,30 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             (void)mbar_wait(&drain, 0);
         }
     } else {
-        // epilogue: TMEM lanes 32 (warp % 4) .. + 31, column half (warp - 2) / 4
+        // epilogue: TMEM lanes 32 (warp % 4) .. + 31 (rows), templates
+        // kTcZpt part .. + kTcZpt - 1 of the chunk, part = (warp - 2) / 4
         const int quarter = warp & 3;
-        const int half = (warp - 2) >> 2;
+        const int part = (warp - 2) >> 2;
         const int row = 32 * quarter + lane;
-        const uint32_t tlane = tmem + ((uint32_t)(32 * quarter) << 16);
+        const uint32_t tlane = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(8 * kTcZpt * part);
         TcSchedule sch(chunks, n_ch, n_tiles, blockIdx.x, gridDim.x);
-        int c;
+        int c, cur = -1, zvalid = 0;
         int64_t t;
         int j = 0;
-        double s1 = 0.0, s2 = 0.0;
+        float sc[kTcZpt];
+        typename P::real *zrow = plane;
+        float2 s1 = make_float2(0.f, 0.f), s2 = make_float2(0.f, 0.f);
+        double d1 = 0.0, d2 = 0.0;
+        constexpr float ps = P::plane_scale;
         while (sch.next(c, t)) {
+            if (c != cur) {
+                cur = c;
+                const int zb = chunks[c].z_begin + kTcZpt * part;
+                zvalid = chunks[c].n_zc - kTcZpt * part;
+#pragma unroll
+                for (int k = 0; k < kTcZpt; ++k) sc[k] = k < zvalid ? __ldg(inv_energy + zb + k) : 0.f;
+                zrow = plane + (int64_t)zb * n_r + 4 * row;
+            }
             const int b = j & 1;
             const bool got = mbar_wait(&acc_full[b], (j >> 1) & 1);
             if (!__all_sync(0xffffffffu, got)) {
@@ -233,55 +252,52 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 break;
             }
             tc_fence_after();
-            const int z0 = chunks[c].z_begin, nzc = chunks[c].n_zc;
-            const int64_t r0 = t * kTcTile + 4 * row;
-            float f1 = 0.f, f2 = 0.f;
-#pragma unroll 1
-            for (int u = 0; u < kTcZ / 4; ++u) {
-                uint32_t v[16];
-                const int col = half * (kTcN / 2) + 16 * u;
-                tmem_ld16(tlane + (uint32_t)(b * kTcAccStride + col), v);
-                tmem_ld_wait();
+            uint32_t v[kTcZpt][8];
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int zz = half * (kTcZ / 2) + 2 * u + h;
-                    const float sc = zz < nzc ? __ldg(inv_energy + z0 + zz) : 0.f;
-                    float pw[4];
-#pragma unroll
-                    for (int p = 0; p < 4; ++p) {
-                        const float re = __uint_as_float(v[8 * h + 2 * p]);
-                        const float im = __uint_as_float(v[8 * h + 2 * p + 1]);
-                        pw[p] = fmaf(re, re, im * im) * sc;
-                        f1 += pw[p];
-                        f2 = fmaf(pw[p], pw[p], f2);
-                    }
-                    if (zz < nzc) {
-                        const typename P::cpx lo =
-                            P::st(make_float2(pw[0] * P::plane_scale, pw[1] * P::plane_scale));
-                        const typename P::cpx hi =
-                            P::st(make_float2(pw[2] * P::plane_scale, pw[3] * P::plane_scale));
-                        uint2 o;
-                        memcpy(&o.x, &lo, 4);
-                        memcpy(&o.y, &hi, 4);
-                        *reinterpret_cast<uint2 *>(plane + (int64_t)(z0 + zz) * n_r + r0) = o;
-                    }
-                }
-            }
-            s1 += (double)f1;
-            s2 += (double)f2;
+            for (int k = 0; k < kTcZpt; ++k)
+                tmem_ld8(tlane + (uint32_t)(b * kTcAccStride + 8 * k), v[k]);
+            tmem_ld_wait();
+            // the accumulator is in registers: hand it back to the MMA thread
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[b]);
+            typename P::real *o = zrow + t * kTcTile;
+#pragma unroll
+            for (int k = 0; k < kTcZpt; ++k) {
+                const float2 sk = make_float2(sc[k], sc[k]);
+                const float2 re01 = make_float2(__uint_as_float(v[k][0]), __uint_as_float(v[k][1]));
+                const float2 re23 = make_float2(__uint_as_float(v[k][2]), __uint_as_float(v[k][3]));
+                const float2 im01 = make_float2(__uint_as_float(v[k][4]), __uint_as_float(v[k][5]));
+                const float2 im23 = make_float2(__uint_as_float(v[k][6]), __uint_as_float(v[k][7]));
+                const float2 p01 = __fmul2_rn(__ffma2_rn(re01, re01, __fmul2_rn(im01, im01)), sk);
+                const float2 p23 = __fmul2_rn(__ffma2_rn(re23, re23, __fmul2_rn(im23, im23)), sk);
+                s1 = __fadd2_rn(s1, __fadd2_rn(p01, p23));
+                s2 = __ffma2_rn(p01, p01, s2);
+                s2 = __ffma2_rn(p23, p23, s2);
+                if (k < zvalid) {
+                    const typename P::cpx lo = P::st(ps == 1.f ? p01 : __fmul2_rn(p01, make_float2(ps, ps)));
+                    const typename P::cpx hi = P::st(ps == 1.f ? p23 : __fmul2_rn(p23, make_float2(ps, ps)));
+                    uint2 w;
+                    memcpy(&w.x, &lo, 4);
+                    memcpy(&w.y, &hi, 4);
+                    *reinterpret_cast<uint2 *>(o + (int64_t)k * n_r) = w;
+                }
+            }
+            // FP32 within a tile, FP64 across tiles
+            d1 += (double)s1.x + (double)s1.y;
+            d2 += (double)s2.x + (double)s2.y;
+            s1 = make_float2(0.f, 0.f);
+            s2 = make_float2(0.f, 0.f);
             ++j;
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
-            s1 += __shfl_down_sync(0xffffffffu, s1, off);
-            s2 += __shfl_down_sync(0xffffffffu, s2, off);
+            d1 += __shfl_down_sync(0xffffffffu, d1, off);
+            d2 += __shfl_down_sync(0xffffffffu, d2, off);
         }
         if (lane == 0) {
-            red[0][warp - 2] = s1;
-            red[1][warp - 2] = s2;
+            red[0][warp - 2] = d1;
+            red[1][warp - 2] = d2;
         }
     }
     if (!ok) atomicOr(flags, 2u);
@@ -304,7 +320,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
 // The template operand of every chunk, laid out exactly as the kernel's
 // shared-memory image: per K step a slab of [n-block 28][K core 2][row 8][8
-// values]; column n = 8 zz + 2 p + c, K element kk of step k is complex tap
+// values]; column n = 8 zz + 4 c + p, K element kk of step k is complex tap
 // q = 8 k + kk / 2, component kk % 2 (re, im).
 template <class P>
 __global__ void tc_bank_kernel(uint16_t *__restrict__ img, const TcChunk *__restrict__ chunks,
@@ -318,7 +334,7 @@ __global__ void tc_bank_kernel(uint16_t *__restrict__ img, const TcChunk *__rest
         const int k = (int)(i / (kTcSlab / 2));
         const int e_lin = (int)(i % (kTcSlab / 2));
         const int nb = e_lin / 128, cb = (e_lin / 64) & 1, rw = (e_lin / 8) & 7, kk8 = e_lin & 7;
-        const int zz = nb, p = rw >> 1, c = rw & 1;
+        const int zz = nb, c = rw >> 2, p = rw & 3;
         const int kk = 8 * cb + kk8;
         const int q = 8 * k + kk / 2, comp = kk & 1;
         double v = 0.0;
