@@ -333,6 +333,8 @@ def run_gpu(args, rank, world, local_rank, dist):
         ck = clocks.stop() if clocks else None
         ms = max_over_ranks(ev0.elapsed_time(ev1))
         prof = plan.profile() if profile else None
+        if profile:
+            plan.profile(False)
         joules = (e1 - e0) if (e0 is not None and e1 is not None) else None
         return ms, prof, joules, ck, nfound
 
@@ -342,8 +344,11 @@ def run_gpu(args, rank, world, local_rank, dist):
     plan = capi.Plan(N_SAMPLES, TSAMP, Z_MAX, Z_STEP, SEG_LEN, N_HARM, precision=capi.FDAS_BF16)
     info = plan.info
     clocks = ClockSampler(local_rank)
-    ms_bf16, prof_bf16, j_bf16, ck, nf_bf16 = timed(plan, xs, args.steps, args.warmup, True,
-                                                    energy, clocks)
+    # timed without tracing (tracing serialises the kernel groups on one
+    # stream); the per-kernel breakdown comes from one traced step after it
+    ms_bf16, _, j_bf16, ck, nf_bf16 = timed(plan, xs, args.steps, args.warmup, False, energy,
+                                            clocks)
+    _, prof_bf16, _, _, _ = timed(plan, xs, 1, 1, True)
     # --- e2e: the same calls with the series in pinned host memory ----------
     hosts = [x.cpu().pin_memory() for x in xs]
     ms_e2e, _, _, _, nf_e2e = timed(plan, hosts, args.steps, max(1, args.warmup // 2))
@@ -354,8 +359,8 @@ def run_gpu(args, rank, world, local_rank, dist):
     if not args.no_fp32:
         plan32 = capi.Plan(N_SAMPLES, TSAMP, Z_MAX, Z_STEP, SEG_LEN, N_HARM,
                            precision=capi.FDAS_FP32)
-        ms_fp32, prof_fp32, j_fp32, _, _ = timed(plan32, xs, args.steps, args.warmup, True,
-                                                 energy)
+        ms_fp32, _, j_fp32, _, _ = timed(plan32, xs, args.steps, args.warmup, False, energy)
+        _, prof_fp32, _, _, _ = timed(plan32, xs, 1, 1, True)
         plan32.close()
 
     # --- uneven batch: full-length and decimated series in one call, graph ---
@@ -415,7 +420,8 @@ def run_gpu(args, rank, world, local_rank, dist):
     roof = roof_of(dom)
     other = roof_of("harmonic" if dom == "correlate" else "correlate")
     alg_gbs = wm["alg_bytes"] * args.batch * args.steps / (ms_bf16 / 1000.0) / 1e9
-    launches = sum(prof_bf16[g][0] for g in groups)
+    # launches of one traced step (the same sequence as an untraced one)
+    launches = sum(prof_bf16[g][0] for g in groups) * args.steps
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_bf16 / args.steps, "higher_is_better": True,

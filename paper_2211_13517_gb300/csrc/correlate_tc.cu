@@ -96,6 +96,10 @@ struct TcSchedule {
     }
 };
 
+__device__ __forceinline__ float2 fsub2(float2 a, float2 b) {
+    return __fadd2_rn(a, make_float2(-b.x, -b.y));
+}
+
 template <class P>
 __global__ void __launch_bounds__(kTcThreads, 1)
     correlate_tc_kernel(const typename P::cpx *__restrict__ spec_pad,
@@ -234,7 +238,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         float sc[kTcZpt];
         typename P::real *zrow = plane;
         float2 s1 = make_float2(0.f, 0.f), s2 = make_float2(0.f, 0.f);
-        double d1 = 0.0, d2 = 0.0;
+        // compensated FP32 sums across tiles (FP64 only once, at the end: the
+        // FP64 pipe is a small fraction of the FP32 one)
+        float2 k1 = make_float2(0.f, 0.f), c1 = make_float2(0.f, 0.f);
+        float2 k2 = make_float2(0.f, 0.f), c2 = make_float2(0.f, 0.f);
         constexpr float ps = P::plane_scale;
         while (sch.next(c, t)) {
             if (c != cur) {
@@ -283,13 +290,21 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     *reinterpret_cast<uint2 *>(o + (int64_t)k * n_r) = w;
                 }
             }
-            // FP32 within a tile, FP64 across tiles
-            d1 += (double)s1.x + (double)s1.y;
-            d2 += (double)s2.x + (double)s2.y;
+            // FP32 within a tile, compensated FP32 across tiles
+            {
+                const float2 y1 = fsub2(s1, c1), t1 = __fadd2_rn(k1, y1);
+                c1 = fsub2(fsub2(t1, k1), y1);
+                k1 = t1;
+                const float2 y2 = fsub2(s2, c2), t2 = __fadd2_rn(k2, y2);
+                c2 = fsub2(fsub2(t2, k2), y2);
+                k2 = t2;
+            }
             s1 = make_float2(0.f, 0.f);
             s2 = make_float2(0.f, 0.f);
             ++j;
         }
+        double d1 = ((double)k1.x - (double)c1.x) + ((double)k1.y - (double)c1.y);
+        double d2 = ((double)k2.x - (double)c2.x) + ((double)k2.y - (double)c2.y);
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
             d1 += __shfl_down_sync(0xffffffffu, d1, off);
