@@ -324,21 +324,34 @@ struct DedupSteps {
             return 0u;
         }
     }
+    // the same for a CTA whose cells all lie inside the row: every span is
+    // the full padded length, a compile-time constant
+    static constexpr unsigned full_bytes(int J) { return (unsigned)(D::padlen(J) * sizeof(real)); }
+    static constexpr unsigned full_group_bytes(int G) {
+        unsigned b = 0;
+        for (int i = 0; i < H; ++i)
+            if (group_of(i) == G) b += full_bytes(j_at(H, i));
+        return b;
+    }
     // one thread: arm each stage's barrier with its byte count and issue the
-    // bulk copies of its harmonic spans
+    // bulk copies of its harmonic spans (source row iz0 + o_j of the top row
+    // iz0 + o, from bin j B / H on)
     template <int IDX>
-    __device__ __forceinline__ static void copy(const real *__restrict__ plane, const int64_t *rowoff,
-                                                int64_t n_r, int64_t B, real *sm, uint64_t *bars) {
+    __device__ __forceinline__ static void copy(const real *__restrict__ plane, int iz0, int o,
+                                                int64_t n_r, int64_t B, bool inside, real *sm,
+                                                uint64_t *bars) {
         if constexpr (IDX < H) {
             constexpr int J = j_at(H, IDX);
             constexpr int G = group_of(IDX);
             if constexpr (IDX == 0 || (IDX & (IDX - 1)) == 0)
-                mbar_arrive_expect_tx(&bars[G], group_bytes<0, G>(n_r, B));
-            const unsigned bytes = span_bytes<J>(n_r, B);
+                mbar_arrive_expect_tx(&bars[G], inside ? full_group_bytes(G)
+                                                        : group_bytes<0, G>(n_r, B));
+            const unsigned bytes = inside ? full_bytes(J) : span_bytes<J>(n_r, B);
+            const int64_t row = iz0 + src_off(H, o, J);
             if (bytes)
-                bulk_copy_g2s(sm + D::off(J), plane + rowoff[J - 1] + (int64_t)J * B / H, bytes,
+                bulk_copy_g2s(sm + D::off(J), plane + row * n_r + (int64_t)J * B / H, bytes,
                               &bars[G]);
-            copy<IDX + 1>(plane, rowoff, n_r, B, sm, bars);
+            copy<IDX + 1>(plane, iz0, o, n_r, B, inside, sm, bars);
         }
     }
 
@@ -414,17 +427,18 @@ __global__ void __launch_bounds__(Dedup<P, H>::T)
     extern __shared__ __align__(16) unsigned char dd_smem[];
     real *sm = reinterpret_cast<real *>(dd_smem);
     using Steps = DedupSteps<P, H>;
-    __shared__ int64_t rowoff[H];
     __shared__ __align__(8) uint64_t bars[Steps::NG];
     const int iz = blockIdx.y;
     const int64_t B = (int64_t)blockIdx.x * D::CELLS;
     const int t = threadIdx.x;
     if (t == 0) {
+        // barriers and every copy at once, before anything else (the copies
+        // themselves land within a fraction of a microsecond from L2)
         for (int g = 0; g < Steps::NG; ++g) mbar_init(&bars[g], 1);
         mbar_fence_init();
+        Steps::template copy<0>(plane, iz0, iz - iz0, n_r, B, B + D::CELLS <= n_r, sm, bars);
     }
-    hs_row_offsets<H>(iz0, iz, n_r, rowoff);   // ends with __syncthreads
-    if (t == 0) Steps::template copy<0>(plane, rowoff, n_r, B, sm, bars);
+    __syncthreads();   // the barriers are initialised
     // Thread 0 (cell B < n_r) waits for every stage's copies before it
     // exits, so the CTA's shared memory outlives all copies into it.
     const int64_t b = B + (int64_t)D::R * t;   // first cell of this thread
