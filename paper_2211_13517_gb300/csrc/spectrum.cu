@@ -9,9 +9,10 @@
 //     X_k = (Z_k + conj(Z_{M-k}))/2 - (i/2) W_N^k (Z_k - conj(Z_{M-k})),
 //
 // k in [0, M) (Z_M = Z_0), with X_0 set to 0.  The normalisation kernel then
-// takes blocks of B bins, sorts |X_k|^2 (bitonic, shared memory), takes the
-// median mu_b (block 0 without k = 0; the mean of the two middle values for
-// an even count) and stores X'_k = X_k sqrt(ln 2 / mu_b) at the plan's
+// takes blocks of B bins, selects the middle order statistics of |X_k|^2
+// (radix selection on their bit patterns, shared memory), takes the median
+// mu_b (block 0 without k = 0; the mean of the two middle values for an even
+// count) and stores X'_k = X_k sqrt(ln 2 / mu_b) at the plan's
 // precision: exponential noise has median ln 2 times its mean, so white noise
 // leaves with unit mean power.  Non-finite spectrum values raise a flag.
 #include "fdas_internal.cuh"
@@ -88,6 +89,67 @@ fdas_status fft_any(int L, const float2 *in, float2 *out, int n_cta, int64_t in_
 }
 
 constexpr int kNormThreads = 512;
+constexpr int kSelBins = 2048;   // radix-select digit of up to 11 bits
+
+// Rank `r` (0-based, ascending) among the n keys key[0..n) (non-negative
+// float bit patterns, so their order as unsigned integers is their order as
+// floats), by radix selection on digits of 11, 11 and 10 bits: each pass
+// counts the keys that share the prefix found so far per digit value,
+// scans the counts and keeps the digit whose range holds the rank.  All
+// threads of the CTA call it; returns the key (every thread gets it).
+__device__ uint32_t radix_select(const uint32_t *key, int n, int r, uint32_t *hist,
+                                 uint32_t *wsum, uint32_t *res) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint32_t prefix = 0u, mask = 0u;
+    int rr = r;
+#pragma unroll 1
+    for (int pass = 0; pass < 3; ++pass) {
+        const int shift = pass == 0 ? 21 : (pass == 1 ? 10 : 0);
+        const int nb = pass == 2 ? 1024 : 2048;
+        for (int i = tid; i < kSelBins; i += kNormThreads) hist[i] = 0u;
+        __syncthreads();
+        for (int i = tid; i < n; i += kNormThreads) {
+            const uint32_t k = key[i];
+            if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & (uint32_t)(nb - 1)], 1u);
+        }
+        __syncthreads();
+        // thread t owns the 4 consecutive bins 4t .. 4t+3
+        uint32_t c[4], local = 0u;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            c[q] = hist[4 * tid + q];
+            local += c[q];
+        }
+        uint32_t incl = local;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += v;
+        }
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        uint32_t base = incl - local;
+        for (int w = 0; w < warp; ++w) base += wsum[w];
+        if ((uint32_t)rr >= base && (uint32_t)rr < base + local) {
+            uint32_t before = base;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if ((uint32_t)rr >= before && (uint32_t)rr < before + c[q]) {
+                    res[0] = (uint32_t)(4 * tid + q);
+                    res[1] = before;
+                }
+                before += c[q];
+            }
+        }
+        __syncthreads();
+        const uint32_t digit = res[0], below = res[1];
+        prefix |= digit << shift;
+        mask |= (uint32_t)(nb - 1) << shift;
+        rr -= (int)below;
+        __syncthreads();   // res is rewritten by the next pass
+    }
+    return prefix;
+}
 
 // One CTA per normalisation block of B bins (B a power of two <= 8192).
 template <class P>
@@ -97,6 +159,9 @@ __global__ void __launch_bounds__(kNormThreads) normalise_kernel(
     extern __shared__ float smem[];
     float *key = smem;                       // [B]
     float2 *xs = (float2 *)(smem + B);       // [B]
+    __shared__ uint32_t hist[kSelBins];
+    __shared__ uint32_t wsum[kNormThreads / 32], res[2];
+    __shared__ uint32_t red_cnt[kNormThreads / 32], red_min[kNormThreads / 32];
     const int tid = threadIdx.x;
     const int64_t k0 = (int64_t)blockIdx.x * B;
     const int64_t N = 2 * M;
@@ -125,24 +190,37 @@ __global__ void __launch_bounds__(kNormThreads) normalise_kernel(
     __syncthreads();
     float f = 1.0f;
     if (median_mode == FDAS_NORM_MEDIAN) {
-        for (int k = 2; k <= B; k <<= 1) {
-            for (int j = k >> 1; j > 0; j >>= 1) {
-                for (int i = tid; i < B; i += kNormThreads) {
-                    const int ixj = i ^ j;
-                    if (ixj > i) {
-                        const bool up = (i & k) == 0;
-                        const float a = key[i], b = key[ixj];
-                        if ((a > b) == up) {
-                            key[i] = b;
-                            key[ixj] = a;
-                        }
-                    }
-                }
-                __syncthreads();
-            }
-        }
+        // the middle order statistics of |X_k|^2 by radix selection (the +inf
+        // key of k = 0 is the largest and never selected)
+        const uint32_t *ukey = reinterpret_cast<const uint32_t *>(key);
         const int cnt = (k0 == 0) ? B - 1 : B;
-        const float med = (cnt & 1) ? key[cnt / 2] : 0.5f * (key[cnt / 2 - 1] + key[cnt / 2]);
+        const int r_lo = (cnt & 1) ? cnt / 2 : cnt / 2 - 1;
+        const uint32_t lo = radix_select(ukey, B, r_lo, hist, wsum, res);
+        float med = __uint_as_float(lo);
+        if (!(cnt & 1)) {
+            // the next order statistic: lo again if it occurs at rank r_lo + 1,
+            // else the smallest key above lo
+            uint32_t n_le = 0u, m_gt = 0xffffffffu;
+            for (int i = tid; i < B; i += kNormThreads) {
+                const uint32_t k = ukey[i];
+                if (k <= lo) ++n_le;
+                else m_gt = min(m_gt, k);
+            }
+            n_le = __reduce_add_sync(0xffffffffu, n_le);
+            m_gt = __reduce_min_sync(0xffffffffu, m_gt);
+            if ((tid & 31) == 0) {
+                red_cnt[tid >> 5] = n_le;
+                red_min[tid >> 5] = m_gt;
+            }
+            __syncthreads();
+            uint32_t tot = 0u, mn = 0xffffffffu;
+            for (int w = 0; w < kNormThreads / 32; ++w) {
+                tot += red_cnt[w];
+                mn = min(mn, red_min[w]);
+            }
+            const uint32_t hi = tot >= (uint32_t)(r_lo + 2) ? lo : mn;
+            med = 0.5f * (__uint_as_float(lo) + __uint_as_float(hi));
+        }
         f = med > 0.f ? (float)sqrt(0.69314718055994530942 / (double)med) : 0.f;
         if (medians != nullptr && tid == 0) medians[blockIdx.x] = med;
     }
