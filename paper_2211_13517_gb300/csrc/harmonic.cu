@@ -228,22 +228,25 @@ __global__ void __launch_bounds__(kHsThreads)
 // ---------------------------------------------------------------------------
 // harmonic sum + threshold for H <= 16 with consecutive cells per thread.
 //
-// Thread t of a CTA owns the R = 16 consecutive cells b = B + 16 t + i of one
+// Thread t of a CTA owns the R = 16 consecutive cells b = B + 16 t + i of a
 // top row (B = the CTA's first cell, a multiple of 16 T).  Because 16 is a
 // multiple of H, harmonic j of cell i reads source bin
 //     j (B + 16 t)/H + d_i,   d_i = floor((i j + H/2)/H) <= DMAX_j,
 // so the thread needs only the DMAX_j + 1 consecutive bins starting at
 // j (B + 16 t)/H, and which of them each cell adds is a compile-time index.
-// The CTA (T = 128 threads, 2048 cells) copies, for every harmonic, the span
-// of its source row that all its threads need (starting at j B / H, a
-// multiple of 128 elements, so 16-byte aligned) into shared memory with one
-// bulk asynchronous copy per harmonic; the copies of each stage complete on
-// that stage's own mbarrier (bounded waits), so the sums of the first stages
-// run while the later spans are still arriving.  Each thread reads its
-// values with the widest aligned shared-memory loads and adds them to its
-// cells, in stage order, comparing each stage with its threshold.  Small
-// CTAs (about 35 KB of BF16 spans) keep six of them per SM in different
-// phases of copy and compute.
+// A CTA (T = 128 threads, 2048 cells) walks QROWS consecutive top rows.  For
+// each row thread 0 copies, for every harmonic whose source row differs from
+// the previous row's (for the first row, every harmonic), the span of the
+// source row that the CTA needs (starting at j B / H, a multiple of 128
+// elements, so 16-byte aligned) into that harmonic's place in shared memory
+// with one bulk asynchronous copy.  From one top row to the next, source row
+// o_j changes with probability j/H, so the walk copies about 30% fewer bytes
+// than copying every span for every row.  The copies of each stage complete
+// on that stage's own mbarrier (bounded waits; one phase per row), so the
+// first stages are summed while later spans are still arriving.  Each
+// thread reads its values with the widest aligned shared-memory loads, adds
+// them to its cells (16-bit planes: one mixed-precision add each), compares
+// each completed stage with its threshold and appends every crossing.
 // ---------------------------------------------------------------------------
 template <class P, int H>
 struct Dedup {
@@ -257,6 +260,10 @@ struct Dedup {
     static constexpr int padlen(int j) { return (len(j) + EPV - 1) / EPV * EPV; }
     static constexpr int off(int j) { return j <= 1 ? 0 : off(j - 1) + padlen(j - 1); }
     static constexpr int SMEM_ELEMS = off(H + 1);
+    // consecutive top rows one CTA walks: from a top row to the next, the
+    // source row o_j of harmonic j changes with probability j/H, and only the
+    // spans that change are copied again
+    static constexpr int QROWS = 16;
     // widest load (elements, power of two <= EPV) that the per-thread start
     // (R/H) j t is always aligned to
     static constexpr int width(int j) {
@@ -333,37 +340,63 @@ struct DedupSteps {
             if (group_of(i) == G) b += full_bytes(j_at(H, i));
         return b;
     }
-    // one thread: arm each stage's barrier with its byte count and issue the
-    // bulk copies of its harmonic spans (source row iz0 + o_j of the top row
-    // iz0 + o, from bin j B / H on)
+    // bit j - 1 set: harmonic j reads another source row for top row o than
+    // for top row o - 1 (every bit for the first row of a walk)
+    template <int J>
+    __device__ __forceinline__ static unsigned changed(int o, bool first) {
+        if constexpr (J <= H) {
+            const unsigned own =
+                (first || src_off(H, o, J) != src_off(H, o - 1, J)) ? (1u << (J - 1)) : 0u;
+            return own | changed<J + 1>(o, first);
+        } else {
+            return 0u;
+        }
+    }
+    template <int IDX, int G>
+    __device__ __forceinline__ static unsigned changed_bytes(int64_t n_r, int64_t B, bool inside,
+                                                             unsigned chg) {
+        if constexpr (IDX < H) {
+            constexpr int J = j_at(H, IDX);
+            unsigned own = 0u;
+            if constexpr (group_of(IDX) == G)
+                if ((chg >> (J - 1)) & 1u) own = inside ? full_bytes(J) : span_bytes<J>(n_r, B);
+            return own + changed_bytes<IDX + 1, G>(n_r, B, inside, chg);
+        } else {
+            return 0u;
+        }
+    }
+    // one thread, per top row: arm each stage's barrier with the bytes of its
+    // changed spans and copy them (source row iz0 + o_j of the top row
+    // iz0 + o, from bin j B / H on) over the previous row's spans
     template <int IDX>
     __device__ __forceinline__ static void copy(const real *__restrict__ plane, int iz0, int o,
-                                                int64_t n_r, int64_t B, bool inside, real *sm,
-                                                uint64_t *bars) {
+                                                int64_t n_r, int64_t B, bool inside, unsigned chg,
+                                                real *sm, uint64_t *bars) {
         if constexpr (IDX < H) {
             constexpr int J = j_at(H, IDX);
             constexpr int G = group_of(IDX);
             if constexpr (IDX == 0 || (IDX & (IDX - 1)) == 0)
-                mbar_arrive_expect_tx(&bars[G], inside ? full_group_bytes(G)
-                                                        : group_bytes<0, G>(n_r, B));
-            const unsigned bytes = inside ? full_bytes(J) : span_bytes<J>(n_r, B);
-            const int64_t row = iz0 + src_off(H, o, J);
-            if (bytes)
-                bulk_copy_g2s(sm + D::off(J), plane + row * n_r + (int64_t)J * B / H, bytes,
-                              &bars[G]);
-            copy<IDX + 1>(plane, iz0, o, n_r, B, inside, sm, bars);
+                mbar_arrive_expect_tx(&bars[G], changed_bytes<0, G>(n_r, B, inside, chg));
+            if ((chg >> (J - 1)) & 1u) {
+                const unsigned bytes = inside ? full_bytes(J) : span_bytes<J>(n_r, B);
+                const int64_t row = iz0 + src_off(H, o, J);
+                if (bytes)
+                    bulk_copy_g2s(sm + D::off(J), plane + row * n_r + (int64_t)J * B / H, bytes,
+                                  &bars[G]);
+            }
+            copy<IDX + 1>(plane, iz0, o, n_r, B, inside, chg, sm, bars);
         }
     }
 
     // add harmonic j_at(H, IDX) to the thread's cells; stage(s, S) at the end
     // of every stage.  False if a stage's copies did not land in time.
     template <int IDX, class F>
-    __device__ __forceinline__ static bool sums(const real *sm, uint64_t *bars, int t,
-                                                float2 (&S2)[D::R / 2], F &&stage) {
+    __device__ __forceinline__ static bool sums(const real *sm, uint64_t *bars, unsigned parity,
+                                                int t, float2 (&S2)[D::R / 2], F &&stage) {
         if constexpr (IDX < H) {
             constexpr int J = j_at(H, IDX);
             if constexpr (IDX == 0 || (IDX & (IDX - 1)) == 0)
-                if (!mbar_wait(&bars[group_of(IDX)], 0)) return false;
+                if (!mbar_wait(&bars[group_of(IDX)], parity)) return false;
             constexpr int NVAL = D::dmax(J) + 1;
             constexpr int W = D::width(J);
             constexpr int NLD = (NVAL + W - 1) / W;
@@ -408,7 +441,7 @@ struct DedupSteps {
                 }
             }
             if constexpr (((IDX + 1) & IDX) == 0) stage(ilog2h(IDX + 1), S2);
-            return sums<IDX + 1>(sm, bars, t, S2, stage);
+            return sums<IDX + 1>(sm, bars, parity, t, S2, stage);
         } else {
             return true;
         }
@@ -416,7 +449,7 @@ struct DedupSteps {
 };
 
 template <class P, int H, bool kWriteSums>
-__global__ void __launch_bounds__(Dedup<P, H>::T)
+__global__ void __launch_bounds__(Dedup<P, H>::T, 6)
     harmonic_dedup_kernel(const typename P::real *__restrict__ plane, int64_t n_r, int n_z,
                           int iz0, const TrialStats *__restrict__ st, uint32_t rank,
                           CandRec *__restrict__ cand, unsigned long long *__restrict__ count,
@@ -428,62 +461,86 @@ __global__ void __launch_bounds__(Dedup<P, H>::T)
     real *sm = reinterpret_cast<real *>(dd_smem);
     using Steps = DedupSteps<P, H>;
     __shared__ __align__(8) uint64_t bars[Steps::NG];
-    const int iz = blockIdx.y;
     const int64_t B = (int64_t)blockIdx.x * D::CELLS;
     const int t = threadIdx.x;
+    const int iz_begin = blockIdx.y * D::QROWS;
+    const int iz_end = min(iz_begin + D::QROWS, n_z);
+    const bool inside = B + D::CELLS <= n_r;
     if (t == 0) {
-        // barriers and every copy at once, before anything else (the copies
-        // themselves land within a fraction of a microsecond from L2)
         for (int g = 0; g < Steps::NG; ++g) mbar_init(&bars[g], 1);
         mbar_fence_init();
-        Steps::template copy<0>(plane, iz0, iz - iz0, n_r, B, B + D::CELLS <= n_r, sm, bars);
     }
-    __syncthreads();   // the barriers are initialised
-    // Thread 0 (cell B < n_r) waits for every stage's copies before it
-    // exits, so the CTA's shared memory outlives all copies into it.
     const int64_t b = B + (int64_t)D::R * t;   // first cell of this thread
-    if (b >= n_r) return;
+    const bool active = b < n_r;   // thread 0 always is
     const float inv = 1.0f / P::plane_scale;
-    float2 S2[D::R / 2];
+    bool failed = false;
+    int q = 0;
+    for (int iz = iz_begin; iz < iz_end; ++iz, ++q) {
+        // every thread is done with the previous row's spans (and, for the
+        // first row, the barriers are initialised); stop together after a
+        // wait that gave up
+        if (__syncthreads_or(failed)) {
+            failed = true;
+            break;
+        }
+        if (t == 0) {
+            // the spans whose source row changed, over the previous row's
+            // (their reads by this CTA's threads come before the copies)
+            fence_proxy_async_smem();
+            const unsigned chg = Steps::template changed<1>(iz - iz0, q == 0);
+            Steps::template copy<0>(plane, iz0, iz - iz0, n_r, B, inside, chg, sm, bars);
+        }
+        if (!active) continue;
+        float2 S2[D::R / 2];
 #pragma unroll
-    for (int c = 0; c < D::R / 2; ++c) S2[c] = make_float2(0.f, 0.f);
-    const bool ok = Steps::template sums<0>(sm, bars, t, S2, [&](int s, float2 (&Sv)[D::R / 2]) {
-        if constexpr (kWriteSums) {
+        for (int c = 0; c < D::R / 2; ++c) S2[c] = make_float2(0.f, 0.f);
+        const bool ok = Steps::template sums<0>(sm, bars, (unsigned)(q & 1), t, S2,
+                                                [&](int s, float2 (&Sv)[D::R / 2]) {
+            if constexpr (kWriteSums) {
 #pragma unroll
-            for (int c = 0; c < D::R / 2; ++c) {
-                float *o = sums_out + ((int64_t)s * n_z + iz) * n_r + b + 2 * c;
-                o[0] = Sv[c].x * inv;
-                o[1] = Sv[c].y * inv;
-            }
-        } else {
-            const float th = st->thr[s];
-            float m = fmaxf(Sv[0].x, Sv[0].y);
+                for (int c = 0; c < D::R / 2; ++c) {
+                    float *o = sums_out + ((int64_t)s * n_z + iz) * n_r + b + 2 * c;
+                    o[0] = Sv[c].x * inv;
+                    o[1] = Sv[c].y * inv;
+                }
+            } else {
+                const float th = st->thr[s];
+                // largest of the 16 sums: they are >= 0, so their bit patterns
+                // order as signed integers (3-input integer max, 8 steps)
+                int mi = __vimax3_s32(__float_as_int(Sv[0].x), __float_as_int(Sv[0].y),
+                                      __float_as_int(Sv[1].x));
+                mi = __vimax3_s32(mi, __float_as_int(Sv[1].y), __float_as_int(Sv[2].x));
 #pragma unroll
-            for (int c = 1; c < D::R / 2; ++c) m = fmaxf(m, fmaxf(Sv[c].x, Sv[c].y));
-            if (m * inv > th) {
+                for (int c = 2; c < D::R / 2 - 1; ++c)
+                    mi = __vimax3_s32(mi, __float_as_int(Sv[c].y), __float_as_int(Sv[c + 1].x));
+                mi = max(mi, __float_as_int(Sv[D::R / 2 - 1].y));
+                const float m = __int_as_float(mi);
+                if (m * inv > th) {
 #pragma unroll
-                for (int i = 0; i < D::R; ++i) {
-                    const float val = ((i & 1) ? Sv[i / 2].y : Sv[i / 2].x) * inv;
-                    if (val > th) {
-                        const unsigned long long idx = atomicAdd(count, 1ull);
-                        if ((int64_t)idx < cap) {
-                            CandRec rec;
-                            rec.key = cand_key(rank, s, iz, (uint32_t)(b + i));
-                            rec.power = val;
-                            rec.pad = 0.f;
-                            cand[idx] = rec;
+                    for (int i = 0; i < D::R; ++i) {
+                        const float val = ((i & 1) ? Sv[i / 2].y : Sv[i / 2].x) * inv;
+                        if (val > th) {
+                            const unsigned long long idx = atomicAdd(count, 1ull);
+                            if ((int64_t)idx < cap) {
+                                CandRec rec;
+                                rec.key = cand_key(rank, s, iz, (uint32_t)(b + i));
+                                rec.power = val;
+                                rec.pad = 0.f;
+                                cand[idx] = rec;
+                            }
                         }
                     }
                 }
             }
-        }
-    });
-    if (!ok) {
-        atomicOr(flags, 2u);
+        });
+        if (!ok) failed = true;
+    }
+    if (__syncthreads_or(failed)) {
+        if (t == 0) atomicOr(flags, 2u);
         // copies still in flight must land before the CTA's shared memory
-        // is released (each wait bounded)
-        if (t == 0)
-            for (int g = 0; g < Steps::NG; ++g) (void)mbar_wait(&bars[g], 0);
+        // is released (each wait bounded): those of the last row issued
+        if (t == 0 && q > 0)
+            for (int g = 0; g < Steps::NG; ++g) (void)mbar_wait(&bars[g], (unsigned)((q - 1) & 1));
     }
 }
 
@@ -622,7 +679,8 @@ fdas_status launch_dedup(Plan &p, const void *plane, const TrialStats *st, uint3
     const size_t smem = sizeof(typename P::real) * (size_t)D::SMEM_ELEMS;
     auto k = harmonic_dedup_kernel<P, H, kWriteSums>;
     FDAS_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    dim3 grid((unsigned)((p.n_r + D::CELLS - 1) / D::CELLS), p.n_z);
+    dim3 grid((unsigned)((p.n_r + D::CELLS - 1) / D::CELLS),
+              (unsigned)((p.n_z + D::QROWS - 1) / D::QROWS));
     k<<<grid, D::T, smem, s>>>((const typename P::real *)plane, p.n_r, p.n_z, p.iz0, st, rank,
                                p.cand, p.cand_count, p.max_cands, sums_out, p.flags);
     FDAS_CUDA_TRY(cudaGetLastError());
