@@ -23,19 +23,24 @@
 namespace fdas {
 namespace {
 
-// Strided FFT of length L per CTA: input element n of CTA c at
+// Strided FFTs of length L, W per CTA: input element n of transform c at
 // in[c*in_cs + n*in_es], output element k to out[c*out_cs + k*out_es],
-// multiplied by W_tw^{c k} when tw_m > 0.
-template <int L>
-__global__ void __launch_bounds__(L / 16) fft_strided_kernel(const float2 *__restrict__ in,
-                                                             float2 *__restrict__ out,
-                                                             int64_t in_cs, int64_t in_es,
-                                                             int64_t out_cs, int64_t out_es,
-                                                             int64_t tw_m) {
+// multiplied by W_tw^{c k} when tw_m > 0.  Thread i of the CTA works on
+// transform W blockIdx + i % W as its thread i / W, so that with in_cs = 1
+// (or out_cs = 1) a warp's strided accesses touch W consecutive elements of
+// each of 32 / W rows instead of one element per 32-byte sector.
+template <int L, int W>
+__global__ void __launch_bounds__(W * (L / 16)) fft_strided_kernel(const float2 *__restrict__ in,
+                                                                   float2 *__restrict__ out,
+                                                                   int64_t in_cs, int64_t in_es,
+                                                                   int64_t out_cs, int64_t out_es,
+                                                                   int64_t tw_m) {
     using F = CtaFft<L, -1>;
-    extern __shared__ float2 buf[];
-    const int tid = threadIdx.x;
-    const int64_t c = blockIdx.x;
+    extern __shared__ float2 smem_fft[];
+    const int g = threadIdx.x % W;
+    const int tid = threadIdx.x / W;
+    const int64_t c = (int64_t)blockIdx.x * W + g;
+    float2 *buf = smem_fft + g * F::SMEM_ELEMS;
     float2 v[16];
 #pragma unroll
     for (int r = 0; r < 16; ++r) v[r] = in[c * in_cs + (int64_t)(tid + r * (L / 16)) * in_es];
@@ -61,15 +66,29 @@ __global__ void __launch_bounds__(L / 16) fft_strided_kernel(const float2 *__res
         }
 }
 
+template <int L, int W>
+fdas_status launch_fft_w(const float2 *in, float2 *out, int n_cta, int64_t in_cs, int64_t in_es,
+                         int64_t out_cs, int64_t out_es, int64_t tw_m, cudaStream_t s) {
+    const size_t smem = sizeof(float2) * W * CtaFft<L, -1>::SMEM_ELEMS;
+    FDAS_CUDA_TRY(cudaFuncSetAttribute(fft_strided_kernel<L, W>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    fft_strided_kernel<L, W><<<n_cta / W, W * (L / 16), smem, s>>>(in, out, in_cs, in_es, out_cs,
+                                                                     out_es, tw_m);
+    FDAS_CUDA_TRY(cudaGetLastError());
+    return FDAS_OK;
+}
+
+// two transforms per CTA where the count allows (the strided passes of the
+// four-step split come in powers of two; two measured faster than four,
+// which limits the SM to one 512-thread CTA)
 template <int L>
 fdas_status launch_fft(const float2 *in, float2 *out, int n_cta, int64_t in_cs, int64_t in_es,
                        int64_t out_cs, int64_t out_es, int64_t tw_m, cudaStream_t s) {
-    const size_t smem = sizeof(float2) * CtaFft<L, -1>::SMEM_ELEMS;
-    FDAS_CUDA_TRY(cudaFuncSetAttribute(fft_strided_kernel<L>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    fft_strided_kernel<L><<<n_cta, L / 16, smem, s>>>(in, out, in_cs, in_es, out_cs, out_es, tw_m);
-    FDAS_CUDA_TRY(cudaGetLastError());
-    return FDAS_OK;
+    if constexpr (L <= 4096) {
+        if (n_cta % 2 == 0)
+            return launch_fft_w<L, 2>(in, out, n_cta, in_cs, in_es, out_cs, out_es, tw_m, s);
+    }
+    return launch_fft_w<L, 1>(in, out, n_cta, in_cs, in_es, out_cs, out_es, tw_m, s);
 }
 
 fdas_status fft_any(int L, const float2 *in, float2 *out, int n_cta, int64_t in_cs, int64_t in_es,
