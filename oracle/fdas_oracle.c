@@ -188,6 +188,71 @@ void oracle_harmonic_at(const double *P, int64_t n_r, int iz0, int H,
         out[c] = stage_sum(P, n_r, iz0, H, 1 << st[c], iz[c], ir[c]);
 }
 
+/*
+ * Fundamental-indexed harmonic sums (the variant in which a candidate is
+ * labelled by its fundamental): S_h(iz, ir) = sum_{k=1..h} P[iz0 + k o][k ir],
+ * o = iz - iz0, defined where every harmonic k <= h lies in the plane:
+ * h ir <= n_r - 1 and 0 <= iz0 + h o < n_z.
+ */
+static int fund_in_domain(int64_t n_r, int n_z, int iz0, int h, int iz, int64_t ir)
+{
+    const int64_t top = (int64_t)iz0 + (int64_t)h * (iz - iz0);
+    return ir * h <= n_r - 1 && top >= 0 && top < n_z;
+}
+
+static double fund_sum(const double *P, int64_t n_r, int iz0, int h, int iz, int64_t ir)
+{
+    const int o = iz - iz0;
+    double s = 0.0;
+    for (int k = 1; k <= h; ++k)
+        s += P[(int64_t)(iz0 + k * o) * n_r + (int64_t)k * ir];
+    return s;
+}
+
+/* S[st][iz][ir] (0 outside the stage's domain). */
+void oracle_fund_planes(const double *P, int64_t n_r, int n_z, int iz0, int H, double *S)
+{
+    int n_st = 0;
+    while ((1 << n_st) <= H)
+        ++n_st;
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int st = 0; st < n_st; ++st)
+        for (int iz = 0; iz < n_z; ++iz)
+            for (int64_t ir = 0; ir < n_r; ++ir)
+                S[((int64_t)st * n_z + iz) * n_r + ir] =
+                    fund_in_domain(n_r, n_z, iz0, 1 << st, iz, ir)
+                        ? fund_sum(P, n_r, iz0, 1 << st, iz, ir) : 0.0;
+}
+
+/* Every in-domain (stage, iz, ir) with S_h > lo[st], in (iz, st, ir) order;
+ * returns the count, stores the first `cap`. */
+int64_t oracle_fund_cells(const double *P, int64_t n_r, int n_z, int iz0, int H,
+                          const double *lo, int64_t cap, int32_t *out_st,
+                          int32_t *out_iz, int64_t *out_ir, double *out_s)
+{
+    int n_st = 0;
+    while ((1 << n_st) <= H)
+        ++n_st;
+    int64_t total = 0;
+    for (int iz = 0; iz < n_z; ++iz)
+        for (int st = 0; st < n_st; ++st)
+            for (int64_t ir = 0; ir < n_r; ++ir) {
+                if (!fund_in_domain(n_r, n_z, iz0, 1 << st, iz, ir))
+                    continue;
+                const double v = fund_sum(P, n_r, iz0, 1 << st, iz, ir);
+                if (v > lo[st]) {
+                    if (total < cap) {
+                        out_st[total] = st;
+                        out_iz[total] = iz;
+                        out_ir[total] = ir;
+                        out_s[total] = v;
+                    }
+                    ++total;
+                }
+            }
+    return total;
+}
+
 /* Number of OpenMP threads the loops above use (for reporting). */
 int oracle_threads(void)
 {

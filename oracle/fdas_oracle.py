@@ -29,7 +29,9 @@ paper and follows the stated readings):
 5. ``plane_stats``   mean and population standard deviation of P over the
                      whole n_z x N_r plane.
 6. ``harmonic_*``    top-harmonic-indexed sums S_h, h = 1, 2, 4, ..., H
-                     (C loop in fdas_oracle.c).
+                     (C loop in fdas_oracle.c); ``fund_planes`` the variant
+                     labelled by the fundamental, S_h = sum_{k<=h} P at the
+                     exact multiples (k o, k ir), in its domain.
 7. ``thresholds``    S_h > T_h with T_h = mean * Q^-1(h, Phibar(sigma))
                      (Gamma(h,1) tail at the Gaussian-equivalent false-alarm
                      probability of `sigma`), or T_h = h*mean + sigma*sqrt(h)*std.
@@ -96,6 +98,10 @@ def _c():
         lib.oracle_harmonic_cells.restype = i64
         lib.oracle_harmonic_at.argtypes = [P, i64, i32, i32, i64, P, P, P, P]
         lib.oracle_harmonic_at.restype = None
+        lib.oracle_fund_planes.argtypes = [P, i64, i32, i32, i32, P]
+        lib.oracle_fund_planes.restype = None
+        lib.oracle_fund_cells.argtypes = [P, i64, i32, i32, i32, P, i64, P, P, P, P]
+        lib.oracle_fund_cells.restype = i64
         lib.oracle_threads.argtypes = []
         lib.oracle_threads.restype = i32
         _lib = lib
@@ -299,6 +305,27 @@ def harmonic_planes(P: np.ndarray, geom: Geometry) -> np.ndarray:
     return S
 
 
+# fundamental-indexed variant: the candidate is labelled by its fundamental
+# (iz, ir) and harmonic k reads the exact multiple (iz0 + k o, k ir); stage h
+# is defined where every k <= h lies inside the plane (h ir <= N_r - 1 and
+# |h o| <= K)
+TOP_HARMONIC, FUNDAMENTAL = 0, 1
+
+
+def fund_domain(geom: Geometry, h: int, iz: int, ir: int) -> bool:
+    o = iz - geom.iz0
+    return ir * h <= geom.n_r - 1 and 0 <= geom.iz0 + h * o < geom.n_z
+
+
+def fund_planes(P: np.ndarray, geom: Geometry) -> np.ndarray:
+    """S[st][iz][ir] = sum_{k<=h} P[iz0 + k o][k ir] in the stage's domain, 0
+    outside it, for every stage h = 2^st <= H."""
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    S = np.empty((len(geom.stages),) + P.shape, dtype=np.float64)
+    _c().oracle_fund_planes(_ptr(P), P.shape[1], P.shape[0], geom.iz0, geom.n_harm, _ptr(S))
+    return S
+
+
 def harmonic_at(P: np.ndarray, geom: Geometry, st, iz, ir) -> np.ndarray:
     P = np.ascontiguousarray(P, dtype=np.float64)
     st = np.ascontiguousarray(np.asarray(st, dtype=np.int32))
@@ -361,10 +388,11 @@ CAND_DTYPE = np.dtype([("trial", np.uint32), ("harm", np.int32), ("iz", np.int32
 
 def candidates(P: np.ndarray, geom: Geometry, mean: float, std: float,
                sigma: float = 6.0, mode: int = GAMMA_TAIL, trial: int = 0,
-               guard: float = 0.0, cap: int = 1 << 22):
+               guard: float = 0.0, cap: int = 1 << 22, harmonic_mode: int = TOP_HARMONIC):
     """(candidates, guard_cells).
 
-    candidates: every (h, iz, ir) with S_h > T_h, sorted by (trial, h, iz, ir).
+    candidates: every (h, iz, ir) with S_h > T_h, sorted by (trial, h, iz, ir)
+    (top-harmonic sums, or fundamental-indexed sums in their domain).
     guard_cells: the cells with |S_h - T_h| <= guard * T_h (same dtype),
     where a rounding difference may flip the decision.
     """
@@ -375,9 +403,9 @@ def candidates(P: np.ndarray, geom: Geometry, mean: float, std: float,
     out_iz = np.empty(cap, dtype=np.int32)
     out_ir = np.empty(cap, dtype=np.int64)
     out_s = np.empty(cap, dtype=np.float64)
-    n = _c().oracle_harmonic_cells(_ptr(P), P.shape[1], P.shape[0], geom.iz0,
-                                   geom.n_harm, _ptr(lo), cap, _ptr(out_st),
-                                   _ptr(out_iz), _ptr(out_ir), _ptr(out_s))
+    cells = _c().oracle_fund_cells if harmonic_mode == FUNDAMENTAL else _c().oracle_harmonic_cells
+    n = cells(_ptr(P), P.shape[1], P.shape[0], geom.iz0, geom.n_harm, _ptr(lo), cap,
+              _ptr(out_st), _ptr(out_iz), _ptr(out_ir), _ptr(out_s))
     if n > cap:
         raise RuntimeError(f"oracle candidate buffer too small ({n} > {cap})")
     st, iz, ir, s = out_st[:n], out_iz[:n], out_ir[:n], out_s[:n]
@@ -422,7 +450,7 @@ def fourier_power(Xn: np.ndarray, r: float, z: float):
 def search(x: np.ndarray, z_max: float, z_step: float, n_harm: int,
            sigma: float = 6.0, mode: int = GAMMA_TAIL, norm: str = "median",
            norm_block: int = 2048, trial: int = 0, guard: float = 0.0,
-           bank: Bank | None = None):
+           bank: Bank | None = None, harmonic_mode: int = TOP_HARMONIC):
     """Run steps 1-8 on one series; returns a dict of every intermediate."""
     geom = geometry(x.shape[0], z_max, z_step, n_harm)
     X = spectrum(x)
@@ -431,7 +459,8 @@ def search(x: np.ndarray, z_max: float, z_step: float, n_harm: int,
         bank = template_bank(geom)
     P = power_plane(Xn, bank)
     mean, std = plane_stats(P)
-    cands, guards = candidates(P, geom, mean, std, sigma, mode, trial, guard)
+    cands, guards = candidates(P, geom, mean, std, sigma, mode, trial, guard,
+                               harmonic_mode=harmonic_mode)
     return dict(geom=geom, X=X, Xn=Xn, medians=meds, bank=bank, P=P,
                 mean=mean, std=std, T=thresholds(n_harm, sigma, mode, mean, std),
                 candidates=cands, guard=guards)

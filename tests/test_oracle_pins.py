@@ -305,6 +305,70 @@ def test_harmonic_sum_brute_force_small():
 
 
 # --------------------------------------------------------------------------
+# fundamental-indexed harmonic sum (variant)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("H", [1, 2, 4, 8, 16])
+def test_fundamental_sums_equal_top_harmonic_sums_at_multiple_cells(H):
+    """At a top cell whose offsets are h times a fundamental's, top-harmonic
+    stage h reads harmonics j = k H/h at (k o_f, k r_f) with no rounding: the
+    same cells the fundamental-indexed stage h sums.  Pins the variant to the
+    independently written top-harmonic oracle."""
+    g = O.geometry(2048, 40.0, 1.0, H)
+    rng = np.random.default_rng(H)
+    P = rng.random((g.n_z, g.n_r))
+    top = O.harmonic_planes(P, g)
+    fund = O.fund_planes(P, g)
+    n = 0
+    for st, h in enumerate(g.stages):
+        for o in range(-(g.iz0 // h), g.iz0 // h + 1):
+            for rf in range(0, (g.n_r - 1) // h + 1, 7):
+                assert fund[st, g.iz0 + o, rf] == top[st, g.iz0 + h * o, h * rf]
+                n += 1
+    assert n > 100
+
+
+@pytest.mark.parametrize("H", [2, 8, 16])
+def test_fundamental_domain_size_closed_form(H):
+    """Stage h is defined on ceil(N_r / h) bins x (2 floor(K / h) + 1) rows;
+    outside it the sums are 0 and no cell is ever a candidate."""
+    g = O.geometry(1024, 20.0, 1.0, H)
+    P = np.ones((g.n_z, g.n_r))
+    S = O.fund_planes(P, g)
+    for st, h in enumerate(g.stages):
+        inside = S[st] > 0
+        assert inside.sum() == -(-g.n_r // h) * (2 * (g.iz0 // h) + 1)
+        assert np.all(S[st][inside] == h)          # constant plane: S_h = h
+    # candidates (a low threshold, so there are many) lie in their stage's
+    # domain and carry the stage sum
+    R = np.random.default_rng(H).exponential(size=(g.n_z, g.n_r))
+    SR = O.fund_planes(R, g)
+    m, sd = O.plane_stats(R)
+    c, _ = O.candidates(R, g, m, sd, sigma=1.0, harmonic_mode=O.FUNDAMENTAL)
+    assert len(c) > 1000
+    for rec in c[::37]:
+        h = int(rec["harm"])
+        st = g.stages.index(h)
+        assert O.fund_domain(g, h, int(rec["iz"]), int(rec["ir"]))
+        assert rec["power"] == SR[st, rec["iz"], rec["ir"]]
+
+
+@pytest.mark.parametrize("of", [3, -2, 0])
+def test_fundamental_sum_spike_train(of):
+    """Spikes 2^k at the exact multiples (k o_f, k r_f): stage h at the
+    fundamental is 2^1 + ... + 2^h, and stage 1 is the plane."""
+    H = 16
+    g = O.geometry(4096, 48.0, 1.0, H)
+    rf = 97
+    P = np.zeros((g.n_z, g.n_r))
+    for k in range(1, H + 1):
+        P[g.iz0 + k * of, k * rf] += 2.0 ** k
+    S = O.fund_planes(P, g)
+    assert np.array_equal(S[0], P)
+    for st, h in enumerate(g.stages):
+        assert S[st][g.iz0 + of, rf] == sum(2.0 ** k for k in range(1, h + 1))
+
+
+# --------------------------------------------------------------------------
 # thresholds
 # --------------------------------------------------------------------------
 def test_gamma_tail_factors_closed_form():
