@@ -63,6 +63,15 @@ enum { FDAS_NORM_MEDIAN = 0, FDAS_NORM_NONE = 1 };
  *   FDAS_FP16 only, with m_overlap <= 112, i.e. z_max <= 208);
  * FDAS_CORR_AUTO: TENSOR where it applies, else FFT. */
 enum { FDAS_CORR_AUTO = 0, FDAS_CORR_FFT = 1, FDAS_CORR_TENSOR = 2 };
+/* harmonic sum:
+ * FDAS_HARM_TOP (default): top-harmonic indexed, every plane cell (ir, iz) is
+ *   the top harmonic; harmonic j of H reads the rounded sub-multiple
+ *   (iz0 + sign(o) floor((|o| j + H/2)/H), floor((ir j + H/2)/H));
+ * FDAS_HARM_FUNDAMENTAL: a candidate is labelled by its fundamental (ir, iz)
+ *   and stage h sums the exact multiples P[iz0 + k o][k ir], k = 1..h, on the
+ *   cells where every multiple lies in the plane (h ir <= N_r - 1,
+ *   |h o| <= K); fewer gathers and additions, a different candidate list. */
+enum { FDAS_HARM_TOP = 0, FDAS_HARM_FUNDAMENTAL = 1 };
 
 typedef struct {
     int32_t precision;       /* FDAS_FP32 (default), FDAS_BF16, FDAS_FP16          */
@@ -79,7 +88,7 @@ typedef struct {
                                 series, a non-default stream); 0 (default): direct */
     int32_t correlator;      /* FDAS_CORR_AUTO (default), _FFT or _TENSOR; asking
                                 for _TENSOR where it does not apply is FDAS_ERR_ARG */
-    int32_t reserved;        /* 0 */
+    int32_t harmonic_mode;   /* FDAS_HARM_TOP (default) or FDAS_HARM_FUNDAMENTAL */
 } fdas_opts;
 
 /* One dedispersed time series (one DM trial).  `data` points to n_samples
@@ -120,7 +129,7 @@ typedef struct {
     int32_t use_graph;
     double tuned_ms;          /* autotune: correlation time per series (ms), else 0 */
     int32_t correlator;       /* FDAS_CORR_FFT or FDAS_CORR_TENSOR, as built    */
-    int32_t reserved;
+    int32_t harmonic_mode;    /* FDAS_HARM_TOP or FDAS_HARM_FUNDAMENTAL         */
 } fdas_plan_info;
 
 typedef struct fdas_plan fdas_plan;

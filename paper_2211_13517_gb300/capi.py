@@ -36,6 +36,7 @@ FDAS_FP32, FDAS_BF16, FDAS_FP16 = 0, 1, 2
 FDAS_THRESH_GAMMA_TAIL, FDAS_THRESH_MEAN_PLUS_KSIGMA = 0, 1
 FDAS_NORM_MEDIAN, FDAS_NORM_NONE = 0, 1
 FDAS_CORR_AUTO, FDAS_CORR_FFT, FDAS_CORR_TENSOR = 0, 1, 2
+FDAS_HARM_TOP, FDAS_HARM_FUNDAMENTAL = 0, 1
 
 EXPORTED = ["fdas_opts_default", "fdas_plan_create", "fdas_plan_destroy",
             "fdas_plan_get_info", "fdas_search", "fdas_spectrum", "fdas_power_plane",
@@ -50,7 +51,7 @@ class fdas_opts(Structure):
                 ("threshold_mode", c_int32), ("norm_mode", c_int32),
                 ("norm_block", c_int32), ("max_candidates", c_int64),
                 ("autotune", c_int32), ("use_graph", c_int32),
-                ("correlator", c_int32), ("reserved", c_int32)]
+                ("correlator", c_int32), ("harmonic_mode", c_int32)]
 
 
 class fdas_series(Structure):
@@ -76,7 +77,7 @@ class fdas_plan_info(Structure):
                 ("tsamp", c_double), ("z_max", c_double), ("z_step", c_double),
                 ("threshold_sigma", c_double), ("stage_factor", c_double * 6),
                 ("workspace_bytes", c_int64), ("z_chunks", c_int32), ("use_graph", c_int32),
-                ("tuned_ms", c_double), ("correlator", c_int32), ("reserved", c_int32)]
+                ("tuned_ms", c_double), ("correlator", c_int32), ("harmonic_mode", c_int32)]
 
 
 class fdas_seed(Structure):
@@ -303,7 +304,7 @@ class Plan:
                  n_harm=16, precision=FDAS_FP32, threshold_sigma=6.0,
                  threshold_mode=FDAS_THRESH_GAMMA_TAIL, norm_mode=FDAS_NORM_MEDIAN,
                  norm_block=2048, max_candidates=1 << 20, autotune=False, use_graph=False,
-                 correlator=None):
+                 correlator=None, harmonic_mode=FDAS_HARM_TOP):
         o = fdas_opts_default()
         o.precision = precision
         o.threshold_sigma = threshold_sigma
@@ -315,6 +316,7 @@ class Plan:
         o.use_graph = 1 if use_graph else 0
         if correlator is not None:
             o.correlator = correlator
+        o.harmonic_mode = harmonic_mode
         self.handle = fdas_plan_create(n_samples, tsamp, z_max, z_step, seg_len, n_harm, o)
         self.info = fdas_plan_get_info(self.handle)
 

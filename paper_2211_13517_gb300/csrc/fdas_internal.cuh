@@ -161,6 +161,7 @@ struct Plan {
     cudaGraphExec_t graph_exec = nullptr;   // last captured batch
     double tuned_ms = 0.0;
     int correlator = FDAS_CORR_FFT;   // FDAS_CORR_FFT or FDAS_CORR_TENSOR
+    int harm_mode = FDAS_HARM_TOP;    // FDAS_HARM_TOP or FDAS_HARM_FUNDAMENTAL
     // tensor-core correlation: template chunks, their operand images and the
     // spectrum window each GEMM tile reads (complex elements)
     TcChunk *tc_chunks = nullptr;

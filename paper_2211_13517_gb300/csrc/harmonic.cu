@@ -717,16 +717,187 @@ fdas_status launch_hs(Plan &p, const void *plane, const TrialStats *st, uint32_t
     return FDAS_OK;
 }
 
+// ---------------------------------------------------------------------------
+// fundamental-indexed harmonic sum (FDAS_HARM_FUNDAMENTAL).  Thread per
+// kFundR = 4 consecutive fundamentals ir = a .. a + 3 of one row o.  Stage 1
+// is the cells themselves; stage h adds the exact multiples
+// P[iz0 + k o][k ir], k = h/2 + 1 .. h, on the cells where every multiple of
+// the stage lies in the plane (h ir <= N_r - 1, |h o| <= K; the domain only
+// shrinks as h grows).  For harmonic k the thread loads the contiguous run of
+// 4k bins k a .. k (a + 4) - 1 with vector loads (the runs of consecutive
+// lanes are adjacent, so the warp reads one contiguous range) and adds its
+// every k-th element; cells at the domain's edge take a checked scalar path.
+// FP32 sums in the order k = 1, 2, ...
+// ---------------------------------------------------------------------------
+constexpr int kFundThreads = 256;
+constexpr int kFundR = 4;
+
+// the 32-bit words of n bytes at p (16-byte loads when p is 16-byte aligned)
+template <int NBYTES>
+__device__ __forceinline__ void load_words(const void *p, uint32_t *w, bool aligned16) {
+    static_assert(NBYTES % 8 == 0, "8-byte multiples");
+    if (aligned16 && NBYTES % 16 == 0) {
+#pragma unroll
+        for (int q = 0; q < NBYTES / 16; ++q) {
+            const uint4 u = __ldg(reinterpret_cast<const uint4 *>(p) + q);
+            w[4 * q] = u.x;
+            w[4 * q + 1] = u.y;
+            w[4 * q + 2] = u.z;
+            w[4 * q + 3] = u.w;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < NBYTES / 8; ++q) {
+            const uint2 u = __ldg(reinterpret_cast<const uint2 *>(p) + q);
+            w[2 * q] = u.x;
+            w[2 * q + 1] = u.y;
+        }
+    }
+}
+
+// element e of the words (16-bit or 32-bit values) as FP32
+template <class P>
+__device__ __forceinline__ float word_value(const uint32_t *w, int e) {
+    if constexpr (sizeof(typename P::real) == 2) {
+        const uint32_t x = w[e >> 1];
+        const unsigned short h = (unsigned short)((e & 1) ? (x >> 16) : (x & 0xffffu));
+        typename P::real r;
+        memcpy(&r, &h, 2);
+        return P::ldr(r);
+    } else {
+        return __uint_as_float(w[e]);
+    }
+}
+
+template <class P, int K>
+__device__ __forceinline__ void fund_add_run(const typename P::real *row, int64_t a,
+                                             float (&S)[kFundR]) {
+    using real = typename P::real;
+    constexpr int NBYTES = K * kFundR * (int)sizeof(real);
+    uint32_t w[NBYTES / 4];
+    const real *p = row + (int64_t)K * a;
+    load_words<NBYTES>(p, w, (reinterpret_cast<uintptr_t>(p) & 15u) == 0);
+#pragma unroll
+    for (int i = 0; i < kFundR; ++i) S[i] += word_value<P>(w, K * i);
+}
+
+template <class P, int KLO, int KHI>
+__device__ __forceinline__ void fund_add_stage(const typename P::real *plane, int64_t n_r,
+                                               int iz0, int o, int64_t a, bool full, int h,
+                                               float (&S)[kFundR]) {
+    if constexpr (KLO <= KHI) {
+        const typename P::real *row = plane + (int64_t)(iz0 + KLO * o) * n_r;
+        if (full) {
+            fund_add_run<P, KLO>(row, a, S);
+        } else {
+#pragma unroll
+            for (int i = 0; i < kFundR; ++i)
+                if ((a + i) * h <= n_r - 1) S[i] += P::ldr(row[(int64_t)KLO * (a + i)]);
+        }
+        fund_add_stage<P, KLO + 1, KHI>(plane, n_r, iz0, o, a, full, h, S);
+    }
+}
+
+template <class P, int H, int SV, class F>
+__device__ __forceinline__ bool fund_stages(const typename P::real *plane, int64_t n_r, int n_z,
+                                            int iz0, int o, int64_t a, float (&S)[kFundR],
+                                            int &done, const F &emit) {
+    if constexpr ((1 << SV) <= H) {
+        constexpr int h = 1 << SV;
+        if constexpr (SV > 0) {
+            const int top = iz0 + h * o;
+            if (top < 0 || top >= n_z || a * h > n_r - 1) return true;
+            const bool full = (a + kFundR) * h <= n_r;
+            fund_add_stage<P, h / 2 + 1, h>(plane, n_r, iz0, o, a, full, h, S);
+        }
+#pragma unroll
+        for (int i = 0; i < kFundR; ++i)
+            if ((a + i) * h <= n_r - 1) emit(SV, i, S[i]);
+        done = SV + 1;
+        return fund_stages<P, H, SV + 1, F>(plane, n_r, n_z, iz0, o, a, S, done, emit);
+    } else {
+        return true;
+    }
+}
+
+template <class P, int H, bool kWriteSums>
+__global__ void __launch_bounds__(kFundThreads)
+    harmonic_fund_kernel(const typename P::real *__restrict__ plane, int64_t n_r, int n_z,
+                         int iz0, const TrialStats *__restrict__ st, uint32_t rank,
+                         CandRec *__restrict__ cand, unsigned long long *__restrict__ count,
+                         int64_t cap, float *__restrict__ sums_out) {
+    const int64_t a = ((int64_t)blockIdx.x * kFundThreads + threadIdx.x) * kFundR;
+    const int iz = blockIdx.y;
+    if (a >= n_r) return;   // n_r is a multiple of 4: a .. a + 3 are all inside
+    const int o = iz - iz0;
+    const float inv = 1.0f / P::plane_scale;
+    float S[kFundR];
+#pragma unroll
+    for (int i = 0; i < kFundR; ++i) S[i] = 0.f;
+    // stage 1 is k = 1: the run of the cells themselves
+    fund_add_run<P, 1>(plane + (int64_t)iz * n_r, a, S);
+    int done = 0;
+    auto emit = [&](int sv, int i, float sum) {
+        const float val = sum * inv;
+        if constexpr (kWriteSums) {
+            sums_out[((int64_t)sv * n_z + iz) * n_r + a + i] = val;
+        } else {
+            if (val > st->thr[sv]) {
+                const unsigned long long idx = atomicAdd(count, 1ull);
+                if ((int64_t)idx < cap) {
+                    CandRec rec;
+                    rec.key = cand_key(rank, sv, iz, (uint32_t)(a + i));
+                    rec.power = val;
+                    rec.pad = 0.f;
+                    cand[idx] = rec;
+                }
+            }
+        }
+    };
+    fund_stages<P, H, 0>(plane, n_r, n_z, iz0, o, a, S, done, emit);
+    if constexpr (kWriteSums) {
+        // 0 for the stages (and cells) outside the domain
+        constexpr int NS = ilog2h(H) + 1;
+        for (int sv = 1; sv < NS; ++sv) {
+            const int h = 1 << sv;
+            const int top = iz0 + h * o;
+            for (int i = 0; i < kFundR; ++i)
+                if (sv >= done || top < 0 || top >= n_z || (a + i) * h > n_r - 1)
+                    sums_out[((int64_t)sv * n_z + iz) * n_r + a + i] = 0.f;
+        }
+    }
+}
+
+template <class P, int H, bool kWriteSums>
+fdas_status launch_fund(Plan &p, const void *plane, const TrialStats *st, uint32_t rank,
+                        float *sums_out, cudaStream_t s) {
+    const int64_t per_cta = (int64_t)kFundThreads * kFundR;
+    dim3 grid((unsigned)((p.n_r + per_cta - 1) / per_cta), p.n_z);
+    harmonic_fund_kernel<P, H, kWriteSums><<<grid, kFundThreads, 0, s>>>(
+        (const typename P::real *)plane, p.n_r, p.n_z, p.iz0, st, rank, p.cand, p.cand_count,
+        p.max_cands, sums_out);
+    FDAS_CUDA_TRY(cudaGetLastError());
+    return FDAS_OK;
+}
+
+template <class P, int H, bool kWriteSums>
+fdas_status launch_hs_mode(Plan &p, const void *plane, const TrialStats *st, uint32_t rank,
+                           float *sums_out, cudaStream_t s) {
+    if (p.harm_mode == FDAS_HARM_FUNDAMENTAL)
+        return launch_fund<P, H, kWriteSums>(p, plane, st, rank, sums_out, s);
+    return launch_hs<P, H, kWriteSums>(p, plane, st, rank, sums_out, s);
+}
+
 template <class P, bool kWriteSums>
 fdas_status launch_hs_P(Plan &p, const void *plane, const TrialStats *st, uint32_t rank,
                         float *sums_out, cudaStream_t s) {
     switch (p.H) {
-        case 1: return launch_hs<P, 1, kWriteSums>(p, plane, st, rank, sums_out, s);
-        case 2: return launch_hs<P, 2, kWriteSums>(p, plane, st, rank, sums_out, s);
-        case 4: return launch_hs<P, 4, kWriteSums>(p, plane, st, rank, sums_out, s);
-        case 8: return launch_hs<P, 8, kWriteSums>(p, plane, st, rank, sums_out, s);
-        case 16: return launch_hs<P, 16, kWriteSums>(p, plane, st, rank, sums_out, s);
-        case 32: return launch_hs<P, 32, kWriteSums>(p, plane, st, rank, sums_out, s);
+        case 1: return launch_hs_mode<P, 1, kWriteSums>(p, plane, st, rank, sums_out, s);
+        case 2: return launch_hs_mode<P, 2, kWriteSums>(p, plane, st, rank, sums_out, s);
+        case 4: return launch_hs_mode<P, 4, kWriteSums>(p, plane, st, rank, sums_out, s);
+        case 8: return launch_hs_mode<P, 8, kWriteSums>(p, plane, st, rank, sums_out, s);
+        case 16: return launch_hs_mode<P, 16, kWriteSums>(p, plane, st, rank, sums_out, s);
+        case 32: return launch_hs_mode<P, 32, kWriteSums>(p, plane, st, rank, sums_out, s);
         default: set_error("bad n_harm"); return FDAS_ERR_ARG;
     }
 }

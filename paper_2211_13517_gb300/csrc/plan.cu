@@ -218,6 +218,8 @@ static fdas_status create(Plan *&out, int64_t n_samples, double tsamp, double z_
     if (o->correlator != FDAS_CORR_AUTO && o->correlator != FDAS_CORR_FFT &&
         o->correlator != FDAS_CORR_TENSOR)
         return arg_error("unknown correlator");
+    if (o->harmonic_mode != FDAS_HARM_TOP && o->harmonic_mode != FDAS_HARM_FUNDAMENTAL)
+        return arg_error("unknown harmonic_mode");
 
     Plan *pp = new (std::nothrow) Plan();
     if (!pp) return arg_error("out of host memory");
@@ -237,6 +239,7 @@ static fdas_status create(Plan *&out, int64_t n_samples, double tsamp, double z_
     p.thr_mode = o->threshold_mode;
     p.sigma = o->threshold_sigma;
     p.max_cands = o->max_candidates;
+    p.harm_mode = o->harmonic_mode;
     for (int s = 0; s < 6; ++s) p.G[s] = s < p.n_stages ? gamma_tail_factor(1 << s, p.sigma) : 0.0;
 
     // template half-widths m(z) = 8 + ceil(|z|/2) on the exact grid
@@ -872,7 +875,7 @@ fdas_status fdas_plan_get_info(const fdas_plan *plan, fdas_plan_info *info) {
     info->use_graph = p.use_graph ? 1 : 0;
     info->tuned_ms = p.tuned_ms;
     info->correlator = p.correlator;
-    info->reserved = 0;
+    info->harmonic_mode = p.harm_mode;
     return FDAS_OK;
 }
 
