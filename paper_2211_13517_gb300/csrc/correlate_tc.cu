@@ -59,6 +59,7 @@ constexpr int kTcTmemCols = 512;
 constexpr int kTcAccStride = 256;                // TMEM column of accumulator 1
 constexpr int kTcEpiSteps = 11;                  // epilogue time of a tile, in MMA K steps
 constexpr size_t kTcMinSmem = 120 * 1024;        // keeps one CTA (and one TMEM owner) per SM
+constexpr int kTcCtasPerSm = 1;                  // persistent CTAs per SM
 
 // The (chunk, tile) items of CTA k of G: items are ordered chunk-major with
 // weight max(ks, kTcEpiSteps) each (the MMAs of a tile overlap the epilogue
@@ -467,7 +468,13 @@ bool tc_applicable(const Plan &p, std::string *why) {
 
 int correlate_tc_ctas(const Plan &p) {
     const int64_t items = (p.n_r / kTcTile) * (int64_t)p.tc_n_ch;
-    return (int)std::max<int64_t>(1, std::min<int64_t>(p.n_sms, items));
+    return (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)kTcCtasPerSm * p.n_sms, items));
+}
+
+int64_t tc_bank_bytes(const std::vector<TcChunk> &table) {
+    int64_t b = 0;
+    for (const TcChunk &c : table) b = std::max<int64_t>(b, c.b_off + (int64_t)c.ks * kTcSlab);
+    return b;
 }
 
 fdas_status launch_tc_bank(Plan &p, cudaStream_t s) {

@@ -230,6 +230,7 @@ fdas_status launch_tc_bank(Plan &p, cudaStream_t s);
 fdas_status launch_correlate_tc(Plan &p, const void *spec_padded, void *plane, double2 *partials,
                                 cudaStream_t s);
 int correlate_tc_ctas(const Plan &p);
+int64_t tc_bank_bytes(const std::vector<TcChunk> &table);
 fdas_status launch_finalize_stats(Plan &p, const double2 *partials, int n_partials,
                                   const double *given_stats, TrialStats *out,
                                   cudaStream_t s);

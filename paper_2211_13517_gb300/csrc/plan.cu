@@ -282,7 +282,7 @@ static fdas_status create(Plan *&out, int64_t n_samples, double tsamp, double z_
     p.n_zchunk = choose_zchunks(p, p.n_sms);
     // partials serve every length the plan accepts (N, N/2, ..., 2^10) and
     // any template chunking up to 32
-    p.partials_cap = std::max<int64_t>((int64_t)p.n_seg * 32, p.n_sms);
+    p.partials_cap = std::max<int64_t>((int64_t)p.n_seg * 32, 4 * (int64_t)p.n_sms);
     for (int64_t n = n_samples; n >= (1 << 10); n /= 2) {
         Plan v = p;
         set_length(v, n);
@@ -373,8 +373,7 @@ static fdas_status create(Plan *&out, int64_t n_samples, double tsamp, double z_
     PLAN_CUDA(cudaMemcpy(p.tap_m, m.data(), sizeof(int32_t) * p.n_z, cudaMemcpyHostToDevice));
     PLAN_TRY(launch_template_bank(p, p.aux));
     if (p.correlator == FDAS_CORR_TENSOR) {
-        int64_t img = 0;
-        for (const TcChunk &c : tc_table) img = std::max<int64_t>(img, c.b_off + (int64_t)c.ks * 7168);
+        const int64_t img = tc_bank_bytes(tc_table);
         PLAN_TRY(dalloc(p, &p.tc_chunks, sizeof(TcChunk) * tc_table.size()));
         PLAN_TRY(dalloc(p, &p.tc_bank, (size_t)img));
         PLAN_TRY(dalloc(p, &p.tc_inv_energy, sizeof(float) * (size_t)p.n_z));
