@@ -87,10 +87,13 @@ def test_batch_rejects_lengths_the_plan_cannot_take(capi):
     plan.close()
 
 
-def test_graph_replay_equals_direct_launches(capi, uneven):
+@pytest.mark.parametrize("prec", [0, 1])
+def test_graph_replay_equals_direct_launches(capi, uneven, prec):
+    """FP32 (FFT correlator) and BF16 (tensor-core correlator) batches
+    captured into a CUDA graph give the direct launches' candidates."""
     lengths, xs, ids, refs = uneven
-    direct = capi.Plan(NMAX, 64e-6, ZMAX, ZSTEP, L, H)
-    graph = capi.Plan(NMAX, 64e-6, ZMAX, ZSTEP, L, H, use_graph=True)
+    direct = capi.Plan(NMAX, 64e-6, ZMAX, ZSTEP, L, H, precision=prec)
+    graph = capi.Plan(NMAX, 64e-6, ZMAX, ZSTEP, L, H, use_graph=True, precision=prec)
     assert graph.info.use_graph == 1
     side = torch.cuda.Stream()
     batches = [[torch.from_numpy(x).cuda() for x in xs],
@@ -102,9 +105,26 @@ def test_graph_replay_equals_direct_launches(capi, uneven):
         st_d, cd, nf_d = direct.search(dev, trial_ids=ids)
         assert st_g == st_d == capi.FDAS_OK
         assert nf_g == nf_d and cg.tolist() == cd.tolist(), rnd
-    _check(graph.search(batches[0], trial_ids=ids, stream=side)[1], refs[1e-4], 1e-4, 1e-4)
+    if prec == 0:
+        _check(graph.search(batches[0], trial_ids=ids, stream=side)[1], refs[1e-4], 1e-4, 1e-4)
+    else:
+        _check(graph.search(batches[0], trial_ids=ids, stream=side)[1], refs[0.03], 0.03, 0.03)
     direct.close()
     graph.close()
+
+
+def test_uneven_batch_fundamental_harmonic(capi, uneven):
+    """The fundamental-indexed harmonic sum on decimated series (each series
+    its own N_r and domain), BF16 storage, against the oracle."""
+    lengths, xs, ids, _ = uneven
+    refs = [O.search(x, ZMAX, ZSTEP, H, trial=t, guard=0.03, harmonic_mode=O.FUNDAMENTAL)
+            for x, t in zip(xs, ids)]
+    plan = capi.Plan(NMAX, 64e-6, ZMAX, ZSTEP, L, H, precision=capi.FDAS_BF16,
+                     harmonic_mode=capi.FDAS_HARM_FUNDAMENTAL)
+    st, cands, nf = plan.search([torch.from_numpy(x).cuda() for x in xs], trial_ids=ids)
+    assert st == capi.FDAS_OK and nf == len(cands)
+    _check(cands, refs, 0.03, 0.03)
+    plan.close()
 
 
 def test_autotuned_plan(capi, uneven):
