@@ -23,7 +23,7 @@
 // 208 KB, once per chunk) and the spectrum windows (A, a ring of 4) into shared
 // memory; warp 1 (one thread) issues the tcgen05 MMAs (M = 128, N = 224, K = 16
 // each, BF16 or FP16 operands, FP32 accumulators) into one of two TMEM
-// accumulators; warps 2..17 read the finished accumulator (tcgen05.ld, all
+// accumulators; warps 2..9 read the finished accumulator (tcgen05.ld, all
 // loads of a tile before one wait, then release the accumulator at once),
 // form P = re^2 + im^2 with packed FP32x2 arithmetic (the column order puts
 // the re and the im parts of the 4 phases side by side), store 4 consecutive
@@ -51,7 +51,7 @@ constexpr int kTcZ = 28;                         // templates per chunk
 constexpr int kTcN = kTcZ * kTcPhases * 2;       // GEMM columns (224)
 constexpr int kTcSlab = kTcN / 8 * 256;          // bytes of B per K step of 16
 constexpr int kTcStages = 4;                     // spectrum-window ring
-constexpr int kTcEpiWarps = 16;
+constexpr int kTcEpiWarps = 8;
 constexpr int kTcZpt = kTcZ / (kTcEpiWarps / 4);   // templates per epilogue thread
 static_assert(kTcZ % (kTcEpiWarps / 4) == 0, "epilogue split");
 constexpr int kTcThreads = 32 * (2 + kTcEpiWarps);
@@ -203,11 +203,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     kofs = chunks[c].kofs;
                 }
                 const int s = j % kTcStages, b = j & 1;
-                if (!mbar_wait(&a_full[s], (j / kTcStages) & 1)) {
+                if (!mbar_test(&a_full[s], (j / kTcStages) & 1) &&
+                    !mbar_wait(&a_full[s], (j / kTcStages) & 1)) {
                     ok = false;
                     break;
                 }
-                if (j >= 2 && !mbar_wait(&acc_empty[b], ((j >> 1) - 1) & 1)) {
+                if (j >= 2 && !mbar_test(&acc_empty[b], ((j >> 1) - 1) & 1) &&
+                    !mbar_wait(&acc_empty[b], ((j >> 1) - 1) & 1)) {
                     ok = false;
                     break;
                 }

@@ -64,6 +64,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned phase) {
     return ok != 0;
 }
 
+// non-blocking probe of the given phase (cheaper than try_wait when the
+// phase is usually complete already)
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, unsigned phase) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
 // wait for the given phase of the barrier; false once `limit` clock cycles
 // have passed without it
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned phase,
