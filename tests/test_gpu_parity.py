@@ -310,6 +310,21 @@ def test_search_low_precision_within_three_percent(capi, prec, corr):
     plan.close()
 
 
+@pytest.mark.parametrize("H,prec", [(32, 0), (32, 1), (16, 2), (2, 1)])
+def test_search_other_harmonic_counts(capi, H, prec):
+    """Whole searches with H = 32 (the direct gather kernel), H = 16 at FP16
+    and H = 2, against the oracle (FP32: 1e-4 guard; 16-bit: 3%)."""
+    n = 1 << 16
+    x, _ = S.pulsar_series(n, seed=21, height=1.0, z_abs=14.0)
+    guard = 1e-4 if prec == 0 else 0.03
+    ref = O.search(x, 16.0, 2.0, H, guard=guard)
+    plan = _plan(capi, n, 16.0, 2.0, 2048, H, precision=prec)
+    st, cands, nf = plan.search([torch.from_numpy(x).cuda()], capacity=1 << 18)
+    assert st == capi.FDAS_OK and nf == len(cands) and nf > 0
+    _compare_cands(cands, ref["candidates"], ref["guard"], rel_power=guard)
+    plan.close()
+
+
 def test_batch_order_host_input_and_reuse(capi):
     n = 1 << 15
     xs, refs = [], []
