@@ -30,20 +30,31 @@
 #include <stdlib.h>
 #include <string.h>
 
-/* One cell of the direct correlation.  g holds 2m+1 taps, g[e+m] = g_z[e]. */
-static double cell_power(const double *xr, const double *xi, int64_t n_r,
-                         int64_t r, int m, const double *gr, const double *gi)
+/* One cell of the direct correlation, F = (*fr, *fi).  g holds 2m+1 taps,
+ * g[e+m] = g_z[e]. */
+static void cell_corr(const double *xr, const double *xi, int64_t n_r, int64_t r,
+                      int m, const double *gr, const double *gi, double *fr,
+                      double *fi)
 {
-    double fr = 0.0, fi = 0.0;
+    double sr = 0.0, si = 0.0;
     for (int e = -m; e <= m; ++e) {
         int64_t k = r - e;
         if (k < 0 || k >= n_r)
             continue;
         double ar = xr[k], ai = xi[k];
         double br = gr[e + m], bi = gi[e + m];
-        fr += ar * br - ai * bi;
-        fi += ar * bi + ai * br;
+        sr += ar * br - ai * bi;
+        si += ar * bi + ai * br;
     }
+    *fr = sr;
+    *fi = si;
+}
+
+static double cell_power(const double *xr, const double *xi, int64_t n_r,
+                         int64_t r, int m, const double *gr, const double *gi)
+{
+    double fr, fi;
+    cell_corr(xr, xi, n_r, r, m, gr, gi, &fr, &fi);
     return fr * fr + fi * fi;
 }
 
@@ -66,6 +77,19 @@ void oracle_plane(const double *xr, const double *xi, int64_t n_r, int n_z,
                     cell_power(xr, xi, n_r, r, m[iz], gr + goff[iz], gi + goff[iz]);
         }
     }
+}
+
+/* The complex correlation plane F[iz][r] = (Fr, Fi), laid out as P above
+ * (the input of interbinning, which needs F at neighbouring bins). */
+void oracle_corr_plane(const double *xr, const double *xi, int64_t n_r, int n_z,
+                       const int32_t *m, const int64_t *goff, const double *gr,
+                       const double *gi, double *Fr, double *Fi)
+{
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int iz = 0; iz < n_z; ++iz)
+        for (int64_t r = 0; r < n_r; ++r)
+            cell_corr(xr, xi, n_r, r, m[iz], gr + goff[iz], gi + goff[iz],
+                      Fr + (int64_t)iz * n_r + r, Fi + (int64_t)iz * n_r + r);
 }
 
 /* The same sum at an explicit list of cells (sampled checks at full size). */

@@ -36,6 +36,11 @@ paper and follows the stated readings):
                      (Gamma(h,1) tail at the Gaussian-equivalent false-alarm
                      probability of `sigma`), or T_h = h*mean + sigma*sqrt(h)*std.
 8. ``candidates``    every cell above threshold, sorted by (trial, h, iz, ir).
+   ``interbin_plane`` (option) the plane on a half-bin grid from the complex
+                     correlation F: column 2r holds |F(r)|^2 and column 2r + 1
+                     the interbinned power (pi/4)^2 |F(r) - F(r+1)|^2, with
+                     F(N_r) = 0 beyond the last bin; stats, harmonic sums and
+                     candidates then run on that 2 N_r-column plane.
 9. ``fourier_power`` the off-grid power used to refine candidates:
                      F(r, z) = sum_k X'_k conj(rho(r - k, z)) over the bins
                      within 32 + ceil(|z|/2) of round(r), unnormalised rho,
@@ -89,6 +94,8 @@ def _c():
         i64, i32 = ctypes.c_int64, ctypes.c_int32
         lib.oracle_plane.argtypes = [P, P, i64, i32, P, P, P, P, P]
         lib.oracle_plane.restype = None
+        lib.oracle_corr_plane.argtypes = [P, P, i64, i32, P, P, P, P, P, P]
+        lib.oracle_corr_plane.restype = None
         lib.oracle_cells.argtypes = [P, P, i64, P, P, P, P, i64, P, P, P]
         lib.oracle_cells.restype = None
         lib.oracle_harmonic_planes.argtypes = [P, i64, i32, i32, i32, P]
@@ -263,6 +270,39 @@ def power_plane(Xn: np.ndarray, bank: Bank) -> np.ndarray:
     P = np.empty((bank.geom.n_z, n_r), dtype=np.float64)
     _c().oracle_plane(_ptr(xr), _ptr(xi), n_r, bank.geom.n_z, _ptr(m),
                       _ptr(offs), _ptr(gr), _ptr(gi), _ptr(P))
+    return P
+
+
+def correlation_plane(Xn: np.ndarray, bank: Bank) -> np.ndarray:
+    """F[iz][r] = sum_e X'_{r-e} g_z[e] over the whole plane (complex, FP64)."""
+    n_r = Xn.shape[0]
+    xr = np.ascontiguousarray(Xn.real)
+    xi = np.ascontiguousarray(Xn.imag)
+    gr, gi, offs, m = _flat_taps(bank)
+    Fr = np.empty((bank.geom.n_z, n_r), dtype=np.float64)
+    Fi = np.empty((bank.geom.n_z, n_r), dtype=np.float64)
+    _c().oracle_corr_plane(_ptr(xr), _ptr(xi), n_r, bank.geom.n_z, _ptr(m),
+                           _ptr(offs), _ptr(gr), _ptr(gi), _ptr(Fr), _ptr(Fi))
+    return Fr + 1j * Fi
+
+
+# Interbinning: the response half-way between two bins estimated from the
+# complex values at the two bins.  For a sinusoid exactly between bins k and
+# k + 1 (rho(1/2, 0) = 2i/pi, rho(-1/2, 0) = -2i/pi) the difference
+# F(k) - F(k+1) is 4/pi times the full response, hence the factor pi/4 on the
+# amplitude, (pi/4)^2 on the power.
+INTERBIN_POWER = (math.pi / 4.0) ** 2
+
+
+def interbin_plane(F: np.ndarray) -> np.ndarray:
+    """P[iz][c] on the half-bin grid c = 0 .. 2 N_r - 1 (r = c / 2):
+    P[iz][2r] = |F(r)|^2, P[iz][2r+1] = (pi/4)^2 |F(r) - F(r+1)|^2, F(N_r) = 0."""
+    n_z, n_r = F.shape
+    Fnext = np.zeros_like(F)
+    Fnext[:, :-1] = F[:, 1:]
+    P = np.empty((n_z, 2 * n_r), dtype=np.float64)
+    P[:, 0::2] = np.abs(F) ** 2
+    P[:, 1::2] = INTERBIN_POWER * np.abs(F - Fnext) ** 2
     return P
 
 
@@ -450,14 +490,17 @@ def fourier_power(Xn: np.ndarray, r: float, z: float):
 def search(x: np.ndarray, z_max: float, z_step: float, n_harm: int,
            sigma: float = 6.0, mode: int = GAMMA_TAIL, norm: str = "median",
            norm_block: int = 2048, trial: int = 0, guard: float = 0.0,
-           bank: Bank | None = None, harmonic_mode: int = TOP_HARMONIC):
-    """Run steps 1-8 on one series; returns a dict of every intermediate."""
+           bank: Bank | None = None, harmonic_mode: int = TOP_HARMONIC,
+           interbin: bool = False):
+    """Run steps 1-8 on one series; returns a dict of every intermediate.
+    With interbin, P is the 2 N_r-column half-bin plane and candidate ir
+    values are half-bin columns (r = ir / 2)."""
     geom = geometry(x.shape[0], z_max, z_step, n_harm)
     X = spectrum(x)
     Xn, meds = normalise(X, norm_block, norm)
     if bank is None:
         bank = template_bank(geom)
-    P = power_plane(Xn, bank)
+    P = interbin_plane(correlation_plane(Xn, bank)) if interbin else power_plane(Xn, bank)
     mean, std = plane_stats(P)
     cands, guards = candidates(P, geom, mean, std, sigma, mode, trial, guard,
                                harmonic_mode=harmonic_mode)

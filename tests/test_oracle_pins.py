@@ -395,6 +395,99 @@ def test_mean_plus_ksigma_threshold():
 
 
 # --------------------------------------------------------------------------
+# interbinning (half-bin grid from the complex correlation)
+# --------------------------------------------------------------------------
+def _rho0(q):
+    """rho(q, 0) = (exp(2 pi i q) - 1) / (2 pi i q), rho(0, 0) = 1."""
+    q = np.asarray(q, dtype=np.float64)
+    out = np.ones(q.shape, dtype=np.complex128)
+    nz = q != 0
+    out[nz] = (np.exp(2j * np.pi * q[nz]) - 1.0) / (2j * np.pi * q[nz])
+    return out
+
+
+def test_correlation_plane_squared_is_the_power_plane():
+    g = _small_geom()
+    Xn, _ = O.normalise(O.spectrum(S.white_noise(g.n_samples, 5)), 512)
+    bank = O.template_bank(g)
+    F = O.correlation_plane(Xn, bank)
+    P = O.power_plane(Xn, bank)
+    assert F.shape == P.shape
+    assert np.max(np.abs(np.abs(F) ** 2 - P)) < 1e-12 * np.max(P)
+
+
+def test_interbin_brute_force_small():
+    rng = np.random.default_rng(3)
+    F = rng.standard_normal((3, 7)) + 1j * rng.standard_normal((3, 7))
+    P = O.interbin_plane(F)
+    assert P.shape == (3, 14)
+    for iz in range(3):
+        for c in range(14):
+            r = c // 2
+            if c % 2 == 0:
+                ref = abs(F[iz, r]) ** 2
+            else:
+                nxt = F[iz, r + 1] if r + 1 < 7 else 0.0
+                ref = (math.pi / 4) ** 2 * abs(F[iz, r] - nxt) ** 2
+            assert abs(P[iz, c] - ref) <= 1e-14 * max(1.0, ref)
+
+
+@pytest.mark.parametrize("k0", [100, 777, 2046])
+def test_interbin_half_bin_tone_closed_form(k0):
+    """X_k = c rho(k0 + 1/2 - k, 0): the half-bin column 2 k0 + 1 recovers |c|^2
+    exactly (the z = 0 template is the unit impulse), while the two bins read
+    only (2/pi)^2 |c|^2."""
+    g = O.geometry(1 << 12, 0.0, 1.0, 1)
+    k = np.arange(g.n_r)
+    c = 1.5 - 2.0j
+    X = c * _rho0(k0 + 0.5 - k)
+    P = O.interbin_plane(O.correlation_plane(X, O.template_bank(g)))
+    assert abs(P[0, 2 * k0 + 1] - abs(c) ** 2) < 1e-10 * abs(c) ** 2
+    for b in (k0, k0 + 1):
+        assert abs(P[0, 2 * b] - (2 / math.pi) ** 2 * abs(c) ** 2) < 1e-10 * abs(c) ** 2
+    assert int(np.argmax(P[0])) == 2 * k0 + 1
+
+
+def test_interbin_integer_tone_neighbours_and_last_column():
+    """A tone on bin k0: the half bins on either side read (pi/4)^2 |c|^2
+    (rho(+-1, 0) = 0); the last column uses F(N_r) = 0."""
+    g = O.geometry(1 << 11, 0.0, 1.0, 1)
+    k = np.arange(g.n_r)
+    k0 = 300
+    c = 2.0 + 0.5j
+    X = c * _rho0(k0 - k)
+    F = O.correlation_plane(X, O.template_bank(g))
+    P = O.interbin_plane(F)
+    want = (math.pi / 4) ** 2 * abs(c) ** 2
+    assert abs(P[0, 2 * k0 + 1] - want) < 1e-10 * want
+    assert abs(P[0, 2 * k0 - 1] - want) < 1e-10 * want
+    assert abs(P[0, 2 * k0] - abs(c) ** 2) < 1e-10 * abs(c) ** 2
+    assert P[0, -1] == pytest.approx((math.pi / 4) ** 2 * abs(F[0, -1]) ** 2, rel=1e-14)
+
+
+def test_interbin_search_recovers_half_bin_sinusoid():
+    """A time-domain sinusoid half-way between bins loses (2/pi)^2 of its power
+    on the integer grid; the interbinned plane recovers most of it at the
+    half-bin column (up to the truncation of the half-bin estimate)."""
+    n, a = 1 << 14, 0.05
+    u = np.arange(n) / n
+    r_bar = 1234.5
+    x = a * np.cos(2 * np.pi * r_bar * u)
+    full = (a * n / 2) ** 2
+    plain = O.search(x, 4.0, 2.0, 1, norm="none")
+    ib = O.search(x, 4.0, 2.0, 1, norm="none", interbin=True)
+    g = plain["geom"]
+    assert ib["P"].shape == (g.n_z, 2 * g.n_r)
+    assert np.allclose(ib["P"][:, 0::2], plain["P"], rtol=1e-12, atol=0.0)
+    best_plain = plain["P"][g.iz0].max()
+    assert abs(best_plain / full - (2 / math.pi) ** 2) < 0.01
+    assert ib["P"][g.iz0, 2 * 1234 + 1] > 0.95 * full
+    assert int(np.argmax(ib["P"][g.iz0])) == 2 * 1234 + 1
+    c = ib["candidates"]
+    assert np.any((c["ir"] == 2 * 1234 + 1) & (c["iz"] == g.iz0))
+
+
+# --------------------------------------------------------------------------
 # whole path on the 2^17-sample workload
 # --------------------------------------------------------------------------
 def test_sinusoid_workload_detected_at_expected_cell():
