@@ -378,6 +378,26 @@ def run_gpu(args, rank, world, local_rank, dist):
                 "note": "same search with the fundamental-indexed harmonic sum (another "
                         "candidate definition; the headline uses top-harmonic indexing)"}
 
+    # --- interbinning (half-bin plane, 2 N_r columns), BF16, 64 series ----
+    ib = None
+    if not args.no_interbin:
+        nb = min(64, len(xs))
+        plani = capi.Plan(N_SAMPLES, TSAMP, Z_MAX, Z_STEP, SEG_LEN, N_HARM,
+                          precision=capi.FDAS_BF16, interbin=True)
+        ids_keep = ids
+        ids = ids[:nb]
+        ms_i, _, _, _, nf_i = timed(plani, xs[:nb], args.steps, args.warmup, False)
+        _, prof_i, _, _, _ = timed(plani, xs[:nb], 1, 1, True)
+        ids = ids_keep
+        plani.close()
+        ib = {"value": nb * args.steps * world / (ms_i / 1000.0), "unit": UNIT,
+              "series_per_step": nb, "ms_per_step": ms_i / args.steps,
+              "kernels_ms_per_trial": {g: prof_i[g][2] / max(1, prof_i["trials"])
+                                       for g in ("spectrum", "correlate", "harmonic")},
+              "candidates_per_trial": nf_i / (nb * args.steps),
+              "note": "same search on the half-bin plane (interbinning: complex correlation, "
+                      "then |F(r)|^2 and (pi/4)^2 |F(r) - F(r+1)|^2; 2x the plane cells)"}
+
     # --- uneven batch: full-length and decimated series in one call, graph ---
     uneven = None
     if not args.no_uneven:
@@ -469,6 +489,8 @@ def run_gpu(args, rank, world, local_rank, dist):
         line["uneven_batch"] = uneven
     if fund is not None:
         line["fundamental_harmonic"] = fund
+    if ib is not None:
+        line["interbin"] = ib
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
@@ -527,6 +549,8 @@ def main():
     ap.add_argument("--no-uneven", action="store_true")
     ap.add_argument("--no-fund", action="store_true",
                     help="skip the fundamental-indexed harmonic-sum leg")
+    ap.add_argument("--no-interbin", action="store_true",
+                    help="skip the interbinning (half-bin plane) leg")
     ap.add_argument("--uneven-batch", type=int, default=64)
     ap.add_argument("--n-log2", type=int, default=23,
                     help="series length 2^n (smaller only for profiling captures)")

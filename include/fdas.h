@@ -72,6 +72,15 @@ enum { FDAS_CORR_AUTO = 0, FDAS_CORR_FFT = 1, FDAS_CORR_TENSOR = 2 };
  *   cells where every multiple lies in the plane (h ir <= N_r - 1,
  *   |h o| <= K); fewer gathers and additions, a different candidate list. */
 enum { FDAS_HARM_TOP = 0, FDAS_HARM_FUNDAMENTAL = 1 };
+/* Interbinning (fdas_opts.interbin = 1; the paper does not use it, an
+ * option of the search): the power plane is sampled every half bin, n_z x
+ * 2 N_r cells.  With F(r, z) the complex correlation (the matched-filter
+ * output before |.|^2), column 2r holds |F(r)|^2 and column 2r + 1 holds
+ * (pi/4)^2 |F(r) - F(r+1)|^2, with F(N_r) = 0: a sinusoid half-way between
+ * two bins, which keeps only (2/pi)^2 of its power in either bin, is
+ * recovered in full there.  Statistics, harmonic sums (the index formulas
+ * applied to columns) and thresholds run on that plane; a candidate's `ir`
+ * is its column, the spectral bin ir/2. */
 
 typedef struct {
     int32_t precision;       /* FDAS_FP32 (default), FDAS_BF16, FDAS_FP16          */
@@ -89,6 +98,9 @@ typedef struct {
     int32_t correlator;      /* FDAS_CORR_AUTO (default), _FFT or _TENSOR; asking
                                 for _TENSOR where it does not apply is FDAS_ERR_ARG */
     int32_t harmonic_mode;   /* FDAS_HARM_TOP (default) or FDAS_HARM_FUNDAMENTAL */
+    int32_t interbin;        /* 1: the plane on the half-bin grid (see below);
+                                0 (default): whole bins.  Needs n_samples <= 2^23 */
+    int32_t reserved0;       /* set to 0 */
 } fdas_opts;
 
 /* One dedispersed time series (one DM trial).  `data` points to n_samples
@@ -130,6 +142,9 @@ typedef struct {
     double tuned_ms;          /* autotune: correlation time per series (ms), else 0 */
     int32_t correlator;       /* FDAS_CORR_FFT or FDAS_CORR_TENSOR, as built    */
     int32_t harmonic_mode;    /* FDAS_HARM_TOP or FDAS_HARM_FUNDAMENTAL         */
+    int32_t interbin;         /* 1: half-bin plane                             */
+    int32_t reserved0;
+    int64_t plane_cols;       /* columns of the power plane: N_r or 2 N_r      */
 } fdas_plan_info;
 
 typedef struct fdas_plan fdas_plan;
@@ -291,13 +306,26 @@ fdas_status fdas_spectrum(fdas_plan *plan, const float *series,
  */
 fdas_status fdas_power_plane(fdas_plan *plan, const void *spectrum,
                              void *plane_out, double *stats_out, void *stream);
+/* (With interbinning, plane_out holds n_z * 2 N_r elements: the half-bin
+ * plane, and stats_out its mean/std.) */
+
+/*
+ * The complex correlation itself, F[iz][r] = sum_{|e|<=m(z_iz)} X'_{r-e}
+ * g_z[e] for r in [0, N_r) (the same correlator as fdas_power_plane, before
+ * |.|^2; the input of interbinning).  spectrum: device, N_r complex elements
+ * (plan precision).  corr_out: device, n_z * N_r complex elements of the
+ * plan precision (FP16 unscaled).  Any plan.  Asynchronous.
+ */
+fdas_status fdas_correlation_plane(fdas_plan *plan, const void *spectrum,
+                                   void *corr_out, void *stream);
 
 /*
  * Harmonic sums of a plane, written out (for checking; the search itself
  * never stores them).  Top-harmonic indexing: for the cell (ir, iz), o =
  * iz - iz0, harmonic j of H reads (iz0 + sign(o) floor((|o| j + H/2)/H),
  * floor((ir j + H/2)/H)); stage h = 2^s sums the harmonics j = kH/h, k=1..h.
- * plane: device (plan precision).  sums_out: device float[n_stages][n_z][N_r].
+ * plane: device (plan precision).  sums_out: device float[n_stages][n_z][N_r]
+ * (plane_cols columns with interbinning).
  */
 fdas_status fdas_harmonic_sums(fdas_plan *plan, const void *plane,
                                float *sums_out, void *stream);

@@ -40,6 +40,7 @@ FDAS_HARM_TOP, FDAS_HARM_FUNDAMENTAL = 0, 1
 
 EXPORTED = ["fdas_opts_default", "fdas_plan_create", "fdas_plan_destroy",
             "fdas_plan_get_info", "fdas_search", "fdas_spectrum", "fdas_power_plane",
+            "fdas_correlation_plane",
             "fdas_harmonic_sums", "fdas_threshold", "fdas_template_bank",
             "fdas_spectrum_static", "fdas_fourier_power", "fdas_fourier_power_backward",
             "fdas_refine", "fdas_profile_enable", "fdas_profile_read",
@@ -51,7 +52,8 @@ class fdas_opts(Structure):
                 ("threshold_mode", c_int32), ("norm_mode", c_int32),
                 ("norm_block", c_int32), ("max_candidates", c_int64),
                 ("autotune", c_int32), ("use_graph", c_int32),
-                ("correlator", c_int32), ("harmonic_mode", c_int32)]
+                ("correlator", c_int32), ("harmonic_mode", c_int32),
+                ("interbin", c_int32), ("reserved0", c_int32)]
 
 
 class fdas_series(Structure):
@@ -77,7 +79,8 @@ class fdas_plan_info(Structure):
                 ("tsamp", c_double), ("z_max", c_double), ("z_step", c_double),
                 ("threshold_sigma", c_double), ("stage_factor", c_double * 6),
                 ("workspace_bytes", c_int64), ("z_chunks", c_int32), ("use_graph", c_int32),
-                ("tuned_ms", c_double), ("correlator", c_int32), ("harmonic_mode", c_int32)]
+                ("tuned_ms", c_double), ("correlator", c_int32), ("harmonic_mode", c_int32),
+                ("interbin", c_int32), ("reserved0", c_int32), ("plane_cols", c_int64)]
 
 
 class fdas_seed(Structure):
@@ -138,6 +141,8 @@ def lib() -> ctypes.CDLL:
         L.fdas_spectrum.restype = c_int32
         L.fdas_power_plane.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
         L.fdas_power_plane.restype = c_int32
+        L.fdas_correlation_plane.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
+        L.fdas_correlation_plane.restype = c_int32
         L.fdas_harmonic_sums.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
         L.fdas_harmonic_sums.restype = c_int32
         L.fdas_threshold.argtypes = [c_void_p, c_void_p, c_void_p, c_uint32, c_void_p, c_int64,
@@ -219,6 +224,11 @@ def fdas_spectrum(plan, series_ptr, spectrum_ptr, medians_ptr=None, stream=None)
 def fdas_power_plane(plan, spectrum_ptr, plane_ptr, stats_ptr=None, stream=None):
     _check(lib().fdas_power_plane(plan, spectrum_ptr, plane_ptr, stats_ptr, stream),
            "fdas_power_plane")
+
+
+def fdas_correlation_plane(plan, spectrum_ptr, corr_ptr, stream=None):
+    _check(lib().fdas_correlation_plane(plan, spectrum_ptr, corr_ptr, stream),
+           "fdas_correlation_plane")
 
 
 def fdas_harmonic_sums(plan, plane_ptr, sums_ptr, stream=None):
@@ -304,7 +314,7 @@ class Plan:
                  n_harm=16, precision=FDAS_FP32, threshold_sigma=6.0,
                  threshold_mode=FDAS_THRESH_GAMMA_TAIL, norm_mode=FDAS_NORM_MEDIAN,
                  norm_block=2048, max_candidates=1 << 20, autotune=False, use_graph=False,
-                 correlator=None, harmonic_mode=FDAS_HARM_TOP):
+                 correlator=None, harmonic_mode=FDAS_HARM_TOP, interbin=False):
         o = fdas_opts_default()
         o.precision = precision
         o.threshold_sigma = threshold_sigma
@@ -317,6 +327,7 @@ class Plan:
         if correlator is not None:
             o.correlator = correlator
         o.harmonic_mode = harmonic_mode
+        o.interbin = 1 if interbin else 0
         self.handle = fdas_plan_create(n_samples, tsamp, z_max, z_step, seg_len, n_harm, o)
         self.info = fdas_plan_get_info(self.handle)
 
@@ -379,16 +390,25 @@ class Plan:
 
     def power_plane(self, spec, stream=None):
         import torch
-        plane = torch.empty((self.info.n_z, self.info.n_r), dtype=self.spec_dtype,
+        plane = torch.empty((self.info.n_z, self.info.plane_cols), dtype=self.spec_dtype,
                             device=spec.device)
         stats = torch.empty(2, dtype=torch.float64, device=spec.device)
         fdas_power_plane(self.handle, c_void_p(spec.data_ptr()), c_void_p(plane.data_ptr()),
                          c_void_p(stats.data_ptr()), _stream_ptr(stream))
         return plane, stats
 
+    def correlation_plane(self, spec, stream=None):
+        """Complex F[n_z][N_r] as a (n_z, 2 N_r) tensor of (re, im) pairs."""
+        import torch
+        corr = torch.empty((self.info.n_z, 2 * self.info.n_r), dtype=self.spec_dtype,
+                           device=spec.device)
+        fdas_correlation_plane(self.handle, c_void_p(spec.data_ptr()), c_void_p(corr.data_ptr()),
+                               _stream_ptr(stream))
+        return corr
+
     def harmonic_sums(self, plane, stream=None):
         import torch
-        out = torch.empty((self.info.n_stages, self.info.n_z, self.info.n_r),
+        out = torch.empty((self.info.n_stages, self.info.n_z, self.info.plane_cols),
                           dtype=torch.float32, device=plane.device)
         fdas_harmonic_sums(self.handle, c_void_p(plane.data_ptr()), c_void_p(out.data_ptr()),
                            _stream_ptr(stream))

@@ -20,6 +20,9 @@
 // partial sums across templates with compensated (Kahan) FP32 sums; the CTA
 // adds them in FP64 in a fixed order and writes one partial per CTA, which the
 // statistics kernel reduces in a fixed order (deterministic mean and std).
+//
+// With kCplx the kernels write the complex F itself (plane of complex values
+// at the plan's precision, no statistics): the input of interbinning.
 #include "fdas_internal.cuh"
 #include "fft_cta.cuh"
 #include "fft8k.cuh"
@@ -38,10 +41,10 @@ struct Kahan {
     }
 };
 
-template <int L, class P>
+template <int L, class P, bool kCplx>
 __global__ void __launch_bounds__(L / 16, 1)
     correlate_kernel(const typename P::cpx *__restrict__ spec_pad,
-                     const typename P::cpx *__restrict__ bank, typename P::real *__restrict__ plane,
+                     const typename P::cpx *__restrict__ bank, void *__restrict__ out,
                      double2 *__restrict__ partials, int64_t n_r, int n_z, int V, int m_ov,
                      int z_per_cta, float bank_scale) {
     using Fw = CtaFft<L, -1>;
@@ -73,7 +76,8 @@ __global__ void __launch_bounds__(L / 16, 1)
         for (int r = 0; r < 16; ++r) v[r] = cmul(S[r], P::ld(__ldg(h + tid + r * T)));
         float2 o[16];
         Iv::to_regs(v, buf, tid, tw, o);
-        typename P::real *row = plane + (int64_t)iz * n_r;
+        typename P::real *row = static_cast<typename P::real *>(out) + (int64_t)iz * n_r;
+        typename P::cpx *crow = static_cast<typename P::cpx *>(out) + (int64_t)iz * n_r;
         float zs = 0.f, zq = 0.f;   // this template's 16 outputs, plain FP32
 #pragma unroll
         for (int b = 0; b < NB; ++b)
@@ -83,6 +87,10 @@ __global__ void __launch_bounds__(L / 16, 1)
                 const int64_t rr = seg0 + n - m_ov;
                 if (n >= m_ov && n < m_ov + V && rr < n_r) {
                     const float2 y = o[b * R + r];
+                    if constexpr (kCplx) {
+                        crow[rr] = P::st(y);
+                        continue;
+                    }
                     const float pw = fmaf(y.x, y.x, y.y * y.y);
                     row[rr] = P::str(pw * P::plane_scale);
                     zs += pw;
@@ -120,10 +128,10 @@ __global__ void __launch_bounds__(L / 16, 1)
 // asynchronous copies (cp.async.bulk + mbarrier): the spectrum of template
 // z + 1 is in flight while the inverse FFT of template z runs.  A bounded
 // wait that gives up sets bit 1 of `flags` and the CTA returns.
-template <class P>
+template <class P, bool kCplx>
 __global__ void __launch_bounds__(256, 1)
     correlate8k_kernel(const typename P::cpx *__restrict__ spec_pad,
-                       const typename P::cpx *__restrict__ bank, typename P::real *__restrict__ plane,
+                       const typename P::cpx *__restrict__ bank, void *__restrict__ out,
                        double2 *__restrict__ partials, int64_t n_r, int n_z, int V, int m_ov,
                        int z_per_cta, float bank_scale, unsigned int *__restrict__ flags) {
     using Fw = Fft8k<-1>;
@@ -224,9 +232,17 @@ __global__ void __launch_bounds__(256, 1)
         }
         Iv::pass1(buf, t, w1);
         Iv::pass2(buf, t, w2, o);
-        typename P::real *row = plane + (seg0 - m_ov) + (int64_t)iz * n_r + t;
+        typename P::real *row = static_cast<typename P::real *>(out) + (seg0 - m_ov) + (int64_t)iz * n_r + t;
+        typename P::cpx *crow = static_cast<typename P::cpx *>(out) + (seg0 - m_ov) + (int64_t)iz * n_r + t;
         float zs = 0.f, zq = 0.f;
-        if (interior) {
+        if constexpr (kCplx) {
+#pragma unroll
+            for (int r = 0; r < 32; ++r) {
+                const int n = t + 256 * r;
+                const int64_t rr = seg0 + n - m_ov;
+                if (n >= m_ov && n < m_ov + V && rr < n_r) crow[256 * r] = P::st(o[r]);
+            }
+        } else if (interior) {
             // outputs r = 1..30 lie inside [m_ov, L - m_ov) when m_ov <= 256,
             // and inside the plane row when the segment is not the last
 #pragma unroll
@@ -274,45 +290,45 @@ __global__ void __launch_bounds__(256, 1)
     }
 }
 
-template <class P>
+template <class P, bool kCplx>
 fdas_status launch_8k(Plan &p, const void *spec_padded, void *plane, double2 *partials,
                       cudaStream_t s) {
     const size_t smem = sizeof(float2) * Fft8k<1>::SMEM_ELEMS + 2 * 8192 * sizeof(typename P::cpx);
-    auto k = correlate8k_kernel<P>;
+    auto k = correlate8k_kernel<P, kCplx>;
     FDAS_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int zper = (p.n_z + p.n_zchunk - 1) / p.n_zchunk;
     dim3 grid(p.n_seg, p.n_zchunk);
     const float bank_scale = P::id == FDAS_FP16 ? 1.0f / (float)p.L : 1.0f;
     k<<<grid, 256, smem, s>>>((const typename P::cpx *)spec_padded, (const typename P::cpx *)p.bank,
-                              (typename P::real *)plane, partials, p.n_r, p.n_z, p.V, p.m_ov, zper,
+                              plane, partials, p.n_r, p.n_z, p.V, p.m_ov, zper,
                               bank_scale, p.flags);
     FDAS_CUDA_TRY(cudaGetLastError());
     return FDAS_OK;
 }
 
-template <int L, class P>
+template <int L, class P, bool kCplx>
 fdas_status launch_L(Plan &p, const void *spec_padded, void *plane, double2 *partials,
                      cudaStream_t s) {
     const size_t smem = sizeof(float2) * CtaFft<L, 1>::SMEM_ELEMS;
-    auto k = correlate_kernel<L, P>;
+    auto k = correlate_kernel<L, P, kCplx>;
     FDAS_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int zper = (p.n_z + p.n_zchunk - 1) / p.n_zchunk;
     dim3 grid(p.n_seg, p.n_zchunk);
     const float bank_scale = P::id == FDAS_FP16 ? 1.0f / (float)p.L : 1.0f;
     k<<<grid, L / 16, smem, s>>>((const typename P::cpx *)spec_padded,
-                                 (const typename P::cpx *)p.bank, (typename P::real *)plane,
+                                 (const typename P::cpx *)p.bank, plane,
                                  partials, p.n_r, p.n_z, p.V, p.m_ov, zper, bank_scale);
     FDAS_CUDA_TRY(cudaGetLastError());
     return FDAS_OK;
 }
 
-template <class P>
+template <class P, bool kCplx>
 fdas_status launch_P(Plan &p, const void *spec, void *plane, double2 *partials, cudaStream_t s) {
     switch (p.L) {
-        case 1024: return launch_L<1024, P>(p, spec, plane, partials, s);
-        case 2048: return launch_L<2048, P>(p, spec, plane, partials, s);
-        case 4096: return launch_L<4096, P>(p, spec, plane, partials, s);
-        case 8192: return launch_8k<P>(p, spec, plane, partials, s);
+        case 1024: return launch_L<1024, P, kCplx>(p, spec, plane, partials, s);
+        case 2048: return launch_L<2048, P, kCplx>(p, spec, plane, partials, s);
+        case 4096: return launch_L<4096, P, kCplx>(p, spec, plane, partials, s);
+        case 8192: return launch_8k<P, kCplx>(p, spec, plane, partials, s);
         default:
             set_error("seg_len " + std::to_string(p.L) + " is not built");
             return FDAS_ERR_UNSUPPORTED;
@@ -325,15 +341,22 @@ int correlate_ctas(const Plan &p) {
     return p.correlator == FDAS_CORR_TENSOR ? correlate_tc_ctas(p) : p.n_seg * p.n_zchunk;
 }
 
-fdas_status launch_correlate(Plan &p, const void *spec_padded, void *plane, double2 *partials,
-                             cudaStream_t s) {
-    if (p.correlator == FDAS_CORR_TENSOR)
-        return launch_correlate_tc(p, spec_padded, plane, partials, s);
+template <bool kCplx>
+fdas_status launch_prec(Plan &p, const void *spec_padded, void *plane, double2 *partials,
+                        cudaStream_t s) {
     switch (p.prec) {
-        case FDAS_FP32: return launch_P<PrecF32>(p, spec_padded, plane, partials, s);
-        case FDAS_BF16: return launch_P<PrecBF16>(p, spec_padded, plane, partials, s);
-        default: return launch_P<PrecF16>(p, spec_padded, plane, partials, s);
+        case FDAS_FP32: return launch_P<PrecF32, kCplx>(p, spec_padded, plane, partials, s);
+        case FDAS_BF16: return launch_P<PrecBF16, kCplx>(p, spec_padded, plane, partials, s);
+        default: return launch_P<PrecF16, kCplx>(p, spec_padded, plane, partials, s);
     }
+}
+
+fdas_status launch_correlate(Plan &p, const void *spec_padded, void *plane, double2 *partials,
+                             cudaStream_t s, bool cplx) {
+    if (p.correlator == FDAS_CORR_TENSOR)
+        return launch_correlate_tc(p, spec_padded, plane, partials, s, cplx);
+    return cplx ? launch_prec<true>(p, spec_padded, plane, partials, s)
+                : launch_prec<false>(p, spec_padded, plane, partials, s);
 }
 
 }  // namespace fdas

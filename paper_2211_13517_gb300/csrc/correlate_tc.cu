@@ -34,6 +34,10 @@
 // Unit template energy (noise cells distributed as Exp(1)) is kept for the
 // taps as rounded to 16 bits: P is |F|^2 / E'_z with E'_z = sum_e |g'_z[e]|^2
 // of the rounded taps g', one FP32 factor per template.
+//
+// With kCplx the epilogue writes the complex F / sqrt(E'_z) instead (4
+// consecutive bins per template as one 16-byte store, no statistics): the
+// input of interbinning, which needs F at neighbouring bins.
 #include <algorithm>
 
 #include "fdas_internal.cuh"
@@ -101,13 +105,13 @@ __device__ __forceinline__ float2 fsub2(float2 a, float2 b) {
     return __fadd2_rn(a, make_float2(-b.x, -b.y));
 }
 
-template <class P>
+template <class P, bool kCplx>
 __global__ void __launch_bounds__(kTcThreads, 1)
     correlate_tc_kernel(const typename P::cpx *__restrict__ spec_pad,
                         const unsigned char *__restrict__ bank_img,
                         const TcChunk *__restrict__ chunks, int n_ch,
                         const float *__restrict__ inv_energy,
-                        typename P::real *__restrict__ plane, double2 *__restrict__ partials,
+                        void *__restrict__ out, double2 *__restrict__ partials,
                         int64_t n_r, int win_bytes, int b_bytes_max, unsigned int *flags) {
     extern __shared__ __align__(128) unsigned char tc_smem[];
     unsigned char *const sB = tc_smem;
@@ -238,8 +242,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         int c, cur = -1, zvalid = 0;
         int64_t t;
         int j = 0;
-        float sc[kTcZpt];
-        typename P::real *zrow = plane;
+        float sc[kTcZpt];   // 1 / E'_z (power) or 1 / sqrt(E'_z) (complex)
+        typename P::real *zrow = static_cast<typename P::real *>(out);
+        typename P::cpx *zcrow = static_cast<typename P::cpx *>(out);
         float2 s1 = make_float2(0.f, 0.f), s2 = make_float2(0.f, 0.f);
         // compensated FP32 sums across tiles (FP64 only once, at the end: the
         // FP64 pipe is a small fraction of the FP32 one)
@@ -252,8 +257,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 const int zb = chunks[c].z_begin + kTcZpt * part;
                 zvalid = chunks[c].n_zc - kTcZpt * part;
 #pragma unroll
-                for (int k = 0; k < kTcZpt; ++k) sc[k] = k < zvalid ? __ldg(inv_energy + zb + k) : 0.f;
-                zrow = plane + (int64_t)zb * n_r + 4 * row;
+                for (int k = 0; k < kTcZpt; ++k) {
+                    const float ie = k < zvalid ? __ldg(inv_energy + zb + k) : 0.f;
+                    sc[k] = kCplx ? sqrtf(ie) : ie;
+                }
+                if constexpr (kCplx)
+                    zcrow = static_cast<typename P::cpx *>(out) + (int64_t)zb * n_r + 4 * row;
+                else
+                    zrow = static_cast<typename P::real *>(out) + (int64_t)zb * n_r + 4 * row;
             }
             const int b = j & 1;
             const bool got = mbar_wait(&acc_full[b], (j >> 1) & 1);
@@ -271,6 +282,24 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[b]);
+            if constexpr (kCplx) {
+                typename P::cpx *oc = zcrow + t * kTcTile;
+#pragma unroll
+                for (int k = 0; k < kTcZpt; ++k) {
+                    if (k < zvalid) {
+                        uint32_t w[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const typename P::cpx cq = P::st(make_float2(
+                                __uint_as_float(v[k][q]) * sc[k], __uint_as_float(v[k][4 + q]) * sc[k]));
+                            memcpy(&w[q], &cq, 4);
+                        }
+                        *reinterpret_cast<uint4 *>(oc + (int64_t)k * n_r) = make_uint4(w[0], w[1], w[2], w[3]);
+                    }
+                }
+                ++j;
+                continue;
+            }
             typename P::real *o = zrow + t * kTcTile;
 #pragma unroll
             for (int k = 0; k < kTcZpt; ++k) {
@@ -402,16 +431,16 @@ size_t tc_smem_bytes(int max_ks, int win) {
     return std::max(need, kTcMinSmem);
 }
 
-template <class P>
+template <class P, bool kCplx>
 fdas_status launch_tc_P(Plan &p, const void *spec_padded, void *plane, double2 *partials,
                         cudaStream_t s) {
     const size_t smem = tc_smem_bytes(p.tc_max_ks, p.tc_win);
-    auto k = correlate_tc_kernel<P>;
+    auto k = correlate_tc_kernel<P, kCplx>;
     FDAS_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = correlate_tc_ctas(p);
     k<<<grid, kTcThreads, smem, s>>>((const typename P::cpx *)spec_padded,
                                       (const unsigned char *)p.tc_bank, p.tc_chunks, p.tc_n_ch,
-                                      p.tc_inv_energy, (typename P::real *)plane, partials, p.n_r,
+                                      p.tc_inv_energy, plane, partials, p.n_r,
                                       p.tc_win * 4,
                                       p.tc_max_ks * kTcSlab, p.flags);
     FDAS_CUDA_TRY(cudaGetLastError());
@@ -503,10 +532,14 @@ fdas_status launch_tc_bank(Plan &p, cudaStream_t s) {
 }
 
 fdas_status launch_correlate_tc(Plan &p, const void *spec_padded, void *plane, double2 *partials,
-                                cudaStream_t s) {
+                                cudaStream_t s, bool cplx) {
     switch (p.prec) {
-        case FDAS_BF16: return launch_tc_P<PrecBF16>(p, spec_padded, plane, partials, s);
-        case FDAS_FP16: return launch_tc_P<PrecF16>(p, spec_padded, plane, partials, s);
+        case FDAS_BF16:
+            return cplx ? launch_tc_P<PrecBF16, true>(p, spec_padded, plane, partials, s)
+                        : launch_tc_P<PrecBF16, false>(p, spec_padded, plane, partials, s);
+        case FDAS_FP16:
+            return cplx ? launch_tc_P<PrecF16, true>(p, spec_padded, plane, partials, s)
+                        : launch_tc_P<PrecF16, false>(p, spec_padded, plane, partials, s);
         default:
             set_error("tensor-core correlation: 16-bit precisions only");
             return FDAS_ERR_UNSUPPORTED;

@@ -162,6 +162,7 @@ struct Plan {
     double tuned_ms = 0.0;
     int correlator = FDAS_CORR_FFT;   // FDAS_CORR_FFT or FDAS_CORR_TENSOR
     int harm_mode = FDAS_HARM_TOP;    // FDAS_HARM_TOP or FDAS_HARM_FUNDAMENTAL
+    bool interbin = false;            // plane on the half-bin grid (2 n_r columns)
     // tensor-core correlation: template chunks, their operand images and the
     // spectrum window each GEMM tile reads (complex elements)
     TcChunk *tc_chunks = nullptr;
@@ -179,7 +180,8 @@ struct Plan {
     int64_t n_taps = 0;
     float2 *fft_a = nullptr, *fft_b = nullptr;   // [M] scratch each
     void *spec_pad = nullptr;       // [n_seg*V + 2 m_ov] cpx, zero-padded
-    void *plane[2] = {nullptr, nullptr};
+    void *plane[2] = {nullptr, nullptr};   // [n_z][plane_cols] real
+    void *corr = nullptr;           // interbinning: [n_z][n_r] complex F
     double2 *partials[2] = {nullptr, nullptr};   // per correlation CTA
     TrialStats *stats = nullptr;    // [stats_cap]
     int64_t stats_cap = 0;
@@ -218,8 +220,10 @@ struct Plan {
 fdas_status launch_template_bank(Plan &p, cudaStream_t s);
 fdas_status launch_spectrum(Plan &p, const float *x, void *spec_out_padded,
                             float *medians, cudaStream_t s);
+// cplx: write the complex F (plane of the plan's complex type) instead of
+// |F|^2 and its statistics
 fdas_status launch_correlate(Plan &p, const void *spec_padded, void *plane,
-                             double2 *partials, cudaStream_t s);
+                             double2 *partials, cudaStream_t s, bool cplx = false);
 int correlate_ctas(const Plan &p);
 // tensor-core correlation: whether it applies to the plan's geometry, the
 // host-side chunk table, the operand images (from the FP64 taps) and launch
@@ -228,9 +232,16 @@ std::vector<TcChunk> tc_chunk_table(const Plan &p, const std::vector<int32_t> &m
                                     int *max_ks);
 fdas_status launch_tc_bank(Plan &p, cudaStream_t s);
 fdas_status launch_correlate_tc(Plan &p, const void *spec_padded, void *plane, double2 *partials,
-                                cudaStream_t s);
+                                cudaStream_t s, bool cplx);
 int correlate_tc_ctas(const Plan &p);
 int64_t tc_bank_bytes(const std::vector<TcChunk> &table);
+// interbinning: complex F [n_z][n_r] -> plane [n_z][2 n_r] and one FP64
+// (sum P, sum P^2) partial per CTA
+fdas_status launch_interbin(Plan &p, const void *F, void *plane, double2 *partials,
+                            cudaStream_t s);
+int interbin_ctas(const Plan &p);
+// columns of the power plane: n_r, or 2 n_r on the half-bin grid
+inline int64_t plane_cols(const Plan &p) { return p.interbin ? 2 * p.n_r : p.n_r; }
 fdas_status launch_finalize_stats(Plan &p, const double2 *partials, int n_partials,
                                   const double *given_stats, TrialStats *out,
                                   cudaStream_t s);

@@ -74,6 +74,7 @@ static void free_plan_memory(Plan *p) {
     cudaFree(p->fft_a);
     cudaFree(p->fft_b);
     cudaFree(p->spec_pad);
+    cudaFree(p->corr);
     cudaFree(p->tc_chunks);
     cudaFree(p->tc_bank);
     cudaFree(p->tc_inv_energy);
@@ -177,6 +178,15 @@ static void set_length(Plan &p, int64_t n) {
 }
 
 // the plan's buffers with the geometry of a shorter series
+// the plan as the statistics and harmonic kernels see it: the plane's
+// columns (half bins with interbinning) in place of the spectral bins
+static Plan harm_view(const Plan &v) {
+    Plan h = v;
+    h.n_r = plane_cols(v);
+    h.interbin = false;
+    return h;
+}
+
 static Plan plan_view(const Plan &p, int64_t n) {
     Plan v = p;
     set_length(v, n);
@@ -220,6 +230,10 @@ static fdas_status create(Plan *&out, int64_t n_samples, double tsamp, double z_
         return arg_error("unknown correlator");
     if (o->harmonic_mode != FDAS_HARM_TOP && o->harmonic_mode != FDAS_HARM_FUNDAMENTAL)
         return arg_error("unknown harmonic_mode");
+    if (o->interbin != 0 && o->interbin != 1) return arg_error("interbin must be 0 or 1");
+    // candidate records keep the plane column in 23 bits
+    if (o->interbin && n_samples > (1 << 23))
+        return arg_error("interbinning takes n_samples <= 2^23");
 
     Plan *pp = new (std::nothrow) Plan();
     if (!pp) return arg_error("out of host memory");
@@ -240,6 +254,7 @@ static fdas_status create(Plan *&out, int64_t n_samples, double tsamp, double z_
     p.sigma = o->threshold_sigma;
     p.max_cands = o->max_candidates;
     p.harm_mode = o->harmonic_mode;
+    p.interbin = o->interbin != 0;
     for (int s = 0; s < 6; ++s) p.G[s] = s < p.n_stages ? gamma_tail_factor(1 << s, p.sigma) : 0.0;
 
     // template half-widths m(z) = 8 + ceil(|z|/2) on the exact grid
@@ -340,11 +355,12 @@ static fdas_status create(Plan *&out, int64_t n_samples, double tsamp, double z_
     const size_t pad_elems = (size_t)p.n_seg * p.V + 2 * (size_t)p.m_ov + 64;
     PLAN_TRY(dalloc(p, &p.spec_pad, cb * pad_elems));
     for (int b = 0; b < 2; ++b) {
-        PLAN_TRY(dalloc(p, &p.plane[b], rb * (size_t)p.n_z * (size_t)p.n_r));
+        PLAN_TRY(dalloc(p, &p.plane[b], rb * (size_t)p.n_z * (size_t)plane_cols(p)));
         PLAN_TRY(dalloc(p, &p.partials[b], sizeof(double2) * (size_t)p.partials_cap));
         PLAN_CUDA(cudaEventCreateWithFlags(&p.ev_conv[b], cudaEventDisableTiming));
         PLAN_CUDA(cudaEventCreateWithFlags(&p.ev_hsum[b], cudaEventDisableTiming));
     }
+    if (p.interbin) PLAN_TRY(dalloc(p, &p.corr, cb * (size_t)p.n_z * (size_t)p.n_r));
     PLAN_TRY(grow_stats(p, 64));
     const int64_t rec_cap = next_pow2(p.max_cands);
     PLAN_TRY(dalloc(p, &p.cand, sizeof(CandRec) * (size_t)rec_cap));
@@ -570,18 +586,26 @@ static fdas_status enqueue_batch(Plan &p, const fdas_series *batch, int32_t n_se
             FDAS_CUDA_TRY(cudaStreamWaitEvent(s, p.ev_hsum[b], 0));
             if (p.profiling) e1 = mark(s);
         }
-        FDAS_TRY(launch_correlate(v, p.spec_pad, p.plane[b], p.partials[b], s));
+        if (p.interbin) {
+            FDAS_TRY(launch_correlate(v, p.spec_pad, p.corr, p.partials[b], s, true));
+            FDAS_TRY(launch_interbin(v, p.corr, p.plane[b], p.partials[b], s));
+        } else {
+            FDAS_TRY(launch_correlate(v, p.spec_pad, p.plane[b], p.partials[b], s));
+        }
         cudaEvent_t e2 = p.profiling ? mark(s) : nullptr;
         FDAS_CUDA_TRY(cudaEventRecord(p.ev_conv[b], s));
         FDAS_CUDA_TRY(cudaStreamWaitEvent(hs, p.ev_conv[b], 0));
         cudaEvent_t e3 = p.profiling ? mark(hs) : nullptr;
         TrialStats *ts = p.stats + rank[t];
-        FDAS_TRY(launch_finalize_stats(v, p.partials[b], correlate_ctas(v), nullptr, ts, hs));
-        FDAS_TRY(launch_harmonic_threshold(v, p.plane[b], ts, (uint32_t)rank[t], hs));
+        Plan hv = harm_view(v);
+        FDAS_TRY(launch_finalize_stats(hv, p.partials[b],
+                                       p.interbin ? interbin_ctas(v) : correlate_ctas(v), nullptr,
+                                       ts, hs));
+        FDAS_TRY(launch_harmonic_threshold(hv, p.plane[b], ts, (uint32_t)rank[t], hs));
         cudaEvent_t e4 = p.profiling ? mark(hs) : nullptr;
         FDAS_CUDA_TRY(cudaEventRecord(p.ev_hsum[b], hs));
         p.launches[FDAS_PROF_SPECTRUM] += (v.fft_m1 == 1 ? 1 : 2) + 1;
-        p.launches[FDAS_PROF_CORRELATE] += 1;
+        p.launches[FDAS_PROF_CORRELATE] += p.interbin ? 2 : 1;
         p.launches[FDAS_PROF_HARMONIC] += 2;
         if (p.profiling) {
             iv.push_back({FDAS_PROF_SPECTRUM, e0, e1});
@@ -875,6 +899,9 @@ fdas_status fdas_plan_get_info(const fdas_plan *plan, fdas_plan_info *info) {
     info->tuned_ms = p.tuned_ms;
     info->correlator = p.correlator;
     info->harmonic_mode = p.harm_mode;
+    info->interbin = p.interbin ? 1 : 0;
+    info->reserved0 = 0;
+    info->plane_cols = plane_cols(p);
     return FDAS_OK;
 }
 
@@ -908,20 +935,41 @@ fdas_status fdas_power_plane(fdas_plan *plan, const void *spectrum, void *plane_
     const size_t cb = cpx_bytes(p.prec);
     FDAS_CUDA_TRY(cudaMemcpyAsync((char *)p.spec_pad + cb * (size_t)p.m_ov, spectrum,
                                   cb * (size_t)p.n_r, cudaMemcpyDeviceToDevice, s));
-    FDAS_TRY(launch_correlate(p, p.spec_pad, plane_out, p.partials[0], s));
+    if (p.interbin) {
+        FDAS_TRY(launch_correlate(p, p.spec_pad, p.corr, p.partials[0], s, true));
+        FDAS_TRY(launch_interbin(p, p.corr, plane_out, p.partials[0], s));
+    } else {
+        FDAS_TRY(launch_correlate(p, p.spec_pad, plane_out, p.partials[0], s));
+    }
     if (stats_out) {
-        FDAS_TRY(launch_finalize_stats(p, p.partials[0], correlate_ctas(p), nullptr, p.stats, s));
+        Plan hv = harm_view(p);
+        FDAS_TRY(launch_finalize_stats(hv, p.partials[0],
+                                       p.interbin ? interbin_ctas(p) : correlate_ctas(p), nullptr,
+                                       p.stats, s));
         FDAS_CUDA_TRY(cudaMemcpyAsync(stats_out, p.stats, 2 * sizeof(double),
                                       cudaMemcpyDeviceToDevice, s));
     }
     return FDAS_OK;
 }
 
+fdas_status fdas_correlation_plane(fdas_plan *plan, const void *spectrum, void *corr_out,
+                                   void *stream) {
+    if (!plan || !spectrum || !corr_out) return arg_error("NULL argument");
+    Plan &p = *reinterpret_cast<Plan *>(plan);
+    DeviceGuard guard(p.device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t cb = cpx_bytes(p.prec);
+    FDAS_CUDA_TRY(cudaMemcpyAsync((char *)p.spec_pad + cb * (size_t)p.m_ov, spectrum,
+                                  cb * (size_t)p.n_r, cudaMemcpyDeviceToDevice, s));
+    return launch_correlate(p, p.spec_pad, corr_out, p.partials[0], s, true);
+}
+
 fdas_status fdas_harmonic_sums(fdas_plan *plan, const void *plane, float *sums_out, void *stream) {
     if (!plan || !plane || !sums_out) return arg_error("NULL argument");
     Plan &p = *reinterpret_cast<Plan *>(plan);
     DeviceGuard guard(p.device);
-    return launch_harmonic_sums(p, plane, sums_out, (cudaStream_t)stream);
+    Plan hv = harm_view(p);
+    return launch_harmonic_sums(hv, plane, sums_out, (cudaStream_t)stream);
 }
 
 fdas_status fdas_threshold(fdas_plan *plan, const void *plane, const double *stats,
@@ -936,8 +984,9 @@ fdas_status fdas_threshold(fdas_plan *plan, const void *plane, const double *sta
     FDAS_CUDA_TRY(cudaMemcpyAsync(p.rank_ids, &trial_id, sizeof(uint32_t), cudaMemcpyHostToDevice, s));
     FDAS_CUDA_TRY(cudaMemsetAsync(p.cand_count, 0, sizeof(unsigned long long), s));
     FDAS_CUDA_TRY(cudaMemsetAsync(p.flags, 0, sizeof(unsigned int), s));
-    FDAS_TRY(launch_finalize_stats(p, nullptr, 0, stats, p.stats, s));
-    FDAS_TRY(launch_harmonic_threshold(p, plane, p.stats, 0, s));
+    Plan hv = harm_view(p);
+    FDAS_TRY(launch_finalize_stats(hv, nullptr, 0, stats, p.stats, s));
+    FDAS_TRY(launch_harmonic_threshold(hv, plane, p.stats, 0, s));
     return collect(p, cands, capacity, n_found, s);
 }
 

@@ -45,8 +45,8 @@ def test_every_declared_symbol_is_exported(capi):
 def test_struct_layouts(capi):
     assert ctypes.sizeof(capi.fdas_candidate) == 20
     assert ctypes.sizeof(capi.fdas_series) == 24
-    assert ctypes.sizeof(capi.fdas_opts) == 56
-    assert ctypes.sizeof(capi.fdas_plan_info) == 176
+    assert ctypes.sizeof(capi.fdas_opts) == 64
+    assert ctypes.sizeof(capi.fdas_plan_info) == 192
     assert capi.CANDIDATE_DTYPE.itemsize == 20
     assert ctypes.sizeof(capi.fdas_seed) == capi.SEED_DTYPE.itemsize == 24
     assert ctypes.sizeof(capi.fdas_refined) == capi.REFINED_DTYPE.itemsize == 40
@@ -87,6 +87,17 @@ def test_opts_validation(capi):
     o.precision = 7
     with pytest.raises(capi.FdasError):
         capi.fdas_plan_create(1 << 17, 64e-6, 16.0, 2.0, 2048, 4, o)
+    o = capi.fdas_opts_default()
+    o.interbin = 2
+    with pytest.raises(capi.FdasError) as ei:
+        capi.fdas_plan_create(1 << 17, 64e-6, 16.0, 2.0, 2048, 4, o)
+    assert ei.value.status == capi.FDAS_ERR_ARG and "interbin" in str(ei.value)
+    # the half-bin plane of a 2^24-sample series has 2^24 columns: refused
+    o = capi.fdas_opts_default()
+    o.interbin = 1
+    with pytest.raises(capi.FdasError) as ei:
+        capi.fdas_plan_create(1 << 24, 64e-6, 16.0, 2.0, 2048, 4, o)
+    assert ei.value.status == capi.FDAS_ERR_ARG and "2^23" in str(ei.value)
 
 
 def test_null_arguments_rejected(capi):
@@ -97,3 +108,4 @@ def test_null_arguments_rejected(capi):
     lib.fdas_plan_destroy(None)   # ignored
     assert lib.fdas_selftest_wait_timeout(None, 1000, None) == capi.FDAS_ERR_ARG
     assert lib.fdas_refine(None, None, None, 0, 0, None, None) == capi.FDAS_ERR_ARG
+    assert lib.fdas_correlation_plane(None, None, None, None) == capi.FDAS_ERR_ARG
