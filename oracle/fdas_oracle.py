@@ -41,6 +41,14 @@ paper and follows the stated readings):
                      the interbinned power (pi/4)^2 |F(r) - F(r+1)|^2, with
                      F(N_r) = 0 beyond the last bin; stats, harmonic sums and
                      candidates then run on that 2 N_r-column plane.
+0. ``dm_delays``     (upstream of the search, optional) incoherent
+   ``dedisperse``    dedispersion of a filterbank into DM-trial series:
+                     delay of channel c (frequency f_c = f_top - c df, MHz)
+                     at DM_d = dm_lo + d dm_step is the cold-plasma delay
+                     relative to the top of the band in samples,
+                     Delta(c, d) = floor(K_DM DM_d (f_c^-2 - f_top^-2) / tsamp
+                     + 1/2), K_DM = 4.148808e3 MHz^2 pc^-1 cm^3 s, and
+                     out[d][t] = sum_c in[c][t + Delta(c, d)] (0 past n_t).
 9. ``fourier_power`` the off-grid power used to refine candidates:
                      F(r, z) = sum_k X'_k conj(rho(r - k, z)) over the bins
                      within 32 + ceil(|z|/2) of round(r), unnormalised rho,
@@ -463,6 +471,42 @@ def candidates(P: np.ndarray, geom: Geometry, mean: float, std: float,
     cands = np.sort(rec[is_cand], order=["trial", "harm", "iz", "ir"])
     guards = np.sort(rec[in_guard], order=["trial", "harm", "iz", "ir"])
     return cands, guards
+
+
+# --------------------------------------------------------------------------
+# 0: dedispersion (the stage that produces the DM-trial series)
+# --------------------------------------------------------------------------
+K_DM = 4.148808e3   # dispersion constant, MHz^2 pc^-1 cm^3 s
+
+
+def dm_delays(n_chan: int, f_top: float, df: float, tsamp: float, dm_lo: float,
+              dm_step: float, n_dm: int) -> np.ndarray:
+    """Delta[d][c] in samples (int64), every operation one IEEE FP64 rounding
+    in this order: f = f_top - c*df; a = 1/(f*f); b = 1/(f_top*f_top);
+    dm = dm_lo + d*dm_step; x = ((K_DM*dm)*(a - b))/tsamp; floor(x + 1/2)."""
+    c = np.arange(n_chan, dtype=np.float64)
+    f = f_top - c * df
+    a = 1.0 / (f * f)
+    b = 1.0 / (f_top * f_top)
+    dm = dm_lo + np.arange(n_dm, dtype=np.float64) * dm_step
+    x = ((K_DM * dm)[:, None] * (a - b)[None, :]) / tsamp
+    return np.floor(x + 0.5).astype(np.int64)
+
+
+def dedisperse(fb: np.ndarray, delays: np.ndarray, n_out: int) -> np.ndarray:
+    """out[d][t] = sum_c fb[c][t + delays[d][c]] for t < n_out, samples at or
+    past the end of the filterbank counted as 0 (FP64)."""
+    n_chan, n_t = fb.shape
+    n_dm = delays.shape[0]
+    pad = int(delays.max()) + n_out
+    x = np.zeros((n_chan, max(n_t, pad)), dtype=np.float64)
+    x[:, :n_t] = fb
+    out = np.zeros((n_dm, n_out), dtype=np.float64)
+    for d in range(n_dm):
+        for c in range(n_chan):
+            k = int(delays[d, c])
+            out[d] += x[c, k:k + n_out]
+    return out
 
 
 # --------------------------------------------------------------------------

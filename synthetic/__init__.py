@@ -22,6 +22,9 @@ the paper prints none):
 * ``pulsar_series``     -- 2^23 samples, N(0,1) noise, 3 top-hat pulse trains
                            (duty 0.05, height 0.054), r0 ~ U[1e4, 4e6],
                            z0 ~ U[-90, 90], all drawn from the series seed.
+* ``filterbank_noise``  -- the input of dedispersion: N(0,1) channels x
+                           samples; ``add_at_samples`` plants a pulse at
+                           caller-given samples per channel.
 * ``batch_series``      -- series i of a batch: seed base+i, one sinusoid of
                            amplitude 0.05*sqrt(2^17/N) (keeps the expected
                            matched-filter power near 82 at any N), r0, z0 drawn
@@ -39,6 +42,8 @@ __all__ = [
     "pulsar_series",
     "batch_series",
     "draw_signal_params",
+    "filterbank_noise",
+    "add_at_samples",
 ]
 
 
@@ -147,3 +152,18 @@ def torch_batch_series(count: int, n: int = 1 << 23, base_seed: int = 1000,
         out.append(x)
         params.append((r0, z0))
     return out, params
+
+
+def filterbank_noise(n_chan: int, n_t: int, seed: int) -> np.ndarray:
+    """N(0,1) float32 filterbank [n_chan][n_t] (channel-major) from PCG64(seed)."""
+    return _rng(seed).standard_normal((n_chan, n_t), dtype=np.float64).astype(np.float32)
+
+
+def add_at_samples(fb: np.ndarray, samples, amp: float) -> np.ndarray:
+    """Add `amp` to fb[c, samples[c]] for every channel c (indices given by the
+    caller; samples outside [0, n_t) are skipped).  Returns a new array."""
+    out = np.array(fb, dtype=np.float32, copy=True)
+    for c, t in enumerate(samples):
+        if 0 <= int(t) < out.shape[1]:
+            out[c, int(t)] += np.float32(amp)
+    return out

@@ -488,6 +488,68 @@ def test_interbin_search_recovers_half_bin_sinusoid():
 
 
 # --------------------------------------------------------------------------
+# dedispersion (upstream of the search)
+# --------------------------------------------------------------------------
+def test_dm_delay_textbook_value():
+    """DM 100 pc cm^-3 between 1400 and 1200 MHz: 76.44 ms (4.148808 ms x 100 x
+    (1/1.2^2 - 1/1.4^2) with frequencies in GHz), 1194 samples of 64 us; the top
+    channel has no delay."""
+    d = O.dm_delays(2, 1400.0, 200.0, 64e-6, 100.0, 0.0, 1)
+    assert d.shape == (1, 2)
+    assert d[0, 0] == 0 and d[0, 1] == 1194
+    d2 = O.dm_delays(2, 1400.0, 200.0, 1e-6, 100.0, 0.0, 1)
+    assert abs(d2[0, 1] * 1e-6 - 0.0764380) < 2e-6
+
+
+def test_dm_delays_monotone_and_zero_dm():
+    d = O.dm_delays(64, 1500.0, 2.0, 64e-6, 0.0, 5.0, 20)
+    assert np.all(d[0] == 0)                       # DM 0
+    assert np.all(np.diff(d, axis=0) >= 0)         # grows with DM
+    assert np.all(np.diff(d, axis=1) >= 0)         # grows down the band
+    assert np.all(d[:, 0] == 0)
+
+
+def test_dedisperse_zero_dm_is_the_channel_sum():
+    fb = S.filterbank_noise(16, 300, 4)
+    out = O.dedisperse(fb, np.zeros((1, 16), dtype=np.int64), 300)
+    assert np.allclose(out[0], fb.astype(np.float64).sum(axis=0), rtol=0, atol=1e-12)
+
+
+def test_dedisperse_brute_force_small():
+    rng = np.random.default_rng(9)
+    fb = rng.standard_normal((5, 40))
+    delays = rng.integers(0, 12, size=(3, 5))
+    out = O.dedisperse(fb, delays, 33)
+    for d in range(3):
+        for t in range(33):
+            ref = sum(fb[c, t + delays[d, c]] if t + delays[d, c] < 40 else 0.0
+                      for c in range(5))
+            assert abs(out[d, t] - ref) < 1e-12
+
+
+def test_dedisperse_collapses_a_dispersed_pulse():
+    """A unit pulse planted along the delay curve of DM_k lands as one sample of
+    height n_chan at DM_k, and lower at every other DM."""
+    n_chan, n_t, t0 = 32, 2000, 123
+    delays = O.dm_delays(n_chan, 1450.0, 4.0, 256e-6, 0.0, 20.0, 12)
+    k = 7
+    fb = S.add_at_samples(np.zeros((n_chan, n_t), np.float32), t0 + delays[k], 1.0)
+    out = O.dedisperse(fb, delays, 1000)
+    assert out[k, t0] == n_chan
+    assert np.unravel_index(np.argmax(out), out.shape) == (k, t0)
+    others = np.delete(out, k, axis=0)
+    assert others.max() < n_chan
+
+
+def test_dedisperse_counts_zero_past_the_end():
+    n_chan, n_t = 8, 100
+    delays = np.arange(n_chan, dtype=np.int64)[None, :] * 3    # 0, 3, ..., 21
+    out = O.dedisperse(np.ones((n_chan, n_t)), delays, n_t)
+    for t in (0, 78, 79, 90, 99):
+        assert out[0, t] == sum(1 for c in range(n_chan) if t + 3 * c < n_t)
+
+
+# --------------------------------------------------------------------------
 # whole path on the 2^17-sample workload
 # --------------------------------------------------------------------------
 def test_sinusoid_workload_detected_at_expected_cell():
