@@ -425,6 +425,56 @@ fdas_status fdas_profile_read(const fdas_plan *plan, fdas_profile *out);
  */
 fdas_status fdas_selftest_wait_timeout(fdas_plan *plan, int64_t limit_cycles, void *stream);
 
+/* ---------------------------------------------------------------------
+ * Incoherent dedispersion: the stage upstream of the search that turns a
+ * filterbank into DM-trial series (the paper searches 5925 DM trials, §3,
+ * but does not describe this stage; the textbook definition is used).
+ *
+ * Channel c (0 = top of the band) has frequency f_c = f_top_mhz - c df_mhz.
+ * At DM_d = dm_lo + d dm_step (pc cm^-3) its cold-plasma delay relative to
+ * the top of the band, in samples, is
+ *   Delta(c, d) = floor(K DM_d (f_c^-2 - f_top^-2) / tsamp + 1/2),
+ *   K = 4.148808e3 MHz^2 pc^-1 cm^3 s,
+ * evaluated once per plan in FP64 with each operation rounded on its own in
+ * that order (f_c, 1/f_c^2, 1/f_top^2, DM_d, (K DM_d)(a - b), / tsamp,
+ * + 1/2, floor), and the series is
+ *   out[d][t] = sum_{c} in[c][t + Delta(c, d)],  t < n_out,
+ * with samples at or past n_t counted as 0 (FP32 sums in channel order).
+ * --------------------------------------------------------------------- */
+typedef struct fdas_dedisp_plan fdas_dedisp_plan;
+
+typedef struct {
+    int32_t n_chan, n_dm;
+    int64_t n_t, n_out;
+    double f_top_mhz, df_mhz, tsamp, dm_lo, dm_step;
+    int32_t max_delay;        /* largest Delta(c, d)                           */
+    int32_t tile_span;        /* largest delay spread over 32 consecutive DMs  */
+    int64_t workspace_bytes;  /* device memory the plan holds (delay table)   */
+} fdas_dedisp_info;
+
+/* n_chan in [1, 65536], n_dm in [1, 65536], 1 <= n_out <= n_t,
+ * n_chan * n_t <= 2^36, tsamp > 0, f_top_mhz > 0, df_mhz > 0 with the lowest
+ * channel above 0 MHz, dm_lo >= 0, dm_step >= 0: else FDAS_ERR_ARG.  The delay
+ * spread of 32 consecutive DM trials must stay below 25088 samples, else
+ * FDAS_ERR_UNSUPPORTED.  Computes the delay table on the current device
+ * (blocking); *out owns it until fdas_dedisp_plan_destroy. */
+fdas_status fdas_dedisp_plan_create(fdas_dedisp_plan **out, int32_t n_chan, int64_t n_t,
+                                    double f_top_mhz, double df_mhz, double tsamp,
+                                    double dm_lo, double dm_step, int32_t n_dm,
+                                    int64_t n_out);
+void fdas_dedisp_plan_destroy(fdas_dedisp_plan *plan);
+fdas_status fdas_dedisp_get_info(const fdas_dedisp_plan *plan, fdas_dedisp_info *info);
+
+/* The delay table, host int32[n_dm][n_chan]. */
+fdas_status fdas_dedisp_delays(const fdas_dedisp_plan *plan, int32_t *delays_out);
+
+/* filterbank: device float[n_chan][n_t] (channel-major, each channel a time
+ * series).  out: device float[n_dm][n_out]; row d is DM trial d, ready to be
+ * a fdas_series (16-byte aligned when n_out is a multiple of 4).
+ * Asynchronous on `stream`. */
+fdas_status fdas_dedisperse(fdas_dedisp_plan *plan, const float *filterbank, float *out,
+                            void *stream);
+
 /* Thread-local message describing the last failed call ("" if none). */
 const char *fdas_last_error(void);
 

@@ -44,7 +44,9 @@ EXPORTED = ["fdas_opts_default", "fdas_plan_create", "fdas_plan_destroy",
             "fdas_harmonic_sums", "fdas_threshold", "fdas_template_bank",
             "fdas_spectrum_static", "fdas_fourier_power", "fdas_fourier_power_backward",
             "fdas_refine", "fdas_profile_enable", "fdas_profile_read",
-            "fdas_selftest_wait_timeout", "fdas_last_error", "fdas_version"]
+            "fdas_selftest_wait_timeout", "fdas_last_error", "fdas_version",
+            "fdas_dedisp_plan_create", "fdas_dedisp_plan_destroy", "fdas_dedisp_get_info",
+            "fdas_dedisp_delays", "fdas_dedisperse"]
 
 
 class fdas_opts(Structure):
@@ -108,6 +110,13 @@ class fdas_profile(Structure):
 PROFILE_GROUPS = ["spectrum", "correlate", "harmonic", "finish"]
 
 
+class fdas_dedisp_info(Structure):
+    _fields_ = [("n_chan", c_int32), ("n_dm", c_int32), ("n_t", c_int64), ("n_out", c_int64),
+                ("f_top_mhz", c_double), ("df_mhz", c_double), ("tsamp", c_double),
+                ("dm_lo", c_double), ("dm_step", c_double), ("max_delay", c_int32),
+                ("tile_span", c_int32), ("workspace_bytes", c_int64)]
+
+
 class FdasError(RuntimeError):
     def __init__(self, status: int, where: str, msg: str):
         super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
@@ -130,6 +139,18 @@ def lib() -> ctypes.CDLL:
         L.fdas_plan_create.argtypes = [POINTER(c_void_p), c_int64, c_double, c_double,
                                        c_double, c_int32, c_int32, POINTER(fdas_opts)]
         L.fdas_plan_create.restype = c_int32
+        L.fdas_dedisp_plan_create.argtypes = [POINTER(c_void_p), c_int32, c_int64, c_double,
+                                              c_double, c_double, c_double, c_double, c_int32,
+                                              c_int64]
+        L.fdas_dedisp_plan_create.restype = c_int32
+        L.fdas_dedisp_plan_destroy.argtypes = [c_void_p]
+        L.fdas_dedisp_plan_destroy.restype = None
+        L.fdas_dedisp_get_info.argtypes = [c_void_p, POINTER(fdas_dedisp_info)]
+        L.fdas_dedisp_get_info.restype = c_int32
+        L.fdas_dedisp_delays.argtypes = [c_void_p, c_void_p]
+        L.fdas_dedisp_delays.restype = c_int32
+        L.fdas_dedisperse.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
+        L.fdas_dedisperse.restype = c_int32
         L.fdas_plan_destroy.argtypes = [c_void_p]
         L.fdas_plan_destroy.restype = None
         L.fdas_plan_get_info.argtypes = [c_void_p, POINTER(fdas_plan_info)]
@@ -207,6 +228,32 @@ def fdas_plan_get_info(plan) -> fdas_plan_info:
     info = fdas_plan_info()
     _check(lib().fdas_plan_get_info(plan, ctypes.byref(info)), "fdas_plan_get_info")
     return info
+
+
+def fdas_dedisp_plan_create(n_chan, n_t, f_top_mhz, df_mhz, tsamp, dm_lo, dm_step, n_dm,
+                            n_out) -> c_void_p:
+    h = c_void_p()
+    _check(lib().fdas_dedisp_plan_create(ctypes.byref(h), n_chan, n_t, f_top_mhz, df_mhz, tsamp,
+                                         dm_lo, dm_step, n_dm, n_out), "fdas_dedisp_plan_create")
+    return h
+
+
+def fdas_dedisp_plan_destroy(plan) -> None:
+    lib().fdas_dedisp_plan_destroy(plan)
+
+
+def fdas_dedisp_get_info(plan) -> fdas_dedisp_info:
+    info = fdas_dedisp_info()
+    _check(lib().fdas_dedisp_get_info(plan, ctypes.byref(info)), "fdas_dedisp_get_info")
+    return info
+
+
+def fdas_dedisp_delays(plan, delays_ptr) -> None:
+    _check(lib().fdas_dedisp_delays(plan, delays_ptr), "fdas_dedisp_delays")
+
+
+def fdas_dedisperse(plan, filterbank_ptr, out_ptr, stream=None) -> None:
+    _check(lib().fdas_dedisperse(plan, filterbank_ptr, out_ptr, stream), "fdas_dedisperse")
 
 
 def fdas_search(plan, batch, n_series, cands_ptr, capacity, stream=None):
@@ -507,3 +554,38 @@ def FourierPower():
     if _FP is None:
         _FP = _fourier_power_function()
     return _FP
+
+
+class DedispPlan:
+    """Owns an fdas_dedisp_plan: incoherent dedispersion of a filterbank
+    (device float[n_chan][n_t]) into n_dm DM-trial series of n_out samples."""
+
+    def __init__(self, n_chan, n_t, f_top_mhz, df_mhz, tsamp, dm_lo, dm_step, n_dm, n_out):
+        self.handle = fdas_dedisp_plan_create(n_chan, n_t, f_top_mhz, df_mhz, tsamp, dm_lo,
+                                              dm_step, n_dm, n_out)
+        self.info = fdas_dedisp_get_info(self.handle)
+
+    def close(self):
+        if self.handle:
+            fdas_dedisp_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def delays(self):
+        d = np.zeros((self.info.n_dm, self.info.n_chan), dtype=np.int32)
+        fdas_dedisp_delays(self.handle, d.ctypes.data_as(c_void_p))
+        return d
+
+    def dedisperse(self, filterbank, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty((self.info.n_dm, self.info.n_out), dtype=torch.float32,
+                              device=filterbank.device)
+        fdas_dedisperse(self.handle, c_void_p(filterbank.data_ptr()), c_void_p(out.data_ptr()),
+                        _stream_ptr(stream))
+        return out

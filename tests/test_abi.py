@@ -52,6 +52,26 @@ def test_struct_layouts(capi):
     assert ctypes.sizeof(capi.fdas_refined) == capi.REFINED_DTYPE.itemsize == 40
 
 
+def test_dedisp_info_layout_and_validation(capi):
+    assert ctypes.sizeof(capi.fdas_dedisp_info) == 80
+    bad = [
+        ((0, 1000, 1400.0, 1.0, 64e-6, 0.0, 1.0, 4, 500), "n_chan"),
+        ((16, 1000, 1400.0, 1.0, 64e-6, 0.0, 1.0, 0, 500), "n_dm"),
+        ((16, 1000, 1400.0, 1.0, 64e-6, 0.0, 1.0, 4, 1001), "n_out"),
+        ((16, 1000, 1400.0, 100.0, 64e-6, 0.0, 1.0, 4, 500), "lowest channel"),
+        ((16, 1000, 1400.0, 1.0, 0.0, 0.0, 1.0, 4, 500), "tsamp"),
+        ((16, 1000, 1400.0, 1.0, 64e-6, -1.0, 1.0, 4, 500), "dm_lo"),
+    ]
+    for args, frag in bad:
+        with pytest.raises(capi.FdasError) as ei:
+            capi.fdas_dedisp_plan_create(*args)
+        assert ei.value.status == capi.FDAS_ERR_ARG and frag in str(ei.value), (args, str(ei.value))
+    lib = capi.lib()
+    assert lib.fdas_dedisperse(None, None, None, None) == capi.FDAS_ERR_ARG
+    assert lib.fdas_dedisp_delays(None, None) == capi.FDAS_ERR_ARG
+    lib.fdas_dedisp_plan_destroy(None)
+
+
 def test_defaults_and_version(capi):
     o = capi.fdas_opts_default()
     assert o.precision == capi.FDAS_FP32 and o.threshold_sigma == 6.0
