@@ -398,6 +398,11 @@ def run_gpu(args, rank, world, local_rank, dist):
               "note": "same search on the half-bin plane (interbinning: complex correlation, "
                       "then |F(r)|^2 and (pi/4)^2 |F(r) - F(r+1)|^2; 2x the plane cells)"}
 
+    # --- dedispersion upstream of the search: filterbank -> DM-trial series --
+    dd = None
+    if not args.no_dedisp:
+        dd = run_dedisp(args, dev, capi, world)
+
     # --- uneven batch: full-length and decimated series in one call, graph ---
     uneven = None
     if not args.no_uneven:
@@ -491,9 +496,62 @@ def run_gpu(args, rank, world, local_rank, dist):
         line["fundamental_harmonic"] = fund
     if ib is not None:
         line["interbin"] = ib
+    if dd is not None:
+        line["dedispersion"] = dd
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
+
+
+# dedispersion workload: 1024 channels of 0.25 MHz below 1670 MHz, 64 us
+# samples, 2^23 output samples per DM trial (the search's series length),
+# 128 DM trials from 0 in steps of 0.25 pc cm^-3
+DD_CHAN, DD_FTOP, DD_DF, DD_NDM, DD_DMSTEP = 1024, 1670.0, 0.25, 128, 0.25
+# shared memory delivers one 4-byte word per lane per clock per SM: 32 words
+# x 152 SMs x 2.07 GHz, the bound of a sum that reads every term from it
+SMEM_WORDS_PEAK_T = 32 * 152 * 2.07e9 / 1e12
+
+
+def run_dedisp(args, dev, capi, world):
+    """Incoherent dedispersion of a synthetic N(0,1) filterbank into DM-trial
+    series: DM-trials/s and additions/s against the shared-memory bound."""
+    import torch
+    n_out = N_SAMPLES
+    probe = capi.DedispPlan(DD_CHAN, n_out + 1, DD_FTOP, DD_DF, TSAMP, 0.0, DD_DMSTEP, DD_NDM,
+                            n_out)
+    n_t = n_out + probe.info.max_delay
+    probe.close()
+    plan = capi.DedispPlan(DD_CHAN, n_t, DD_FTOP, DD_DF, TSAMP, 0.0, DD_DMSTEP, DD_NDM, n_out)
+    g = torch.Generator(device=dev)
+    g.manual_seed(77)
+    fb = torch.randn(DD_CHAN, n_t, generator=g, device=dev, dtype=torch.float32)
+    out = torch.empty(DD_NDM, n_out, device=dev, dtype=torch.float32)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        plan.dedisperse(fb, out)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.dedisperse(fb, out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    adds = DD_CHAN * DD_NDM * n_out
+    res = {"value": DD_NDM * world / (ms / 1000.0), "unit": "DM-trials/s",
+           "ms_per_launch": ms, "n_chan": DD_CHAN, "n_dm": DD_NDM, "n_out": n_out,
+           "tile_span": plan.info.tile_span, "max_delay": plan.info.max_delay,
+           "roofline": {"bound": "smem", "achieved": adds / (ms / 1000.0) / 1e12,
+                        "peak": SMEM_WORDS_PEAK_T, "unit": "T additions/s",
+                        "frac": adds / (ms / 1000.0) / 1e12 / SMEM_WORDS_PEAK_T},
+           "note": "dedisperse_kernel, inputs larger than L2 (filterbank 34 GB); one 4-byte "
+                   "shared-memory word per addition is the bound (less where two DM trials "
+                   "share a delay)"}
+    plan.close()
+    del fb, out
+    torch.cuda.empty_cache()
+    return res
 
 
 def run_uneven(args, dev, capi, S, timed_uneven):
@@ -551,6 +609,8 @@ def main():
                     help="skip the fundamental-indexed harmonic-sum leg")
     ap.add_argument("--no-interbin", action="store_true",
                     help="skip the interbinning (half-bin plane) leg")
+    ap.add_argument("--no-dedisp", action="store_true",
+                    help="skip the dedispersion leg")
     ap.add_argument("--uneven-batch", type=int, default=64)
     ap.add_argument("--n-log2", type=int, default=23,
                     help="series length 2^n (smaller only for profiling captures)")
