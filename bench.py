@@ -351,7 +351,22 @@ def run_gpu(args, rank, world, local_rank, dist):
     _, prof_bf16, _, _, _ = timed(plan, xs, 1, 1, True)
     # --- e2e: the same calls with the series in pinned host memory ----------
     hosts = [x.cpu().pin_memory() for x in xs]
-    ms_e2e, _, _, _, nf_e2e = timed(plan, hosts, args.steps, max(1, args.warmup // 2))
+    for _ in range(max(1, args.warmup // 2)):
+        plan.search(hosts, trial_ids=ids, capacity=1 << 16)
+    clocks_e2e = ClockSampler(local_rank)
+    barrier()
+    clocks_e2e.start()
+    step_ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    step_ev[0].record(stream)
+    nf_e2e = 0
+    for i in range(args.steps):
+        _, _, nf = plan.search(hosts, trial_ids=ids, capacity=1 << 16)
+        nf_e2e += nf
+        step_ev[i + 1].record(stream)
+    barrier()
+    ck_e2e = clocks_e2e.stop()
+    ms_e2e = max_over_ranks(step_ev[0].elapsed_time(step_ev[-1]))
+    e2e_steps = [round(step_ev[i].elapsed_time(step_ev[i + 1]), 2) for i in range(args.steps)]
     del hosts
     plan.close()
     # --- FP32 path on the same inputs ---------------------------------------
@@ -475,7 +490,8 @@ def run_gpu(args, rank, world, local_rank, dist):
         "kernels": k_bf16,
         "e2e": {"value": trials / (ms_e2e / 1000.0), "unit": UNIT,
                 "h2d_bytes_per_step": 4 * N_SAMPLES * args.batch,
-                "d2h_bytes_per_step": 20 * (nf_e2e // max(1, args.steps)) + 16},
+                "d2h_bytes_per_step": 20 * (nf_e2e // max(1, args.steps)) + 16,
+                "step_ms": e2e_steps, "clocks": ck_e2e},
         "gpu_launches": launches,
         "clocks": ck,
         "joules_per_trial": (j_bf16 / (args.batch * args.steps)) if j_bf16 else None,
