@@ -410,8 +410,9 @@ def run_gpu(args, rank, world, local_rank, dist):
               "kernels_ms_per_trial": {g: prof_i[g][2] / max(1, prof_i["trials"])
                                        for g in ("spectrum", "correlate", "harmonic")},
               "candidates_per_trial": nf_i / (nb * args.steps),
-              "note": "same search on the half-bin plane (interbinning: complex correlation, "
-                      "then |F(r)|^2 and (pi/4)^2 |F(r) - F(r+1)|^2; 2x the plane cells)"}
+              "note": "same search on the half-bin plane (interbinning: |F(r)|^2 and "
+                      "(pi/4)^2 |F(r) - F(r+1)|^2 written by the tensor-core epilogue; 2x the "
+                      "plane cells)"}
 
     # --- dedispersion upstream of the search: filterbank -> DM-trial series --
     dd = None

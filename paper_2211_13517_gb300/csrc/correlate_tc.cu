@@ -35,9 +35,15 @@
 // taps as rounded to 16 bits: P is |F|^2 / E'_z with E'_z = sum_e |g'_z[e]|^2
 // of the rounded taps g', one FP32 factor per template.
 //
-// With kCplx the epilogue writes the complex F / sqrt(E'_z) instead (4
-// consecutive bins per template as one 16-byte store, no statistics): the
-// input of interbinning, which needs F at neighbouring bins.
+// kMode selects the epilogue: kPower writes P as above; kCplx writes the
+// complex F / sqrt(E'_z) (4 consecutive bins per template as one 16-byte
+// store, no statistics); kInterbin writes the half-bin plane directly: the 4
+// bins of a row and their 4 half bins (pi/4)^2 |F(r) - F(r+1)|^2 as one
+// 16-byte store into the 2 N_r-column plane, F(r + 1) of a row's last bin
+// taken from the next lane.  The last lane of each warp has no next row in
+// the warp: it leaves that half bin for tc_ib_fixup_kernel, and lanes 0 and
+// 31 record their first and last F of the tile in an edge table from which
+// the fix-up computes it (with F(N_r) = 0 after the last tile).
 #include <algorithm>
 
 #include "fdas_internal.cuh"
@@ -105,14 +111,18 @@ __device__ __forceinline__ float2 fsub2(float2 a, float2 b) {
     return __fadd2_rn(a, make_float2(-b.x, -b.y));
 }
 
-template <class P, bool kCplx>
+enum { kPower = 0, kCplx = 1, kInterbin = 2 };
+constexpr float kIbFactor = 0.61685027506808491f;   // (pi/4)^2
+
+template <class P, int kMode>
 __global__ void __launch_bounds__(kTcThreads, 1)
     correlate_tc_kernel(const typename P::cpx *__restrict__ spec_pad,
                         const unsigned char *__restrict__ bank_img,
                         const TcChunk *__restrict__ chunks, int n_ch,
                         const float *__restrict__ inv_energy,
                         void *__restrict__ out, double2 *__restrict__ partials,
-                        int64_t n_r, int win_bytes, int b_bytes_max, unsigned int *flags) {
+                        int64_t n_r, int win_bytes, int b_bytes_max, unsigned int *flags,
+                        float4 *__restrict__ edges) {
     extern __shared__ __align__(128) unsigned char tc_smem[];
     unsigned char *const sB = tc_smem;
     unsigned char *const sA = tc_smem + b_bytes_max;
@@ -242,7 +252,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         int c, cur = -1, zvalid = 0;
         int64_t t;
         int j = 0;
-        float sc[kTcZpt];   // 1 / E'_z (power) or 1 / sqrt(E'_z) (complex)
+        float sc[kTcZpt];   // 1 / E'_z (power) or 1 / sqrt(E'_z) (complex, half bins)
+        int zfirst = 0;     // first template of this warp's part of the chunk
         typename P::real *zrow = static_cast<typename P::real *>(out);
         typename P::cpx *zcrow = static_cast<typename P::cpx *>(out);
         float2 s1 = make_float2(0.f, 0.f), s2 = make_float2(0.f, 0.f);
@@ -259,12 +270,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll
                 for (int k = 0; k < kTcZpt; ++k) {
                     const float ie = k < zvalid ? __ldg(inv_energy + zb + k) : 0.f;
-                    sc[k] = kCplx ? sqrtf(ie) : ie;
+                    sc[k] = kMode == kPower ? ie : sqrtf(ie);
                 }
-                if constexpr (kCplx)
+                if constexpr (kMode == kCplx)
                     zcrow = static_cast<typename P::cpx *>(out) + (int64_t)zb * n_r + 4 * row;
+                else if constexpr (kMode == kInterbin)
+                    zrow = static_cast<typename P::real *>(out) + (int64_t)zb * 2 * n_r + 8 * row;
                 else
                     zrow = static_cast<typename P::real *>(out) + (int64_t)zb * n_r + 4 * row;
+                zfirst = zb;
             }
             const int b = j & 1;
             const bool got = mbar_wait(&acc_full[b], (j >> 1) & 1);
@@ -282,7 +296,58 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[b]);
-            if constexpr (kCplx) {
+            if constexpr (kMode == kInterbin) {
+                typename P::real *o = zrow + t * (2 * kTcTile);
+                const float2 ib = make_float2(kIbFactor, kIbFactor);
+#pragma unroll
+                for (int k = 0; k < kTcZpt; ++k) {
+                    if (k < zvalid) {   // warp-uniform: the shuffles see every lane
+                        const float2 sk = make_float2(sc[k], sc[k]);
+                        const float2 re01 = __fmul2_rn(make_float2(__uint_as_float(v[k][0]), __uint_as_float(v[k][1])), sk);
+                        const float2 re23 = __fmul2_rn(make_float2(__uint_as_float(v[k][2]), __uint_as_float(v[k][3])), sk);
+                        const float2 im01 = __fmul2_rn(make_float2(__uint_as_float(v[k][4]), __uint_as_float(v[k][5])), sk);
+                        const float2 im23 = __fmul2_rn(make_float2(__uint_as_float(v[k][6]), __uint_as_float(v[k][7])), sk);
+                        // F(r + 4) of this row's last bin is the next row's first bin
+                        const float nre = __shfl_down_sync(0xffffffffu, re01.x, 1);
+                        const float nim = __shfl_down_sync(0xffffffffu, im01.x, 1);
+                        const float2 p01 = __ffma2_rn(re01, re01, __fmul2_rn(im01, im01));
+                        const float2 p23 = __ffma2_rn(re23, re23, __fmul2_rn(im23, im23));
+                        const float2 dr01 = fsub2(re01, make_float2(re01.y, re23.x));
+                        const float2 di01 = fsub2(im01, make_float2(im01.y, im23.x));
+                        const float2 dr23 = fsub2(re23, make_float2(re23.y, nre));
+                        const float2 di23 = fsub2(im23, make_float2(im23.y, nim));
+                        const float2 q01 = __fmul2_rn(__ffma2_rn(dr01, dr01, __fmul2_rn(di01, di01)), ib);
+                        float2 q23 = __fmul2_rn(__ffma2_rn(dr23, dr23, __fmul2_rn(di23, di23)), ib);
+                        if (lane == 31) {
+                            // the next row is in another warp or tile: the
+                            // fix-up kernel writes this half bin
+                            q23.y = 0.f;
+                            const int64_t e = ((int64_t)(zfirst + k) * n_tiles + t) * 4 + quarter;
+                            reinterpret_cast<float2 *>(edges + e)[1] = make_float2(re23.y, im23.y);
+                        }
+                        if (lane == 0) {
+                            const int64_t e = ((int64_t)(zfirst + k) * n_tiles + t) * 4 + quarter;
+                            reinterpret_cast<float2 *>(edges + e)[0] = make_float2(re01.x, im01.x);
+                        }
+                        s1 = __fadd2_rn(s1, __fadd2_rn(__fadd2_rn(p01, p23), __fadd2_rn(q01, q23)));
+                        s2 = __ffma2_rn(p01, p01, s2);
+                        s2 = __ffma2_rn(p23, p23, s2);
+                        s2 = __ffma2_rn(q01, q01, s2);
+                        s2 = __ffma2_rn(q23, q23, s2);
+                        const float2 pss = make_float2(ps, ps);
+                        const typename P::cpx w0 = P::st(__fmul2_rn(make_float2(p01.x, q01.x), pss));
+                        const typename P::cpx w1 = P::st(__fmul2_rn(make_float2(p01.y, q01.y), pss));
+                        const typename P::cpx w2 = P::st(__fmul2_rn(make_float2(p23.x, q23.x), pss));
+                        const typename P::cpx w3 = P::st(__fmul2_rn(make_float2(p23.y, q23.y), pss));
+                        uint4 u;
+                        memcpy(&u.x, &w0, 4);
+                        memcpy(&u.y, &w1, 4);
+                        memcpy(&u.z, &w2, 4);
+                        memcpy(&u.w, &w3, 4);
+                        *reinterpret_cast<uint4 *>(o + (int64_t)k * 2 * n_r) = u;
+                    }
+                }
+            } else if constexpr (kMode == kCplx) {
                 typename P::cpx *oc = zcrow + t * kTcTile;
 #pragma unroll
                 for (int k = 0; k < kTcZpt; ++k) {
@@ -299,7 +364,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 }
                 ++j;
                 continue;
-            }
+            } else {
             typename P::real *o = zrow + t * kTcTile;
 #pragma unroll
             for (int k = 0; k < kTcZpt; ++k) {
@@ -321,6 +386,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     memcpy(&w.y, &hi, 4);
                     *reinterpret_cast<uint2 *>(o + (int64_t)k * n_r) = w;
                 }
+            }
             }
             // FP32 within a tile, compensated FP32 across tiles
             {
@@ -426,24 +492,86 @@ __global__ void tc_energy_kernel(float *__restrict__ inv_energy, const double *_
     if (threadIdx.x == 0) inv_energy[iz] = sh[0] > 0.0 ? (float)(1.0 / sh[0]) : 0.f;
 }
 
+// The half bins the interbinning epilogue leaves: the last row of each
+// warp's 32 rows, whose next bin belongs to another warp or tile.  Entry
+// (z, tile, quarter) of the edge table holds that quarter's first F (lane 0,
+// .x .y) and last F (lane 31, .z .w); the half bin after the last F uses the
+// next entry's first F, or F(N_r) = 0 after the last tile.  One FP64 partial
+// (sum Q, sum Q^2) per CTA, after the tensor kernel's.
+template <class P>
+__global__ void __launch_bounds__(256)
+    tc_ib_fixup_kernel(const float4 *__restrict__ edges, typename P::real *__restrict__ plane,
+                       double2 *__restrict__ partials, int64_t n_r, int n_z) {
+    __shared__ double red[2][8];
+    const int64_t n_tiles = n_r / kTcTile;
+    const int64_t n = (int64_t)n_z * n_tiles * 4;
+    float s1 = 0.f, s2 = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) {
+        const int q = (int)(i & 3);
+        const int64_t zt = i >> 2;
+        const int64_t t = zt % n_tiles, z = zt / n_tiles;
+        const float4 a = edges[i];
+        float2 nx = make_float2(0.f, 0.f);
+        if (q < 3 || t + 1 < n_tiles) {
+            const float4 b = edges[i + 1];
+            nx = make_float2(b.x, b.y);
+        }
+        const float dr = a.z - nx.x, di = a.w - nx.y;
+        const float Q = kIbFactor * fmaf(dr, dr, di * di);
+        const int64_t r = t * kTcTile + 128 * q + 127;
+        plane[z * 2 * n_r + 2 * r + 1] = P::str(Q * P::plane_scale);
+        s1 += Q;
+        s2 = fmaf(Q, Q, s2);
+    }
+    double a1 = s1, a2 = s2;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        a1 += __shfl_down_sync(0xffffffffu, a1, off);
+        a2 += __shfl_down_sync(0xffffffffu, a2, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = a1;
+        red[1][threadIdx.x >> 5] = a2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t1 = 0.0, t2 = 0.0;
+        for (int w = 0; w < 8; ++w) {
+            t1 += red[0][w];
+            t2 += red[1][w];
+        }
+        partials[blockIdx.x] = make_double2(t1, t2);
+    }
+}
+
+int tc_ib_fixup_ctas(const Plan &p) {
+    const int64_t n = (int64_t)p.n_z * (p.n_r / kTcTile) * 4;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(4 * (int64_t)p.n_sms, (n + 255) / 256));
+}
+
 size_t tc_smem_bytes(int max_ks, int win) {
     const size_t need = (size_t)max_ks * kTcSlab + (size_t)kTcStages * win * 4;
     return std::max(need, kTcMinSmem);
 }
 
-template <class P, bool kCplx>
+template <class P, int kMode>
 fdas_status launch_tc_P(Plan &p, const void *spec_padded, void *plane, double2 *partials,
                         cudaStream_t s) {
     const size_t smem = tc_smem_bytes(p.tc_max_ks, p.tc_win);
-    auto k = correlate_tc_kernel<P, kCplx>;
+    auto k = correlate_tc_kernel<P, kMode>;
     FDAS_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = correlate_tc_ctas(p);
     k<<<grid, kTcThreads, smem, s>>>((const typename P::cpx *)spec_padded,
                                       (const unsigned char *)p.tc_bank, p.tc_chunks, p.tc_n_ch,
                                       p.tc_inv_energy, plane, partials, p.n_r,
                                       p.tc_win * 4,
-                                      p.tc_max_ks * kTcSlab, p.flags);
+                                      p.tc_max_ks * kTcSlab, p.flags, p.tc_edges);
     FDAS_CUDA_TRY(cudaGetLastError());
+    if constexpr (kMode == kInterbin) {
+        tc_ib_fixup_kernel<P><<<tc_ib_fixup_ctas(p), 256, 0, s>>>(
+            p.tc_edges, (typename P::real *)plane, partials + grid, p.n_r, p.n_z);
+        FDAS_CUDA_TRY(cudaGetLastError());
+    }
     return FDAS_OK;
 }
 
@@ -535,15 +663,34 @@ fdas_status launch_correlate_tc(Plan &p, const void *spec_padded, void *plane, d
                                 cudaStream_t s, bool cplx) {
     switch (p.prec) {
         case FDAS_BF16:
-            return cplx ? launch_tc_P<PrecBF16, true>(p, spec_padded, plane, partials, s)
-                        : launch_tc_P<PrecBF16, false>(p, spec_padded, plane, partials, s);
+            return cplx ? launch_tc_P<PrecBF16, kCplx>(p, spec_padded, plane, partials, s)
+                        : launch_tc_P<PrecBF16, kPower>(p, spec_padded, plane, partials, s);
         case FDAS_FP16:
-            return cplx ? launch_tc_P<PrecF16, true>(p, spec_padded, plane, partials, s)
-                        : launch_tc_P<PrecF16, false>(p, spec_padded, plane, partials, s);
+            return cplx ? launch_tc_P<PrecF16, kCplx>(p, spec_padded, plane, partials, s)
+                        : launch_tc_P<PrecF16, kPower>(p, spec_padded, plane, partials, s);
         default:
             set_error("tensor-core correlation: 16-bit precisions only");
             return FDAS_ERR_UNSUPPORTED;
     }
 }
+
+fdas_status launch_interbin_tc(Plan &p, const void *spec_padded, void *plane, double2 *partials,
+                               cudaStream_t s) {
+    if (!p.tc_edges) {
+        set_error("tensor-core interbinning: the plan holds no edge table");
+        return FDAS_ERR_UNSUPPORTED;
+    }
+    switch (p.prec) {
+        case FDAS_BF16: return launch_tc_P<PrecBF16, kInterbin>(p, spec_padded, plane, partials, s);
+        case FDAS_FP16: return launch_tc_P<PrecF16, kInterbin>(p, spec_padded, plane, partials, s);
+        default:
+            set_error("tensor-core correlation: 16-bit precisions only");
+            return FDAS_ERR_UNSUPPORTED;
+    }
+}
+
+int interbin_tc_partials(const Plan &p) { return correlate_tc_ctas(p) + tc_ib_fixup_ctas(p); }
+
+int64_t tc_edge_bytes(const Plan &p) { return (int64_t)p.n_z * (p.n_r / kTcTile) * 4 * (int64_t)sizeof(float4); }
 
 }  // namespace fdas

@@ -168,6 +168,7 @@ struct Plan {
     TcChunk *tc_chunks = nullptr;
     void *tc_bank = nullptr;
     float *tc_inv_energy = nullptr;   // [n_z] 1 / energy of the 16-bit taps
+    float4 *tc_edges = nullptr;       // interbinning: [n_z][n_r / 512][4] first/last F
     int tc_n_ch = 0, tc_max_ks = 0, tc_win = 0;
     // FFT split of the N/2-point complex FFT in the spectrum stage
     int fft_m1, fft_m2;     // M = m1 * m2 (m1 = 1: single pass)
@@ -234,6 +235,12 @@ fdas_status launch_tc_bank(Plan &p, cudaStream_t s);
 fdas_status launch_correlate_tc(Plan &p, const void *spec_padded, void *plane, double2 *partials,
                                 cudaStream_t s, bool cplx);
 int correlate_tc_ctas(const Plan &p);
+// interbinning fused into the tensor-core epilogue: the half-bin plane and
+// its partials (interbin_tc_partials of them), using the plan's edge table
+fdas_status launch_interbin_tc(Plan &p, const void *spec_padded, void *plane, double2 *partials,
+                               cudaStream_t s);
+int interbin_tc_partials(const Plan &p);
+int64_t tc_edge_bytes(const Plan &p);
 int64_t tc_bank_bytes(const std::vector<TcChunk> &table);
 // interbinning: complex F [n_z][n_r] -> plane [n_z][2 n_r] and one FP64
 // (sum P, sum P^2) partial per CTA

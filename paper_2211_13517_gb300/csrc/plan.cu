@@ -78,6 +78,7 @@ static void free_plan_memory(Plan *p) {
     cudaFree(p->tc_chunks);
     cudaFree(p->tc_bank);
     cudaFree(p->tc_inv_energy);
+    cudaFree(p->tc_edges);
     for (int b = 0; b < 2; ++b) {
         cudaFree(p->plane[b]);
         cudaFree(p->partials[b]);
@@ -178,6 +179,21 @@ static void set_length(Plan &p, int64_t n) {
 }
 
 // the plan's buffers with the geometry of a shorter series
+// the correlation (and interbinning) of one series into `plane`, leaving
+// plane_partials(v) FP64 partials in `partials`
+static fdas_status launch_plane(Plan &v, const void *spec_pad, void *plane, double2 *partials,
+                                cudaStream_t s) {
+    if (!v.interbin) return launch_correlate(v, spec_pad, plane, partials, s);
+    if (v.correlator == FDAS_CORR_TENSOR) return launch_interbin_tc(v, spec_pad, plane, partials, s);
+    FDAS_TRY(launch_correlate(v, spec_pad, v.corr, partials, s, true));
+    return launch_interbin(v, v.corr, plane, partials, s);
+}
+
+static int plane_partials(const Plan &v) {
+    if (!v.interbin) return correlate_ctas(v);
+    return v.correlator == FDAS_CORR_TENSOR ? interbin_tc_partials(v) : interbin_ctas(v);
+}
+
 // the plan as the statistics and harmonic kernels see it: the plane's
 // columns (half bins with interbinning) in place of the spectral bins
 static Plan harm_view(const Plan &v) {
@@ -297,7 +313,7 @@ static fdas_status create(Plan *&out, int64_t n_samples, double tsamp, double z_
     p.n_zchunk = choose_zchunks(p, p.n_sms);
     // partials serve every length the plan accepts (N, N/2, ..., 2^10) and
     // any template chunking up to 32
-    p.partials_cap = std::max<int64_t>((int64_t)p.n_seg * 32, 4 * (int64_t)p.n_sms);
+    p.partials_cap = std::max<int64_t>((int64_t)p.n_seg * 32, 5 * (int64_t)p.n_sms);
     for (int64_t n = n_samples; n >= (1 << 10); n /= 2) {
         Plan v = p;
         set_length(v, n);
@@ -360,7 +376,11 @@ static fdas_status create(Plan *&out, int64_t n_samples, double tsamp, double z_
         PLAN_CUDA(cudaEventCreateWithFlags(&p.ev_conv[b], cudaEventDisableTiming));
         PLAN_CUDA(cudaEventCreateWithFlags(&p.ev_hsum[b], cudaEventDisableTiming));
     }
-    if (p.interbin) PLAN_TRY(dalloc(p, &p.corr, cb * (size_t)p.n_z * (size_t)p.n_r));
+    // interbinning: the FFT correlators write the complex plane for the
+    // interbinning kernel; the tensor-core epilogue writes the half-bin plane
+    // itself and needs only its edge table (allocated below)
+    if (p.interbin && p.correlator != FDAS_CORR_TENSOR)
+        PLAN_TRY(dalloc(p, &p.corr, cb * (size_t)p.n_z * (size_t)p.n_r));
     PLAN_TRY(grow_stats(p, 64));
     const int64_t rec_cap = next_pow2(p.max_cands);
     PLAN_TRY(dalloc(p, &p.cand, sizeof(CandRec) * (size_t)rec_cap));
@@ -393,6 +413,7 @@ static fdas_status create(Plan *&out, int64_t n_samples, double tsamp, double z_
         PLAN_TRY(dalloc(p, &p.tc_chunks, sizeof(TcChunk) * tc_table.size()));
         PLAN_TRY(dalloc(p, &p.tc_bank, (size_t)img));
         PLAN_TRY(dalloc(p, &p.tc_inv_energy, sizeof(float) * (size_t)p.n_z));
+        if (p.interbin) PLAN_TRY(dalloc(p, &p.tc_edges, (size_t)tc_edge_bytes(p)));
         PLAN_CUDA(cudaMemcpyAsync(p.tc_chunks, tc_table.data(), sizeof(TcChunk) * tc_table.size(),
                                   cudaMemcpyHostToDevice, p.aux));
         PLAN_TRY(launch_tc_bank(p, p.aux));
@@ -586,26 +607,19 @@ static fdas_status enqueue_batch(Plan &p, const fdas_series *batch, int32_t n_se
             FDAS_CUDA_TRY(cudaStreamWaitEvent(s, p.ev_hsum[b], 0));
             if (p.profiling) e1 = mark(s);
         }
-        if (p.interbin) {
-            FDAS_TRY(launch_correlate(v, p.spec_pad, p.corr, p.partials[b], s, true));
-            FDAS_TRY(launch_interbin(v, p.corr, p.plane[b], p.partials[b], s));
-        } else {
-            FDAS_TRY(launch_correlate(v, p.spec_pad, p.plane[b], p.partials[b], s));
-        }
+        FDAS_TRY(launch_plane(v, p.spec_pad, p.plane[b], p.partials[b], s));
         cudaEvent_t e2 = p.profiling ? mark(s) : nullptr;
         FDAS_CUDA_TRY(cudaEventRecord(p.ev_conv[b], s));
         FDAS_CUDA_TRY(cudaStreamWaitEvent(hs, p.ev_conv[b], 0));
         cudaEvent_t e3 = p.profiling ? mark(hs) : nullptr;
         TrialStats *ts = p.stats + rank[t];
         Plan hv = harm_view(v);
-        FDAS_TRY(launch_finalize_stats(hv, p.partials[b],
-                                       p.interbin ? interbin_ctas(v) : correlate_ctas(v), nullptr,
-                                       ts, hs));
+        FDAS_TRY(launch_finalize_stats(hv, p.partials[b], plane_partials(v), nullptr, ts, hs));
         FDAS_TRY(launch_harmonic_threshold(hv, p.plane[b], ts, (uint32_t)rank[t], hs));
         cudaEvent_t e4 = p.profiling ? mark(hs) : nullptr;
         FDAS_CUDA_TRY(cudaEventRecord(p.ev_hsum[b], hs));
         p.launches[FDAS_PROF_SPECTRUM] += (v.fft_m1 == 1 ? 1 : 2) + 1;
-        p.launches[FDAS_PROF_CORRELATE] += p.interbin ? 2 : 1;
+        p.launches[FDAS_PROF_CORRELATE] += p.interbin ? 2 : 1;   // + fix-up or interbinning
         p.launches[FDAS_PROF_HARMONIC] += 2;
         if (p.profiling) {
             iv.push_back({FDAS_PROF_SPECTRUM, e0, e1});
@@ -935,17 +949,10 @@ fdas_status fdas_power_plane(fdas_plan *plan, const void *spectrum, void *plane_
     const size_t cb = cpx_bytes(p.prec);
     FDAS_CUDA_TRY(cudaMemcpyAsync((char *)p.spec_pad + cb * (size_t)p.m_ov, spectrum,
                                   cb * (size_t)p.n_r, cudaMemcpyDeviceToDevice, s));
-    if (p.interbin) {
-        FDAS_TRY(launch_correlate(p, p.spec_pad, p.corr, p.partials[0], s, true));
-        FDAS_TRY(launch_interbin(p, p.corr, plane_out, p.partials[0], s));
-    } else {
-        FDAS_TRY(launch_correlate(p, p.spec_pad, plane_out, p.partials[0], s));
-    }
+    FDAS_TRY(launch_plane(p, p.spec_pad, plane_out, p.partials[0], s));
     if (stats_out) {
         Plan hv = harm_view(p);
-        FDAS_TRY(launch_finalize_stats(hv, p.partials[0],
-                                       p.interbin ? interbin_ctas(p) : correlate_ctas(p), nullptr,
-                                       p.stats, s));
+        FDAS_TRY(launch_finalize_stats(hv, p.partials[0], plane_partials(p), nullptr, p.stats, s));
         FDAS_CUDA_TRY(cudaMemcpyAsync(stats_out, p.stats, 2 * sizeof(double),
                                       cudaMemcpyDeviceToDevice, s));
     }
