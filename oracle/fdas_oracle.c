@@ -92,6 +92,18 @@ void oracle_corr_plane(const double *xr, const double *xi, int64_t n_r, int n_z,
                       Fr + (int64_t)iz * n_r + r, Fi + (int64_t)iz * n_r + r);
 }
 
+/* The complex sum at an explicit list of cells (sampled interbinning checks). */
+void oracle_cells_corr(const double *xr, const double *xi, int64_t n_r,
+                       const int32_t *m, const int64_t *goff, const double *gr,
+                       const double *gi, int64_t n_cells, const int32_t *iz,
+                       const int64_t *r, double *out_re, double *out_im)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t c = 0; c < n_cells; ++c)
+        cell_corr(xr, xi, n_r, r[c], m[iz[c]], gr + goff[iz[c]], gi + goff[iz[c]],
+                  out_re + c, out_im + c);
+}
+
 /* The same sum at an explicit list of cells (sampled checks at full size). */
 void oracle_cells(const double *xr, const double *xi, int64_t n_r,
                   const int32_t *m, const int64_t *goff, const double *gr,

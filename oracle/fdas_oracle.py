@@ -104,6 +104,8 @@ def _c():
         lib.oracle_plane.restype = None
         lib.oracle_corr_plane.argtypes = [P, P, i64, i32, P, P, P, P, P, P]
         lib.oracle_corr_plane.restype = None
+        lib.oracle_cells_corr.argtypes = [P, P, i64, P, P, P, P, i64, P, P, P, P]
+        lib.oracle_cells_corr.restype = None
         lib.oracle_cells.argtypes = [P, P, i64, P, P, P, P, i64, P, P, P]
         lib.oracle_cells.restype = None
         lib.oracle_harmonic_planes.argtypes = [P, i64, i32, i32, i32, P]
@@ -326,6 +328,33 @@ def cell_powers(Xn: np.ndarray, bank: Bank, iz, r) -> np.ndarray:
                       _ptr(gr), _ptr(gi), iz.shape[0], _ptr(iz), _ptr(r),
                       _ptr(out))
     return out
+
+
+def cell_correlations(Xn: np.ndarray, bank: Bank, iz, r) -> np.ndarray:
+    """Complex F at the cells (iz[c], r[c]) by the direct sum; F = 0 for
+    r >= N_r (past the last bin, as interbinning reads it)."""
+    iz = np.ascontiguousarray(np.asarray(iz, dtype=np.int32))
+    r = np.ascontiguousarray(np.asarray(r, dtype=np.int64))
+    xr = np.ascontiguousarray(Xn.real)
+    xi = np.ascontiguousarray(Xn.imag)
+    gr, gi, offs, m = _flat_taps(bank)
+    re = np.empty(iz.shape[0], dtype=np.float64)
+    im = np.empty(iz.shape[0], dtype=np.float64)
+    _c().oracle_cells_corr(_ptr(xr), _ptr(xi), Xn.shape[0], _ptr(m), _ptr(offs), _ptr(gr),
+                           _ptr(gi), iz.shape[0], _ptr(iz), _ptr(r), _ptr(re), _ptr(im))
+    F = re + 1j * im
+    F[r >= Xn.shape[0]] = 0.0
+    return F
+
+
+def half_bin_cells(Xn: np.ndarray, bank: Bank, iz, col) -> np.ndarray:
+    """Cells (iz[c], col[c]) of the half-bin plane (interbin_plane) one by one."""
+    iz = np.asarray(iz, dtype=np.int64)
+    col = np.asarray(col, dtype=np.int64)
+    r = col // 2
+    F0 = cell_correlations(Xn, bank, iz, r)
+    F1 = cell_correlations(Xn, bank, iz, r + 1)
+    return np.where(col % 2 == 0, np.abs(F0) ** 2, INTERBIN_POWER * np.abs(F0 - F1) ** 2)
 
 
 def plane_stats(P: np.ndarray):

@@ -9,6 +9,11 @@
   configuration): each GPU candidate's harmonic sum is recomputed by the
   oracle one cell at a time from the series' own spectrum, and must be
   within 3% and above the oracle threshold minus 3%.
+* Interbinning at full size (BF16, the tensor-core epilogue that writes the
+  half-bin plane): sampled cells of the 193 x 2^23-column plane, every kind of
+  half bin (inside a warp's rows, at a warp edge, at a tile edge, the last
+  column) against the oracle's cell-by-cell direct sums on the spectrum as
+  stored; and each candidate of a two-series search recomputed from cells.
 """
 import numpy as np
 import pytest
@@ -127,4 +132,56 @@ def test_fullsize_bf16_batch_candidates_recomputed_by_oracle(capi):
         # GPU plane agrees with the oracle's to far better than 3%)
         st_ = int(np.log2(c["harm"].max()))
         assert np.all(s_ora >= 0.97 * np.array([G[int(np.log2(h))] for h in c["harm"]]) * 0.98)
+    plan.close()
+
+
+def test_fullsize_interbin_cells_and_candidates(capi):
+    xs, params = S.torch_batch_series(2, N, base_seed=2000, device="cuda")
+    plan = capi.Plan(N, 64e-6, Z_MAX, Z_STEP, L, H, precision=capi.FDAS_BF16, interbin=True)
+    assert plan.info.correlator == capi.FDAS_CORR_TENSOR and plan.info.plane_cols == N
+    g = O.geometry(N, Z_MAX, Z_STEP, H)
+    bank = O.template_bank(g)
+    # sampled plane cells, from the spectrum exactly as the GPU stored it
+    spec = plan.spectrum(xs[0])
+    plane, stats = plan.power_plane(spec)
+    torch.cuda.synchronize()
+    a = spec.float().cpu().numpy().astype(np.float64)
+    Xs = a[0::2] + 1j * a[1::2]
+    rng = np.random.default_rng(5)
+    n_r = N // 2
+    iz = rng.integers(0, g.n_z, 6000)
+    col = rng.integers(0, 2 * n_r, 6000)
+    m = rng.integers(0, n_r // 128, 2000)          # half bins after a warp's last row
+    iz = np.concatenate([iz, rng.integers(0, g.n_z, 2000), np.arange(g.n_z)])
+    col = np.concatenate([col, 2 * (128 * m + 127) + 1, np.full(g.n_z, 2 * n_r - 1)])
+    ref = O.half_bin_cells(Xs, bank, iz, col)
+    got = plane[torch.from_numpy(iz).cuda(), torch.from_numpy(col).cuda()].float().cpu().numpy()
+    mean = float(stats[0])
+    # neighbouring bins bound the error of a half bin (see test_gpu_interbin)
+    nb = np.maximum(O.half_bin_cells(Xs, bank, iz, col - col % 2),
+                    O.half_bin_cells(Xs, bank, iz, np.minimum(col - col % 2 + 2, 2 * n_r - 2)))
+    scale = np.where(col % 2 == 0, np.maximum(ref, mean), np.maximum(np.maximum(ref, nb), mean))
+    tol = np.where(col % 2 == 0, 0.03, 0.06)
+    err = np.abs(got - ref) / scale
+    assert np.all(err < tol), (err.max(), iz[np.argmax(err)], col[np.argmax(err)])
+    assert 0.9 < mean < 1.4
+    del plane
+    # candidates of a two-series search, each recomputed from oracle cells
+    st, cands, nf = plan.search(xs, capacity=1 << 20)
+    assert st == capi.FDAS_OK and nf == len(cands)
+    for t, x in enumerate(xs):
+        c = cands[cands["trial_id"] == t]
+        assert len(c) > 0
+        c = c[np.argsort(-c["sigma"])][:300]           # the strongest ones
+        Xn, _ = O.normalise(O.spectrum(x.cpu().numpy()), 2048)
+        cells, owners = [], []
+        for n, (h, izc, ir) in enumerate(zip(c["harm"], c["iz"], c["ir"])):
+            for k in range(1, int(h) + 1):
+                cells.append(O.harmonic_indices(int(ir), int(izc), g.iz0, H, k * (H // int(h))))
+                owners.append(n)
+        cells = np.array(cells)
+        pw = O.half_bin_cells(Xn, bank, cells[:, 0], cells[:, 1])
+        s_ora = np.bincount(np.array(owners), weights=pw, minlength=len(c))
+        rel = np.abs(c["power"] / s_ora - 1)
+        assert rel.max() <= 0.06, (t, rel.max())
     plan.close()

@@ -465,6 +465,19 @@ def test_interbin_integer_tone_neighbours_and_last_column():
     assert P[0, -1] == pytest.approx((math.pi / 4) ** 2 * abs(F[0, -1]) ** 2, rel=1e-14)
 
 
+def test_half_bin_cells_one_by_one_equal_the_plane():
+    g = O.geometry(1 << 12, 8.0, 2.0, 4)
+    Xn, _ = O.normalise(O.spectrum(S.white_noise(g.n_samples, 3)), 512)
+    bank = O.template_bank(g)
+    P = O.interbin_plane(O.correlation_plane(Xn, bank))
+    rng = np.random.default_rng(1)
+    iz = rng.integers(0, g.n_z, 300)
+    col = rng.integers(0, 2 * g.n_r, 300)
+    col[:5] = 2 * g.n_r - 1                       # the last half bin reads F(N_r) = 0
+    v = O.half_bin_cells(Xn, bank, iz, col)
+    assert np.max(np.abs(v - P[iz, col]) / np.maximum(P[iz, col], 1e-3)) < 1e-12
+
+
 def test_interbin_search_recovers_half_bin_sinusoid():
     """A time-domain sinusoid half-way between bins loses (2/pi)^2 of its power
     on the integer grid; the interbinned plane recovers most of it at the
