@@ -565,8 +565,26 @@ def run_dedisp(args, dev, capi, world):
            "note": "dedisperse_kernel, inputs larger than L2 (filterbank 34 GB); one 4-byte "
                    "shared-memory word per addition is the bound (less where two DM trials "
                    "share a delay)"}
+    # the same trials from an 8-bit filterbank (the usual format; exact sums)
+    del fb
+    n_t16 = (n_t + 15) // 16 * 16
     plan.close()
-    del fb, out
+    plan = capi.DedispPlan(DD_CHAN, n_t16, DD_FTOP, DD_DF, TSAMP, 0.0, DD_DMSTEP, DD_NDM, n_out)
+    fb8 = torch.randint(0, 256, (DD_CHAN, n_t16), generator=g, device=dev, dtype=torch.uint8)
+    for _ in range(args.warmup):
+        plan.dedisperse(fb8, out)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.dedisperse(fb8, out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms8 = e0.elapsed_time(e1) / args.steps
+    res["u8"] = {"value": DD_NDM * world / (ms8 / 1000.0), "unit": "DM-trials/s",
+                 "ms_per_launch": ms8,
+                 "frac_of_smem_bound": adds / (ms8 / 1000.0) / 1e12 / SMEM_WORDS_PEAK_T}
+    plan.close()
+    del fb8, out
     torch.cuda.empty_cache()
     return res
 

@@ -475,6 +475,13 @@ fdas_status fdas_dedisp_delays(const fdas_dedisp_plan *plan, int32_t *delays_out
 fdas_status fdas_dedisperse(fdas_dedisp_plan *plan, const float *filterbank, float *out,
                             void *stream);
 
+/* The same for 8-bit samples (the usual filterbank format): filterbank is
+ * device uint8[n_chan][n_t], 16-byte aligned, with n_t a multiple of 16
+ * (else FDAS_ERR_ARG).  The channel sums are exact int32 sums, stored as
+ * FP32 (exact: n_chan * 255 < 2^24). */
+fdas_status fdas_dedisperse_u8(fdas_dedisp_plan *plan, const uint8_t *filterbank, float *out,
+                               void *stream);
+
 /* Thread-local message describing the last failed call ("" if none). */
 const char *fdas_last_error(void);
 

@@ -46,7 +46,7 @@ EXPORTED = ["fdas_opts_default", "fdas_plan_create", "fdas_plan_destroy",
             "fdas_refine", "fdas_profile_enable", "fdas_profile_read",
             "fdas_selftest_wait_timeout", "fdas_last_error", "fdas_version",
             "fdas_dedisp_plan_create", "fdas_dedisp_plan_destroy", "fdas_dedisp_get_info",
-            "fdas_dedisp_delays", "fdas_dedisperse"]
+            "fdas_dedisp_delays", "fdas_dedisperse", "fdas_dedisperse_u8"]
 
 
 class fdas_opts(Structure):
@@ -151,6 +151,8 @@ def lib() -> ctypes.CDLL:
         L.fdas_dedisp_delays.restype = c_int32
         L.fdas_dedisperse.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
         L.fdas_dedisperse.restype = c_int32
+        L.fdas_dedisperse_u8.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
+        L.fdas_dedisperse_u8.restype = c_int32
         L.fdas_plan_destroy.argtypes = [c_void_p]
         L.fdas_plan_destroy.restype = None
         L.fdas_plan_get_info.argtypes = [c_void_p, POINTER(fdas_plan_info)]
@@ -254,6 +256,10 @@ def fdas_dedisp_delays(plan, delays_ptr) -> None:
 
 def fdas_dedisperse(plan, filterbank_ptr, out_ptr, stream=None) -> None:
     _check(lib().fdas_dedisperse(plan, filterbank_ptr, out_ptr, stream), "fdas_dedisperse")
+
+
+def fdas_dedisperse_u8(plan, filterbank_ptr, out_ptr, stream=None) -> None:
+    _check(lib().fdas_dedisperse_u8(plan, filterbank_ptr, out_ptr, stream), "fdas_dedisperse_u8")
 
 
 def fdas_search(plan, batch, n_series, cands_ptr, capacity, stream=None):
@@ -558,7 +564,8 @@ def FourierPower():
 
 class DedispPlan:
     """Owns an fdas_dedisp_plan: incoherent dedispersion of a filterbank
-    (device float[n_chan][n_t]) into n_dm DM-trial series of n_out samples."""
+    (device float32 or uint8 [n_chan][n_t]) into n_dm DM-trial series of
+    n_out samples."""
 
     def __init__(self, n_chan, n_t, f_top_mhz, df_mhz, tsamp, dm_lo, dm_step, n_dm, n_out):
         self.handle = fdas_dedisp_plan_create(n_chan, n_t, f_top_mhz, df_mhz, tsamp, dm_lo,
@@ -586,6 +593,7 @@ class DedispPlan:
         if out is None:
             out = torch.empty((self.info.n_dm, self.info.n_out), dtype=torch.float32,
                               device=filterbank.device)
-        fdas_dedisperse(self.handle, c_void_p(filterbank.data_ptr()), c_void_p(out.data_ptr()),
-                        _stream_ptr(stream))
+        fn = fdas_dedisperse_u8 if filterbank.dtype == torch.uint8 else fdas_dedisperse
+        fn(self.handle, c_void_p(filterbank.data_ptr()), c_void_p(out.data_ptr()),
+           _stream_ptr(stream))
         return out

@@ -70,30 +70,59 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// 16-byte global -> shared copy of the first `valid` bytes (the rest zero)
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, int valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(valid)
+                 : "memory");
+}
+
 // acc_a += w[oa + 32k], acc_b += w[ob + 32k]; one load when oa == ob
-__device__ __forceinline__ void add_pair(const float *w, int oa, int ob, float (&acc_a)[kDdPer],
-                                         float (&acc_b)[kDdPer]) {
+template <class T, class A>
+__device__ __forceinline__ void add_pair(const T *w, int oa, int ob, A (&acc_a)[kDdPer],
+                                         A (&acc_b)[kDdPer]) {
     if (oa == ob) {
 #pragma unroll
         for (int k = 0; k < kDdPer; ++k) {
-            const float v = w[oa + 32 * k];
+            const A v = (A)w[oa + 32 * k];
             acc_a[k] += v;
             acc_b[k] += v;
         }
     } else {
 #pragma unroll
         for (int k = 0; k < kDdPer; ++k) {
-            acc_a[k] += w[oa + 32 * k];
-            acc_b[k] += w[ob + 32 * k];
+            acc_a[k] += (A)w[oa + 32 * k];
+            acc_b[k] += (A)w[ob + 32 * k];
         }
     }
 }
 
+// Input sample type T: FP32 samples sum in FP32 (4-byte asynchronous copies
+// of each window, `pitch` = win elements per channel); 8-bit samples sum in
+// int32, exactly (16-byte copies of the window rounded out to 16-byte
+// boundaries, `pitch` = win + 16 bytes per channel, rows 16-byte aligned).
+template <class T>
+struct DdIn;
+template <>
+struct DdIn<float> {
+    using Acc = float;
+    static constexpr int kPad = 0;
+};
+template <>
+struct DdIn<uint8_t> {
+    using Acc = int;
+    static constexpr int kPad = 16;
+};
+
+template <class T>
 __global__ void __launch_bounds__(kDdThreads, 2)
-    dedisperse_kernel(const float *__restrict__ fb, const int32_t *__restrict__ delays,
+    dedisperse_kernel(const T *__restrict__ fb, const int32_t *__restrict__ delays,
                       float *__restrict__ out, int n_chan, int64_t n_t, int n_dm, int64_t n_out,
                       int win, int chan_batch) {
-    extern __shared__ __align__(16) float sw[];   // [2][chan_batch][win]
+    using Acc = typename DdIn<T>::Acc;
+    extern __shared__ __align__(16) unsigned char dd_smem[];   // [2][chan_batch][pitch] of T
+    T *sw = reinterpret_cast<T *>(dd_smem);
+    const int pitch = win + DdIn<T>::kPad;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t t0 = (int64_t)blockIdx.x * kDdT;
     const int d_lo = blockIdx.y * kDdD;
@@ -102,24 +131,34 @@ __global__ void __launch_bounds__(kDdThreads, 2)
     const int32_t *dw[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) dw[q] = delays + (int64_t)min(d_lo + 4 * warp + q, n_dm - 1) * n_chan;
-    float acc[4][kDdPer];
+    Acc acc[4][kDdPer];
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
-        for (int k = 0; k < kDdPer; ++k) acc[q][k] = 0.f;
+        for (int k = 0; k < kDdPer; ++k) acc[q][k] = 0;
 
-    const size_t buf_elems = (size_t)chan_batch * win;
+    const size_t buf_elems = (size_t)chan_batch * pitch;
     auto stage = [&](int cb, int slot) {
         const int nc = min(chan_batch, n_chan - cb);
-        float *dst0 = sw + slot * buf_elems;
+        T *dst0 = sw + slot * buf_elems;
         for (int j = 0; j < nc; ++j) {
             const int64_t base = t0 + __ldg(dl + cb + j);
-            const float *src = fb + (int64_t)(cb + j) * n_t;
-            float *dst = dst0 + (size_t)j * win;
-            for (int i = threadIdx.x; i < win; i += kDdThreads) {
-                const int64_t s = base + i;
-                const bool ok = s < n_t;
-                cp_async4(dst + i, src + (ok ? s : 0), ok);
+            const T *src = fb + (int64_t)(cb + j) * n_t;
+            T *dst = dst0 + (size_t)j * pitch;
+            if constexpr (sizeof(T) == 4) {
+                for (int i = threadIdx.x; i < win; i += kDdThreads) {
+                    const int64_t s = base + i;
+                    const bool ok = s < n_t;
+                    cp_async4(dst + i, src + (ok ? s : 0), ok);
+                }
+            } else {
+                const int64_t b16 = base & ~(int64_t)15;
+                for (int i = threadIdx.x; i < pitch / 16; i += kDdThreads) {
+                    const int64_t s = b16 + 16 * (int64_t)i;
+                    const int64_t left = n_t - s;
+                    const int valid = left <= 0 ? 0 : (left >= 16 ? 16 : (int)left);
+                    cp_async16(dst + 16 * i, src + (valid > 0 ? s : 0), valid);
+                }
             }
         }
         cp_async_commit();
@@ -136,11 +175,13 @@ __global__ void __launch_bounds__(kDdThreads, 2)
             cp_async_wait<0>();
         }
         __syncthreads();
-        const float *buf = sw + slot * buf_elems + lane;
+        const T *buf = sw + slot * buf_elems + lane;
         for (int j = 0; j < nc; ++j) {
             const int c = cb + j;
             const int lo = __ldg(dl + c);
-            const float *w = buf + (size_t)j * win;
+            // 8-bit windows start at the 16-byte boundary below the first sample
+            const int shift = sizeof(T) == 1 ? (int)((t0 + lo) & 15) : 0;
+            const T *w = buf + (size_t)j * pitch + shift;
             add_pair(w, __ldg(dw[0] + c) - lo, __ldg(dw[1] + c) - lo, acc[0], acc[1]);
             add_pair(w, __ldg(dw[2] + c) - lo, __ldg(dw[3] + c) - lo, acc[2], acc[3]);
         }
@@ -154,7 +195,7 @@ __global__ void __launch_bounds__(kDdThreads, 2)
 #pragma unroll
         for (int k = 0; k < kDdPer; ++k) {
             const int64_t t = t0 + lane + 32 * k;
-            if (t < n_out) row[t] = acc[q][k];
+            if (t < n_out) row[t] = (float)acc[q][k];
         }
     }
 }
@@ -167,9 +208,29 @@ struct DedispPlan {
     double f_top = 0, df = 0, tsamp = 0, dm_lo = 0, dm_step = 0;
     int32_t *delays = nullptr;   // device [n_dm][n_chan]
     std::vector<int32_t> host_delays;
-    int32_t max_delay = 0, span = 0, win = 0, chan_batch = 0;
+    int32_t max_delay = 0, span = 0, win = 0, chan_batch = 0, chan_batch_u8 = 0;
     int device = 0;
 };
+
+template <class T>
+fdas_status launch_dedisperse(DedispPlan &p, const T *filterbank, float *out, cudaStream_t s) {
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != p.device) cudaSetDevice(p.device);
+    const int pitch = p.win + DdIn<T>::kPad;
+    const int cb = sizeof(T) == 4 ? p.chan_batch : p.chan_batch_u8;
+    const size_t smem = 2 * sizeof(T) * (size_t)pitch * cb;
+    cudaError_t e = cudaFuncSetAttribute(dedisperse_kernel<T>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) {
+        dim3 grid((unsigned)((p.n_out + kDdT - 1) / kDdT), (unsigned)((p.n_dm + kDdD - 1) / kDdD));
+        dedisperse_kernel<T><<<grid, kDdThreads, smem, s>>>(filterbank, p.delays, out, p.n_chan,
+                                                            p.n_t, p.n_dm, p.n_out, p.win, cb);
+        e = cudaGetLastError();
+    }
+    if (cur != p.device) cudaSetDevice(cur);
+    return e == cudaSuccess ? FDAS_OK : cuda_status(e, "dedisperse_kernel");
+}
 
 }  // namespace fdas
 
@@ -261,6 +322,9 @@ fdas_status fdas_dedisp_plan_create(fdas_dedisp_plan **out, int32_t n_chan, int6
             return fail(FDAS_ERR_UNSUPPORTED);
         }
         p->chan_batch = (int)std::max<size_t>(1, std::min<size_t>(8, (96 * 1024) / per_chan));
+        // 8-bit windows: a quarter of the bytes, so more channels per batch
+        const size_t per_chan_u8 = 2 * (size_t)(p->win + 16);
+        p->chan_batch_u8 = (int)std::max<size_t>(1, std::min<size_t>(16, (96 * 1024) / per_chan_u8));
         *out = reinterpret_cast<fdas_dedisp_plan *>(p);
         return FDAS_OK;
     } catch (...) {
@@ -304,22 +368,17 @@ fdas_status fdas_dedisp_delays(const fdas_dedisp_plan *plan, int32_t *delays_out
 fdas_status fdas_dedisperse(fdas_dedisp_plan *plan, const float *filterbank, float *out,
                             void *stream) {
     if (!plan || !filterbank || !out) return dd_arg("NULL argument");
+    return fdas::launch_dedisperse(*reinterpret_cast<DedispPlan *>(plan), filterbank, out,
+                                   (cudaStream_t)stream);
+}
+
+fdas_status fdas_dedisperse_u8(fdas_dedisp_plan *plan, const uint8_t *filterbank, float *out,
+                               void *stream) {
+    if (!plan || !filterbank || !out) return dd_arg("NULL argument");
     DedispPlan &p = *reinterpret_cast<DedispPlan *>(plan);
-    int cur = 0;
-    cudaGetDevice(&cur);
-    if (cur != p.device) cudaSetDevice(p.device);
-    const size_t smem = 2 * sizeof(float) * (size_t)p.win * p.chan_batch;
-    cudaError_t e = cudaFuncSetAttribute(fdas::dedisperse_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) {
-        dim3 grid((unsigned)((p.n_out + fdas::kDdT - 1) / fdas::kDdT),
-                  (unsigned)((p.n_dm + fdas::kDdD - 1) / fdas::kDdD));
-        fdas::dedisperse_kernel<<<grid, fdas::kDdThreads, smem, (cudaStream_t)stream>>>(
-            filterbank, p.delays, out, p.n_chan, p.n_t, p.n_dm, p.n_out, p.win, p.chan_batch);
-        e = cudaGetLastError();
-    }
-    if (cur != p.device) cudaSetDevice(cur);
-    return e == cudaSuccess ? FDAS_OK : fdas::cuda_status(e, "dedisperse_kernel");
+    if (p.n_t % 16 != 0 || ((uintptr_t)filterbank & 15u) != 0)
+        return dd_arg("8-bit filterbanks need n_t a multiple of 16 and a 16-byte aligned pointer");
+    return fdas::launch_dedisperse(p, filterbank, out, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -23,8 +23,9 @@ the paper prints none):
                            (duty 0.05, height 0.054), r0 ~ U[1e4, 4e6],
                            z0 ~ U[-90, 90], all drawn from the series seed.
 * ``filterbank_noise``  -- the input of dedispersion: N(0,1) channels x
-                           samples; ``add_at_samples`` plants a pulse at
-                           caller-given samples per channel.
+                           samples (``filterbank_u8``: 8-bit, N(128, 16^2)
+                           rounded and clipped); ``add_at_samples`` plants a
+                           pulse at caller-given samples per channel.
 * ``batch_series``      -- series i of a batch: seed base+i, one sinusoid of
                            amplitude 0.05*sqrt(2^17/N) (keeps the expected
                            matched-filter power near 82 at any N), r0, z0 drawn
@@ -43,6 +44,7 @@ __all__ = [
     "batch_series",
     "draw_signal_params",
     "filterbank_noise",
+    "filterbank_u8",
     "add_at_samples",
 ]
 
@@ -159,11 +161,22 @@ def filterbank_noise(n_chan: int, n_t: int, seed: int) -> np.ndarray:
     return _rng(seed).standard_normal((n_chan, n_t), dtype=np.float64).astype(np.float32)
 
 
+def filterbank_u8(n_chan: int, n_t: int, seed: int, mean: float = 128.0,
+                  std: float = 16.0) -> np.ndarray:
+    """8-bit filterbank [n_chan][n_t]: rounded N(mean, std^2) from PCG64(seed),
+    clipped to [0, 255]."""
+    x = _rng(seed).standard_normal((n_chan, n_t), dtype=np.float64) * std + mean
+    return np.clip(np.rint(x), 0, 255).astype(np.uint8)
+
+
 def add_at_samples(fb: np.ndarray, samples, amp: float) -> np.ndarray:
     """Add `amp` to fb[c, samples[c]] for every channel c (indices given by the
     caller; samples outside [0, n_t) are skipped).  Returns a new array."""
-    out = np.array(fb, dtype=np.float32, copy=True)
+    out = np.array(fb, copy=True)
     for c, t in enumerate(samples):
         if 0 <= int(t) < out.shape[1]:
-            out[c, int(t)] += np.float32(amp)
+            if out.dtype == np.uint8:
+                out[c, int(t)] = min(255, int(out[c, int(t)]) + int(amp))
+            else:
+                out[c, int(t)] += out.dtype.type(amp)
     return out

@@ -5,6 +5,7 @@
 * dedispersed series: FP32 sums of n_chan terms in channel order against the
   FP64 sum: |out - ref| <= (n_chan - 1) 2^-24 sum_c |in| (the recursive-
   summation bound), checked per sample with the oracle's sum of |in|.
+* 8-bit filterbanks: integer sums, so the series equal the oracle's exactly.
 """
 import numpy as np
 import pytest
@@ -108,3 +109,35 @@ def test_dedispersed_rows_feed_the_search(capi):
     assert any(int(r) == 3000 for r in cands["ir"][cands["trial_id"] == 0])
     plan.close()
     dd.close()
+
+
+@pytest.mark.parametrize("n_chan,n_t,n_out,f_top,df,tsamp,dm_lo,dm_step,n_dm", [
+    (64, 20000, 17000, 1500.0, 4.0, 64e-6, 0.0, 2.0, 37),     # ragged DM tile and time tile
+    (96, 8192, 8192, 1400.0, 2.0, 64e-6, 0.0, 5.0, 16),       # n_out = n_t: zeros past the end
+    (40, 60000, 4096, 400.0, 1.0, 64e-6, 0.0, 10.0, 20),      # wide delay spread (1 channel/batch)
+    (1024, 1 << 15, 1 << 14, 1670.0, 0.25, 64e-6, 0.0, 0.25, 70),
+])
+def test_dedisperse_u8_is_exact(capi, n_chan, n_t, n_out, f_top, df, tsamp, dm_lo, dm_step, n_dm):
+    delays = O.dm_delays(n_chan, f_top, df, tsamp, dm_lo, dm_step, n_dm)
+    fb = S.filterbank_u8(n_chan, n_t, 29)
+    plan = capi.DedispPlan(n_chan, n_t, f_top, df, tsamp, dm_lo, dm_step, n_dm, n_out)
+    got = plan.dedisperse(torch.from_numpy(fb).cuda()).cpu().numpy().astype(np.float64)
+    ref = O.dedisperse(fb.astype(np.float64), delays, n_out)
+    assert np.array_equal(got, ref), np.abs(got - ref).max()
+    plan.close()
+
+
+def test_dedisperse_u8_pulse_and_validation(capi):
+    n_chan, k, t0 = 128, 11, 555
+    delays = O.dm_delays(n_chan, 1450.0, 2.0, 64e-6, 0.0, 4.0, 32)
+    fb = S.add_at_samples(S.filterbank_u8(n_chan, 1 << 14, 3), t0 + delays[k], 100)
+    plan = capi.DedispPlan(n_chan, 1 << 14, 1450.0, 2.0, 64e-6, 0.0, 4.0, 32, 1 << 13)
+    out = plan.dedisperse(torch.from_numpy(fb).cuda()).cpu().numpy()
+    assert np.unravel_index(np.argmax(out), out.shape) == (k, t0)
+    plan.close()
+    # 8-bit rows must be 16-byte aligned: n_t a multiple of 16
+    odd = capi.DedispPlan(4, 1000, 1400.0, 1.0, 64e-6, 0.0, 1.0, 2, 500)
+    with pytest.raises(capi.FdasError) as ei:
+        odd.dedisperse(torch.zeros((4, 1000), dtype=torch.uint8, device="cuda"))
+    assert ei.value.status == capi.FDAS_ERR_ARG
+    odd.close()

@@ -153,19 +153,23 @@ def test_interbinned_search_matches_oracle(capi, prec, H):
     plan.close()
 
 
-def test_interbinned_uneven_batch(capi):
+@pytest.mark.parametrize("prec", [0, 1])
+def test_interbinned_uneven_batch(capi, prec):
     """Full-length and decimated series in one call, each on its own
-    half-bin plane."""
+    half-bin plane (FP32: FFT correlator + interbinning kernel; BF16: the
+    tensor-core epilogue and its edge table at two plane widths)."""
     n = 1 << 14
     xs = [S.pulsar_series(n, seed=41, height=1.0, z_abs=6.0)[0],
-          S.pulsar_series(n // 2, seed=42, height=1.0, z_abs=6.0)[0]]
-    plan = capi.Plan(n, 64e-6, 8.0, 2.0, 1024, 4, interbin=True)
-    st, cands, nf = plan.search([torch.from_numpy(x).cuda() for x in xs], trial_ids=[7, 9],
+          S.pulsar_series(n // 2, seed=42, height=1.0, z_abs=6.0)[0],
+          S.pulsar_series(n // 4, seed=43, height=1.0, z_abs=6.0)[0]]
+    guard = 1e-4 if prec == 0 else 0.03
+    plan = capi.Plan(n, 64e-6, 8.0, 2.0, 1024, 4, interbin=True, precision=prec)
+    st, cands, nf = plan.search([torch.from_numpy(x).cuda() for x in xs], trial_ids=[7, 9, 11],
                                 capacity=1 << 18)
     assert st == capi.FDAS_OK and nf == len(cands)
-    for tid, x in zip((7, 9), xs):
-        ref = O.search(x, 8.0, 2.0, 4, guard=1e-4, interbin=True)
+    for tid, x in zip((7, 9, 11), xs):
+        ref = O.search(x, 8.0, 2.0, 4, guard=guard, interbin=True)
         mine = cands[cands["trial_id"] == tid]
         assert len(ref["candidates"]) > 0
-        _compare(mine, ref["candidates"], ref["guard"], 1e-4)
+        _compare(mine, ref["candidates"], ref["guard"], guard)
     plan.close()
