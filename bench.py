@@ -284,8 +284,8 @@ def run_gpu(args, rank, world, local_rank, dist):
     # this rank's block of the job's DM trials, numbered globally
     t_start, t_stop = shard.trial_block(args.batch * world, rank, world)
     ids = list(range(t_start, t_stop))
-    xs, _ = S.torch_batch_series(t_stop - t_start, N_SAMPLES, base_seed=1000 + t_start,
-                                 device=dev)
+    xs, sig_params = S.torch_batch_series(t_stop - t_start, N_SAMPLES, base_seed=1000 + t_start,
+                                          device=dev)
     torch.cuda.synchronize()
     peak_hbm, peak_src = _peaks()
 
@@ -414,6 +414,11 @@ def run_gpu(args, rank, world, local_rank, dist):
                       "(pi/4)^2 |F(r) - F(r+1)|^2 written by the tensor-core epilogue; 2x the "
                       "plane cells)"}
 
+    # --- refinement (Fourier-interpolated power, gradient ascent), FP32 ------
+    ref_leg = None
+    if not args.no_refine:
+        ref_leg = run_refine(args, dev, capi, xs[0], sig_params[0])
+
     # --- dedispersion upstream of the search: filterbank -> DM-trial series --
     dd = None
     if not args.no_dedisp:
@@ -515,6 +520,8 @@ def run_gpu(args, rank, world, local_rank, dist):
         line["interbin"] = ib
     if dd is not None:
         line["dedispersion"] = dd
+    if ref_leg is not None:
+        line["refine"] = ref_leg
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
@@ -527,6 +534,60 @@ DD_CHAN, DD_FTOP, DD_DF, DD_NDM, DD_DMSTEP = 1024, 1670.0, 0.25, 128, 0.25
 # shared memory delivers one 4-byte word per lane per clock per SM: 32 words
 # x 152 SMs x 2.07 GHz, the bound of a sum that reads every term from it
 SMEM_WORDS_PEAK_T = 32 * 152 * 2.07e9 / 1e12
+
+
+def run_refine(args, dev, capi, x, params):
+    """fdas_fourier_power (P and its gradient at arbitrary (r, z)) and
+    fdas_refine (50 ascent steps per seed) on one series' FP32 spectrum."""
+    import numpy as np
+    import torch
+    plan = capi.Plan(N_SAMPLES, TSAMP, Z_MAX, Z_STEP, SEG_LEN, N_HARM, precision=capi.FDAS_FP32)
+    spec = plan.spectrum(x)
+    X = torch.view_as_complex(spec.view(-1, 2))
+    n_r = N_SAMPLES // 2
+    rng = np.random.default_rng(3)
+    n_pts = 8192
+    rz = np.stack([rng.uniform(0.01 * n_r, 0.95 * n_r, n_pts), rng.uniform(-90.0, 90.0, n_pts)], 1)
+    rz_d = torch.from_numpy(rz).to(dev)
+    # work: Y(u) = sum_e X_e exp(2 pi i e u) at 512 nodes over 2m + 1 bins,
+    # m = 32 + ceil(|z|/2): 8 flops per complex multiply-add
+    m = 32 + np.ceil(np.abs(rz[:, 1]) / 2.0 - 1e-12)
+    flops = float(np.sum(8.0 * 512 * (2 * m + 1)))
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        plan.fourier_power(X, rz_d)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.fourier_power(X, rz_d)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    # refinement: 1024 seeds scattered around the injected signal
+    r0, z0 = params
+    seeds = np.zeros(1024, dtype=capi.SEED_DTYPE)
+    seeds["r"] = r0 + rng.uniform(-0.5, 0.5, 1024)
+    seeds["z"] = z0 + rng.uniform(-2.0, 2.0, 1024)
+    plan.refine(X, seeds[:64], n_steps=50)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = plan.refine(X, seeds, n_steps=50)
+    ms_ref = (time.perf_counter() - t0) * 1e3
+    plan.close()
+    ach = flops / (ms / 1000.0) / 1e12
+    return {"fourier_power": {"points_per_s": n_pts / (ms / 1000.0), "ms_per_launch": ms,
+                              "points": n_pts,
+                              "roofline": {"bound": "alu", "achieved": ach,
+                                           "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                           "frac": ach / FP32_ALU_PEAK_TFLOPS}},
+            "refine": {"seeds_per_s": 1024 / (ms_ref / 1000.0), "ms": ms_ref, "seeds": 1024,
+                       "n_steps": 50,
+                       "median_accepted_steps": float(np.median(out["steps"])),
+                       "converged_within_0.1_bin": float(np.mean(np.abs(out["r"] - r0) < 0.1))},
+            "note": "FP32 spectrum of series 0; P and dP/dr, dP/dz at uniform random (r, z); "
+                    "refine times the blocking call (host copies included)"}
 
 
 def run_dedisp(args, dev, capi, world):
@@ -565,7 +626,8 @@ def run_dedisp(args, dev, capi, world):
            "note": "dedisperse_kernel, inputs larger than L2 (filterbank 34 GB); one 4-byte "
                    "shared-memory word per addition is the bound (less where two DM trials "
                    "share a delay)"}
-    # the same trials from an 8-bit filterbank (the usual format; exact sums)
+    # the same trials from an 8-bit filterbank (the usual format; exact sums),
+    # then the whole chain: 8-bit filterbank -> DM-trial series -> BF16 search
     del fb
     n_t16 = (n_t + 15) // 16 * 16
     plan.close()
@@ -583,6 +645,29 @@ def run_dedisp(args, dev, capi, world):
     res["u8"] = {"value": DD_NDM * world / (ms8 / 1000.0), "unit": "DM-trials/s",
                  "ms_per_launch": ms8,
                  "frac_of_smem_bound": adds / (ms8 / 1000.0) / 1e12 / SMEM_WORDS_PEAK_T}
+    splan = capi.Plan(N_SAMPLES, TSAMP, Z_MAX, Z_STEP, SEG_LEN, N_HARM, precision=capi.FDAS_BF16)
+    rows = [out[d] for d in range(DD_NDM)]
+
+    def chain():
+        plan.dedisperse(fb8, out)
+        return splan.search(rows, capacity=1 << 18)
+
+    for _ in range(max(1, args.warmup // 2)):
+        chain()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    n_cand = 0
+    for _ in range(args.steps):
+        n_cand += chain()[2]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    msc = e0.elapsed_time(e1) / args.steps
+    splan.close()
+    res["pipeline_u8_to_candidates"] = {
+        "value": DD_NDM * world / (msc / 1000.0), "unit": "DM-trials/s", "ms_per_step": msc,
+        "candidates_per_trial": n_cand / (args.steps * DD_NDM),
+        "note": "8-bit filterbank (1024 channels) -> 128 DM-trial series -> BF16 FDAS search of "
+                "all of them, per step"}
     plan.close()
     del fb8, out
     torch.cuda.empty_cache()
@@ -644,6 +729,8 @@ def main():
                     help="skip the fundamental-indexed harmonic-sum leg")
     ap.add_argument("--no-interbin", action="store_true",
                     help="skip the interbinning (half-bin plane) leg")
+    ap.add_argument("--no-refine", action="store_true",
+                    help="skip the refinement leg")
     ap.add_argument("--no-dedisp", action="store_true",
                     help="skip the dedispersion leg")
     ap.add_argument("--uneven-batch", type=int, default=64)

@@ -98,31 +98,51 @@ __device__ void load_window(const float2 *__restrict__ X, int64_t n_r, const Win
     __syncthreads();
 }
 
-// F, dF/dr, dF/dz at (delta, z) for the window in sx
+// F, dF/dr, dF/dz at (delta, z) for the window in sx.  Each thread takes the
+// kRefNodes / kRefThreads nodes u_i, i = tid + kRefThreads q, together: their
+// phase recurrences are independent, so each window value read from shared
+// memory feeds all of them and the chains overlap.
+constexpr int kRefPer = kRefNodes / kRefThreads;
+static_assert(kRefNodes % kRefThreads == 0, "nodes per thread");
+
 __device__ void eval_F(const float2 *sx, const Window &w, float z, const float2 *__restrict__ nodes,
                        float2 *red, float2 &F, float2 &Fr, float2 &Fz) {
-    float2 aF = make_float2(0.f, 0.f), aR = aF, aZ = aF;
-    for (int i = threadIdx.x; i < kRefNodes; i += kRefThreads) {
-        const float u = nodes[i].x, wt = nodes[i].y;
-        // conj(A(u)) = exp(-2 pi i [(delta - z/2) u + z u^2 / 2])
-        const float theta = fmaf(0.5f * z * u, u, (w.delta - 0.5f * z) * u);
-        const float2 ca = cispi(-2.0f * theta);
-        // Y(u) = sum_e x_e exp(2 pi i e u), e = -m..m; exact phase every 32 terms
-        float2 Y = make_float2(0.f, 0.f);
-        const float2 step = cispi(2.0f * u);
-        for (int e0 = -w.m; e0 <= w.m; e0 += 32) {
-            float2 ph = cispi(2.0f * (float)e0 * u);
-            const int e1 = min(e0 + 32, w.m + 1);
-            for (int e = e0; e < e1; ++e) {
-                Y = c_add(Y, c_mul(sx[e + w.m], ph));
-                ph = c_mul(ph, step);
+    float u[kRefPer], Y[kRefPer][2];
+    float2 step[kRefPer], ph[kRefPer];
+#pragma unroll
+    for (int q = 0; q < kRefPer; ++q) {
+        u[q] = nodes[threadIdx.x + kRefThreads * q].x;
+        step[q] = cispi(2.0f * u[q]);
+        Y[q][0] = Y[q][1] = 0.f;
+    }
+    // Y(u) = sum_e x_e exp(2 pi i e u), e = -m..m; exact phase every 32 terms
+    for (int e0 = -w.m; e0 <= w.m; e0 += 32) {
+#pragma unroll
+        for (int q = 0; q < kRefPer; ++q) ph[q] = cispi(2.0f * (float)e0 * u[q]);
+        const int e1 = min(e0 + 32, w.m + 1);
+        for (int e = e0; e < e1; ++e) {
+            const float2 x = sx[e + w.m];
+#pragma unroll
+            for (int q = 0; q < kRefPer; ++q) {
+                const float2 t = c_mul(x, ph[q]);
+                Y[q][0] += t.x;
+                Y[q][1] += t.y;
+                ph[q] = c_mul(ph[q], step[q]);
             }
         }
-        const float2 G = c_mul(ca, Y);
+    }
+    float2 aF = make_float2(0.f, 0.f), aR = aF, aZ = aF;
+#pragma unroll
+    for (int q = 0; q < kRefPer; ++q) {
+        const float wt = nodes[threadIdx.x + kRefThreads * q].y;
+        // conj(A(u)) = exp(-2 pi i [(delta - z/2) u + z u^2 / 2])
+        const float theta = fmaf(0.5f * z * u[q], u[q], (w.delta - 0.5f * z) * u[q]);
+        const float2 ca = cispi(-2.0f * theta);
+        const float2 G = c_mul(ca, make_float2(Y[q][0], Y[q][1]));
         const float2 Gw = make_float2(G.x * wt, G.y * wt);
         aF = c_add(aF, Gw);
         // -2 pi i u G and -2 pi i (u^2 - u)/2 G
-        const float su = kTwoPi * u, sz = kTwoPi * 0.5f * (u * u - u);
+        const float su = kTwoPi * u[q], sz = kTwoPi * 0.5f * (u[q] * u[q] - u[q]);
         aR = c_add(aR, make_float2(su * Gw.y, -su * Gw.x));
         aZ = c_add(aZ, make_float2(sz * Gw.y, -sz * Gw.x));
     }
