@@ -243,7 +243,11 @@ __global__ void __launch_bounds__(kHsThreads)
 // o_j changes with probability j/H, so the walk copies about 30% fewer bytes
 // than copying every span for every row.  The copies of each stage complete
 // on that stage's own mbarrier (bounded waits; one phase per row), so the
-// first stages are summed while later spans are still arriving.  Each
+// first stages are summed while later spans are still arriving.  With 16-bit
+// planes the top row itself (j = H, changed every row) is not staged: each
+// thread loads its 16 cells of it from global memory into registers one row
+// ahead, which leaves a smaller shared-memory footprint (7 CTAs per SM
+// instead of 6).  Each
 // thread reads its values with the widest aligned shared-memory loads, adds
 // them to its cells (16-bit planes: one mixed-precision add each), compares
 // each completed stage with its threshold and appends every crossing.
@@ -259,7 +263,10 @@ struct Dedup {
     static constexpr int len(int j) { return (R / H) * j * (T - 1) + dmax(j) + 1; }
     static constexpr int padlen(int j) { return (len(j) + EPV - 1) / EPV * EPV; }
     static constexpr int off(int j) { return j <= 1 ? 0 : off(j - 1) + padlen(j - 1); }
-    static constexpr int SMEM_ELEMS = off(H + 1);
+    // 16-bit planes read the top row (j = H) from global memory into
+    // registers, one row ahead; FP32 planes stage it like the others
+    static constexpr bool kTopRegs = sizeof(real) == 2;
+    static constexpr int SMEM_ELEMS = kTopRegs ? off(H) : off(H + 1);
     // consecutive top rows one CTA walks: from a top row to the next, the
     // source row o_j of harmonic j changes with probability j/H, and only the
     // spans that change are copied again
@@ -375,9 +382,10 @@ struct DedupSteps {
         if constexpr (IDX < H) {
             constexpr int J = j_at(H, IDX);
             constexpr int G = group_of(IDX);
-            if constexpr (IDX == 0 || (IDX & (IDX - 1)) == 0)
+            constexpr bool kSkip = IDX == 0 && D::kTopRegs;
+            if constexpr (!kSkip && (IDX == 0 || (IDX & (IDX - 1)) == 0))
                 mbar_arrive_expect_tx(&bars[G], changed_bytes<0, G>(n_r, B, inside, chg));
-            if ((chg >> (J - 1)) & 1u) {
+            if (!kSkip && ((chg >> (J - 1)) & 1u)) {
                 const unsigned bytes = inside ? full_bytes(J) : span_bytes<J>(n_r, B);
                 const int64_t row = iz0 + src_off(H, o, J);
                 if (bytes)
@@ -388,12 +396,32 @@ struct DedupSteps {
         }
     }
 
+    // 16 consecutive 16-bit cells (32 bytes, aligned) into 8 words
+    __device__ __forceinline__ static void load_top(const real *p, uint32_t (&tv)[8]) {
+        const uint4 a = __ldg(reinterpret_cast<const uint4 *>(p));
+        const uint4 b = __ldg(reinterpret_cast<const uint4 *>(p) + 1);
+        tv[0] = a.x; tv[1] = a.y; tv[2] = a.z; tv[3] = a.w;
+        tv[4] = b.x; tv[5] = b.y; tv[6] = b.z; tv[7] = b.w;
+    }
+
     // add harmonic j_at(H, IDX) to the thread's cells; stage(s, S) at the end
     // of every stage.  False if a stage's copies did not land in time.
     template <int IDX, class F>
     __device__ __forceinline__ static bool sums(const real *sm, uint64_t *bars, unsigned parity,
-                                                int t, float2 (&S2)[D::R / 2], F &&stage) {
-        if constexpr (IDX < H) {
+                                                int t, float2 (&S2)[D::R / 2], F &&stage,
+                                                uint32_t (&tv)[8], const real *next_top) {
+        if constexpr (IDX == 0 && D::kTopRegs) {
+            // j = H: the thread's own 16 cells of the top row, loaded one row
+            // earlier; then the load of the next row's is issued
+#pragma unroll
+            for (int i = 0; i < D::R; ++i) {
+                float &s = (i & 1) ? S2[i / 2].y : S2[i / 2].x;
+                s = (i & 1) ? P::acc_hi(s, tv[i / 2]) : P::acc_lo(s, tv[i / 2]);
+            }
+            if (next_top) load_top(next_top, tv);
+            stage(0, S2);
+            return sums<IDX + 1>(sm, bars, parity, t, S2, stage, tv, next_top);
+        } else if constexpr (IDX < H) {
             constexpr int J = j_at(H, IDX);
             if constexpr (IDX == 0 || (IDX & (IDX - 1)) == 0)
                 if (!mbar_wait(&bars[group_of(IDX)], parity)) return false;
@@ -441,7 +469,7 @@ struct DedupSteps {
                 }
             }
             if constexpr (((IDX + 1) & IDX) == 0) stage(ilog2h(IDX + 1), S2);
-            return sums<IDX + 1>(sm, bars, parity, t, S2, stage);
+            return sums<IDX + 1>(sm, bars, parity, t, S2, stage, tv, next_top);
         } else {
             return true;
         }
@@ -475,6 +503,9 @@ __global__ void __launch_bounds__(Dedup<P, H>::T, 6)
     const float inv = 1.0f / P::plane_scale;
     bool failed = false;
     int q = 0;
+    uint32_t tv[8];   // 16-bit planes: the thread's top-row cells, one row ahead
+    if constexpr (D::kTopRegs)
+        if (active && iz_begin < iz_end) Steps::load_top(plane + (int64_t)iz_begin * n_r + b, tv);
     for (int iz = iz_begin; iz < iz_end; ++iz, ++q) {
         // every thread is done with the previous row's spans (and, for the
         // first row, the barriers are initialised); stop together after a
@@ -494,6 +525,7 @@ __global__ void __launch_bounds__(Dedup<P, H>::T, 6)
         float2 S2[D::R / 2];
 #pragma unroll
         for (int c = 0; c < D::R / 2; ++c) S2[c] = make_float2(0.f, 0.f);
+        const real *next_top = iz + 1 < iz_end ? plane + (int64_t)(iz + 1) * n_r + b : nullptr;
         const bool ok = Steps::template sums<0>(sm, bars, (unsigned)(q & 1), t, S2,
                                                 [&](int s, float2 (&Sv)[D::R / 2]) {
             if constexpr (kWriteSums) {
@@ -532,7 +564,7 @@ __global__ void __launch_bounds__(Dedup<P, H>::T, 6)
                     }
                 }
             }
-        });
+        }, tv, next_top);
         if (!ok) failed = true;
     }
     if (__syncthreads_or(failed)) {
