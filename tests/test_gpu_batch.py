@@ -113,6 +113,29 @@ def test_graph_replay_equals_direct_launches(capi, uneven, prec):
     graph.close()
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_graph_replay_with_interbinning(capi, uneven, prec):
+    """The interbinned search (FP32: complex plane + interbinning kernel;
+    BF16: the tensor-core epilogue and its fix-up kernel) captured into a
+    CUDA graph gives the direct launches' candidates, decimated series
+    included."""
+    lengths, xs, ids, refs = uneven
+    direct = capi.Plan(NMAX, 64e-6, ZMAX, ZSTEP, L, H, precision=prec, interbin=True)
+    graph = capi.Plan(NMAX, 64e-6, ZMAX, ZSTEP, L, H, use_graph=True, precision=prec,
+                      interbin=True)
+    side = torch.cuda.Stream()
+    dev = [torch.from_numpy(x).cuda() for x in xs]
+    for rnd in range(2):
+        torch.cuda.synchronize()
+        with torch.cuda.stream(side):
+            st_g, cg, nf_g = graph.search(dev, trial_ids=ids, stream=side)
+        st_d, cd, nf_d = direct.search(dev, trial_ids=ids)
+        assert st_g == st_d == capi.FDAS_OK and nf_d > 0
+        assert nf_g == nf_d and cg.tolist() == cd.tolist(), rnd
+    direct.close()
+    graph.close()
+
+
 def test_uneven_batch_fundamental_harmonic(capi, uneven):
     """The fundamental-indexed harmonic sum on decimated series (each series
     its own N_r and domain), BF16 storage, against the oracle."""
