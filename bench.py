@@ -377,6 +377,12 @@ def run_gpu(args, rank, world, local_rank, dist):
         ms_fp32, _, j_fp32, _, _ = timed(plan32, xs, args.steps, args.warmup, False, energy)
         _, prof_fp32, _, _, _ = timed(plan32, xs, 1, 1, True)
         plan32.close()
+        # FP32 storage with the split (BF16 hi + lo) tensor-core correlation
+        plan3 = capi.Plan(N_SAMPLES, TSAMP, Z_MAX, Z_STEP, SEG_LEN, N_HARM,
+                          precision=capi.FDAS_FP32, correlator=capi.FDAS_CORR_TENSOR_SPLIT)
+        ms_fp32s, _, _, _, nf_fp32s = timed(plan3, xs, args.steps, args.warmup, False)
+        _, prof_fp32s, _, _, _ = timed(plan3, xs, 1, 1, True)
+        plan3.close()
 
     # --- fundamental-indexed harmonic sum (FDAS_HARM_FUNDAMENTAL), BF16 ----
     fund = None
@@ -512,6 +518,13 @@ def run_gpu(args, rank, world, local_rank, dist):
                         "hbm_alg_frac": wm32["alg_bytes"] * args.batch * args.steps
                         / (ms_fp32 / 1000.0) / 1e9 / peak_hbm}
         line["bf16_speedup_vs_fp32"] = value / v32
+        line["fp32_tensor_split"] = {
+            "value": args.batch * args.steps * world / (ms_fp32s / 1000.0), "unit": UNIT,
+            "ms_per_step": ms_fp32s / args.steps,
+            "kernels_ms_per_trial": {g: prof_fp32s[g][2] / max(1, prof_fp32s["trials"])
+                                     for g in ("spectrum", "correlate", "harmonic")},
+            "note": "FP32 storage, correlation on the tensor cores with BF16 hi + lo operands "
+                    "(three products per term, FP32 accumulation; FDAS_CORR_TENSOR_SPLIT)"}
     if uneven is not None:
         line["uneven_batch"] = uneven
     if fund is not None:

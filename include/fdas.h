@@ -61,8 +61,14 @@ enum { FDAS_NORM_MEDIAN = 0, FDAS_NORM_NONE = 1 };
  * FDAS_CORR_TENSOR: the direct correlation sum_e g_z[e] X'_{r-e} as a GEMM
  *   on the tensor cores (16-bit operands, FP32 accumulation; FDAS_BF16 and
  *   FDAS_FP16 only, with m_overlap <= 112, i.e. z_max <= 208);
- * FDAS_CORR_AUTO: TENSOR where it applies, else FFT. */
-enum { FDAS_CORR_AUTO = 0, FDAS_CORR_FFT = 1, FDAS_CORR_TENSOR = 2 };
+ * FDAS_CORR_TENSOR_SPLIT: FP32 storage on the tensor cores: spectrum and
+ *   taps each as the sum of two BF16 parts (hi = bf16(x), lo = bf16(x - hi)),
+ *   three products per term (hi*hi + hi*lo + lo*hi; the dropped lo*lo term
+ *   is about 2^-16 of each product), FP32 accumulation and FP32 plane; P
+ *   within about 1e-4 of the FP32 result (FDAS_FP32 only, m_overlap <= 56,
+ *   i.e. z_max <= 96 at the default bank);
+ * FDAS_CORR_AUTO: TENSOR where it applies, else FFT (never the split mode). */
+enum { FDAS_CORR_AUTO = 0, FDAS_CORR_FFT = 1, FDAS_CORR_TENSOR = 2, FDAS_CORR_TENSOR_SPLIT = 3 };
 /* harmonic sum:
  * FDAS_HARM_TOP (default): top-harmonic indexed, every plane cell (ir, iz) is
  *   the top harmonic; harmonic j of H reads the rounded sub-multiple
@@ -140,7 +146,7 @@ typedef struct {
     int32_t z_chunks;         /* template chunks per segment in the correlation */
     int32_t use_graph;
     double tuned_ms;          /* autotune: correlation time per series (ms), else 0 */
-    int32_t correlator;       /* FDAS_CORR_FFT or FDAS_CORR_TENSOR, as built    */
+    int32_t correlator;       /* FDAS_CORR_FFT, _TENSOR or _TENSOR_SPLIT, as built */
     int32_t harmonic_mode;    /* FDAS_HARM_TOP or FDAS_HARM_FUNDAMENTAL         */
     int32_t interbin;         /* 1: half-bin plane                             */
     int32_t reserved0;

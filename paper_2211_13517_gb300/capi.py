@@ -35,7 +35,7 @@ STATUS_NAMES = {0: "FDAS_OK", 1: "FDAS_ERR_ARG", 2: "FDAS_ERR_CUDA", 3: "FDAS_ER
 FDAS_FP32, FDAS_BF16, FDAS_FP16 = 0, 1, 2
 FDAS_THRESH_GAMMA_TAIL, FDAS_THRESH_MEAN_PLUS_KSIGMA = 0, 1
 FDAS_NORM_MEDIAN, FDAS_NORM_NONE = 0, 1
-FDAS_CORR_AUTO, FDAS_CORR_FFT, FDAS_CORR_TENSOR = 0, 1, 2
+FDAS_CORR_AUTO, FDAS_CORR_FFT, FDAS_CORR_TENSOR, FDAS_CORR_TENSOR_SPLIT = 0, 1, 2, 3
 FDAS_HARM_TOP, FDAS_HARM_FUNDAMENTAL = 0, 1
 
 EXPORTED = ["fdas_opts_default", "fdas_plan_create", "fdas_plan_destroy",

@@ -114,29 +114,39 @@ __device__ __forceinline__ float2 fsub2(float2 a, float2 b) {
 enum { kPower = 0, kCplx = 1, kInterbin = 2 };
 constexpr float kIbFactor = 0.61685027506808491f;   // (pi/4)^2
 
+// P = PrecF32 is the split mode of FP32 plans: spectrum and taps are each
+// the sum of two BF16 parts (hi + lo), every K step issues the three MMAs
+// hi*hi + hi*lo + lo*hi into the same FP32 accumulator (the lo*lo term,
+// about 2^-16 of the product, is dropped), the template image is twice as
+// large (its lo half `b_lo` bytes after the hi one), two spectrum windows per
+// stage, two stages, and the plane is stored in FP32.
 template <class P, int kMode>
 __global__ void __launch_bounds__(kTcThreads, 1)
-    correlate_tc_kernel(const typename P::cpx *__restrict__ spec_pad,
-                        const unsigned char *__restrict__ bank_img,
+    correlate_tc_kernel(const unsigned char *__restrict__ spec_a,
+                        const unsigned char *__restrict__ spec_lo,
+                        const unsigned char *__restrict__ bank_img, int64_t b_lo,
                         const TcChunk *__restrict__ chunks, int n_ch,
                         const float *__restrict__ inv_energy,
                         void *__restrict__ out, double2 *__restrict__ partials,
                         int64_t n_r, int win_bytes, int b_bytes_max, unsigned int *flags,
                         float4 *__restrict__ edges) {
+    constexpr bool kSplit = P::id == FDAS_FP32;
+    constexpr int kStages = kSplit ? 2 : kTcStages;
+    constexpr int kParts = kSplit ? 2 : 1;   // hi (+ lo) operand images
     extern __shared__ __align__(128) unsigned char tc_smem[];
     unsigned char *const sB = tc_smem;
-    unsigned char *const sA = tc_smem + b_bytes_max;
+    unsigned char *const sA = tc_smem + kParts * b_bytes_max;
     __shared__ __align__(8) uint64_t a_full[kTcStages], a_empty[kTcStages];
     __shared__ __align__(8) uint64_t b_full, b_empty, acc_full[2], acc_empty[2], drain;
     __shared__ uint32_t tmem_base_sh;
     __shared__ double red[2][kTcEpiWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t n_tiles = n_r / kTcTile;
-    constexpr bool kBF16 = P::id == FDAS_BF16;
+    constexpr bool kBF16 = P::id == FDAS_BF16 || kSplit;
     constexpr uint32_t kIdesc = idesc_f16<kBF16>(kTcRows, kTcN);
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < kTcStages; ++i) {
+        for (int i = 0; i < kStages; ++i) {
             mbar_init(&a_full[i], 1);
             mbar_init(&a_empty[i], 1);
         }
@@ -175,23 +185,30 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         break;
                     }
                     const unsigned bytes = (unsigned)chunks[c].ks * kTcSlab;
-                    mbar_arrive_expect_tx(&b_full, bytes);
+                    mbar_arrive_expect_tx(&b_full, kParts * bytes);
                     bulk_copy_g2s(sB, bank_img + chunks[c].b_off, bytes, &b_full);
+                    if constexpr (kSplit)
+                        bulk_copy_g2s(sB + b_bytes_max, bank_img + b_lo + chunks[c].b_off, bytes,
+                                      &b_full);
                     cur = c;
                 }
-                const int s = j % kTcStages;
-                if (j >= kTcStages && !mbar_wait(&a_empty[s], ((j / kTcStages) - 1) & 1)) {
+                const int s = j % kStages;
+                if (j >= kStages && !mbar_wait(&a_empty[s], ((j / kStages) - 1) & 1)) {
                     ok = false;
                     break;
                 }
-                mbar_arrive_expect_tx(&a_full[s], (unsigned)win_bytes);
-                bulk_copy_g2s(sA + s * win_bytes, spec_pad + t * kTcTile, (unsigned)win_bytes,
-                              &a_full[s]);
+                // a window of 16-bit (re, im) pairs: 4 bytes per complex value
+                const int64_t a_off = t * kTcTile * 4;
+                unsigned char *const dstA = sA + s * kParts * win_bytes;
+                mbar_arrive_expect_tx(&a_full[s], (unsigned)(kParts * win_bytes));
+                bulk_copy_g2s(dstA, spec_a + a_off, (unsigned)win_bytes, &a_full[s]);
+                if constexpr (kSplit)
+                    bulk_copy_g2s(dstA + win_bytes, spec_lo + a_off, (unsigned)win_bytes, &a_full[s]);
                 ++j;
             }
             // every copy issued lands before the CTA can exit (bounded)
-            for (int s = 0; s < kTcStages && s < j; ++s) {
-                const int uses = (j - 1 - s) / kTcStages + 1;
+            for (int s = 0; s < kStages && s < j; ++s) {
+                const int uses = (j - 1 - s) / kStages + 1;
                 (void)mbar_wait(&a_full[s], (uses - 1) & 1);
             }
             if (run >= 0) (void)mbar_wait(&b_full, run & 1);
@@ -204,6 +221,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             int64_t t;
             int j = 0;
             const uint64_t bdesc0 = smem_desc(smem_u32(sB), 128, 256);
+            const uint64_t bdesc_lo = smem_desc(smem_u32(sB + (kSplit ? b_bytes_max : 0)), 128, 256);
             while (sch.next(c, t)) {
                 if (c != cur) {
                     if (cur >= 0) tc_commit(&b_empty);   // the old template image is free
@@ -216,9 +234,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     ks = chunks[c].ks;
                     kofs = chunks[c].kofs;
                 }
-                const int s = j % kTcStages, b = j & 1;
-                if (!mbar_test(&a_full[s], (j / kTcStages) & 1) &&
-                    !mbar_wait(&a_full[s], (j / kTcStages) & 1)) {
+                const int s = j % kStages, b = j & 1;
+                if (!mbar_test(&a_full[s], (j / kStages) & 1) &&
+                    !mbar_wait(&a_full[s], (j / kStages) & 1)) {
                     ok = false;
                     break;
                 }
@@ -229,10 +247,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 }
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(b * kTcAccStride);
-                const uint64_t adesc = smem_desc(smem_u32(sA + s * win_bytes) + 4u * kofs, 16, 128);
-                for (int k = 0; k < ks; ++k)
-                    tc_mma_f16(d, adesc + 2ull * k, bdesc0 + (uint64_t)(kTcSlab >> 4) * k, kIdesc,
-                               k > 0 ? 1u : 0u);
+                const uint32_t a_addr = smem_u32(sA + s * kParts * win_bytes) + 4u * kofs;
+                const uint64_t adesc = smem_desc(a_addr, 16, 128);
+                const uint64_t adesc_lo = smem_desc(a_addr + (kSplit ? (uint32_t)win_bytes : 0u), 16, 128);
+                for (int k = 0; k < ks; ++k) {
+                    const uint64_t kb = (uint64_t)(kTcSlab >> 4) * k;
+                    tc_mma_f16(d, adesc + 2ull * k, bdesc0 + kb, kIdesc, k > 0 ? 1u : 0u);
+                    if constexpr (kSplit) {
+                        tc_mma_f16(d, adesc + 2ull * k, bdesc_lo + kb, kIdesc, 1u);
+                        tc_mma_f16(d, adesc_lo + 2ull * k, bdesc0 + kb, kIdesc, 1u);
+                    }
+                }
                 tc_commit(&acc_full[b]);
                 tc_commit(&a_empty[s]);
                 ++j;
@@ -379,12 +404,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 s2 = __ffma2_rn(p01, p01, s2);
                 s2 = __ffma2_rn(p23, p23, s2);
                 if (k < zvalid) {
-                    const typename P::cpx lo = P::st(ps == 1.f ? p01 : __fmul2_rn(p01, make_float2(ps, ps)));
-                    const typename P::cpx hi = P::st(ps == 1.f ? p23 : __fmul2_rn(p23, make_float2(ps, ps)));
-                    uint2 w;
-                    memcpy(&w.x, &lo, 4);
-                    memcpy(&w.y, &hi, 4);
-                    *reinterpret_cast<uint2 *>(o + (int64_t)k * n_r) = w;
+                    if constexpr (kSplit) {
+                        *reinterpret_cast<float4 *>(o + (int64_t)k * n_r) =
+                            make_float4(p01.x, p01.y, p23.x, p23.y);
+                    } else {
+                        const typename P::cpx lo =
+                            P::st(ps == 1.f ? p01 : __fmul2_rn(p01, make_float2(ps, ps)));
+                        const typename P::cpx hi =
+                            P::st(ps == 1.f ? p23 : __fmul2_rn(p23, make_float2(ps, ps)));
+                        uint2 w;
+                        memcpy(&w.x, &lo, 4);
+                        memcpy(&w.y, &hi, 4);
+                        *reinterpret_cast<uint2 *>(o + (int64_t)k * n_r) = w;
+                    }
                 }
             }
             }
@@ -435,10 +467,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 // shared-memory image: per K step a slab of [n-block 28][K core 2][row 8][8
 // values]; column n = 8 zz + 4 c + p, K element kk of step k is complex tap
 // q = 8 k + kk / 2, component kk % 2 (re, im).
+// (split mode: P = PrecBF16 and `lo` set writes the lo part bf16(g - hi) of
+// the FP32 tap g, hi = bf16(g))
 template <class P>
 __global__ void tc_bank_kernel(uint16_t *__restrict__ img, const TcChunk *__restrict__ chunks,
                                const double *__restrict__ taps, const int64_t *__restrict__ off,
-                               const int32_t *__restrict__ m, int W0) {
+                               const int32_t *__restrict__ m, int W0, bool lo) {
     const TcChunk ch = chunks[blockIdx.y];
     const int64_t n_el = (int64_t)ch.ks * (kTcSlab / 2);
     uint16_t *out = img + ch.b_off / 2;
@@ -461,7 +495,9 @@ __global__ void tc_bank_kernel(uint16_t *__restrict__ img, const TcChunk *__rest
                 v = c == 0 ? (comp == 0 ? gr : -gi) : (comp == 0 ? gi : gr);
             }
         }
-        const typename P::real r = P::str((float)v);
+        const float vf = (float)v;
+        const typename P::real h = P::str(vf);
+        const typename P::real r = lo ? P::str(vf - P::ldr(h)) : h;
         uint16_t bits;
         memcpy(&bits, &r, 2);
         out[i] = bits;
@@ -470,17 +506,26 @@ __global__ void tc_bank_kernel(uint16_t *__restrict__ img, const TcChunk *__rest
 
 // 1 / E'_z, E'_z = sum_e |g'_z[e]|^2 of the taps as rounded to the plan's
 // 16-bit type (one block per template, FP64 sum in a fixed order)
+// (split mode: the taps as hi + lo)
+template <class P>
+__device__ __forceinline__ float tc_tap(double v, bool split) {
+    const float f = (float)v;
+    const float h = P::ldr(P::str(f));
+    return split ? h + P::ldr(P::str(f - h)) : h;
+}
+
 template <class P>
 __global__ void tc_energy_kernel(float *__restrict__ inv_energy, const double *__restrict__ taps,
-                                 const int64_t *__restrict__ off, const int32_t *__restrict__ m) {
+                                 const int64_t *__restrict__ off, const int32_t *__restrict__ m,
+                                 bool split) {
     __shared__ double sh[128];
     const int iz = blockIdx.x;
     const int n = 2 * m[iz] + 1;
     double a = 0.0;
     for (int e = threadIdx.x; e < n; e += 128) {
         const int64_t ti = off[iz] + e;
-        const float gr = P::ldr(P::str((float)taps[2 * ti]));
-        const float gi = P::ldr(P::str((float)taps[2 * ti + 1]));
+        const float gr = tc_tap<P>(taps[2 * ti], split);
+        const float gi = tc_tap<P>(taps[2 * ti + 1], split);
         a += (double)gr * gr + (double)gi * gi;
     }
     sh[threadIdx.x] = a;
@@ -549,20 +594,49 @@ int tc_ib_fixup_ctas(const Plan &p) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(4 * (int64_t)p.n_sms, (n + 255) / 256));
 }
 
-size_t tc_smem_bytes(int max_ks, int win) {
-    const size_t need = (size_t)max_ks * kTcSlab + (size_t)kTcStages * win * 4;
+// split mode: the spectrum window as two BF16 parts, hi = bf16(x) and
+// lo = bf16(x - hi), over the whole padded buffer
+__global__ void tc_split_kernel(const float2 *__restrict__ x, __nv_bfloat162 *__restrict__ hi,
+                                __nv_bfloat162 *__restrict__ lo, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 v = x[i];
+        const __nv_bfloat162 h = __float22bfloat162_rn(v);
+        const float2 hf = __bfloat1622float2(h);
+        hi[i] = h;
+        lo[i] = __float22bfloat162_rn(make_float2(v.x - hf.x, v.y - hf.y));
+    }
+}
+
+size_t tc_smem_bytes(int max_ks, int win, bool split) {
+    const size_t parts = split ? 2 : 1, stages = split ? 2 : kTcStages;
+    const size_t need = parts * ((size_t)max_ks * kTcSlab + stages * (size_t)win * 4);
     return std::max(need, kTcMinSmem);
 }
 
 template <class P, int kMode>
 fdas_status launch_tc_P(Plan &p, const void *spec_padded, void *plane, double2 *partials,
                         cudaStream_t s) {
-    const size_t smem = tc_smem_bytes(p.tc_max_ks, p.tc_win);
+    constexpr bool kSplit = P::id == FDAS_FP32;
+    const size_t smem = tc_smem_bytes(p.tc_max_ks, p.tc_win, kSplit);
     auto k = correlate_tc_kernel<P, kMode>;
     FDAS_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = correlate_tc_ctas(p);
-    k<<<grid, kTcThreads, smem, s>>>((const typename P::cpx *)spec_padded,
-                                      (const unsigned char *)p.tc_bank, p.tc_chunks, p.tc_n_ch,
+    const void *spec_a = spec_padded, *spec_lo = nullptr;
+    if constexpr (kSplit) {
+        // the FP32 padded spectrum -> its BF16 hi and lo parts
+        const int64_t n = p.tc_split_elems;
+        const int blocks = (int)std::min<int64_t>(8 * (int64_t)p.n_sms, (n + 255) / 256);
+        tc_split_kernel<<<blocks, 256, 0, s>>>((const float2 *)spec_padded,
+                                               (__nv_bfloat162 *)p.spec_hi,
+                                               (__nv_bfloat162 *)p.spec_lo, n);
+        FDAS_CUDA_TRY(cudaGetLastError());
+        spec_a = p.spec_hi;
+        spec_lo = p.spec_lo;
+    }
+    k<<<grid, kTcThreads, smem, s>>>((const unsigned char *)spec_a, (const unsigned char *)spec_lo,
+                                      (const unsigned char *)p.tc_bank, p.tc_bank_lo, p.tc_chunks,
+                                      p.tc_n_ch,
                                       p.tc_inv_energy, plane, partials, p.n_r,
                                       p.tc_win * 4,
                                       p.tc_max_ks * kTcSlab, p.flags, p.tc_edges);
@@ -604,8 +678,9 @@ std::vector<TcChunk> tc_chunk_table(const Plan &p, const std::vector<int32_t> &m
 }
 
 bool tc_applicable(const Plan &p, std::string *why) {
-    if (p.prec == FDAS_FP32) {
-        if (why) *why = "the tensor-core correlation takes 16-bit storage (FDAS_BF16/FDAS_FP16)";
+    if (p.prec == FDAS_FP32 && !p.tc_split) {
+        if (why) *why = "the tensor-core correlation takes 16-bit storage (FDAS_BF16/FDAS_FP16), "
+                        "or FP32 storage with FDAS_CORR_TENSOR_SPLIT";
         return false;
     }
     if (p.n_r % kTcTile != 0) {
@@ -618,7 +693,7 @@ bool tc_applicable(const Plan &p, std::string *why) {
         cudaGetLastError();
         optin = 0;
     }
-    if (tc_smem_bytes(p.tc_max_ks, p.tc_win) + 1024 > (size_t)optin) {
+    if (tc_smem_bytes(p.tc_max_ks, p.tc_win, p.tc_split) + 1024 > (size_t)optin) {
         if (why) *why = "the widest template chunk does not fit in shared memory (z_max too large)";
         return false;
     }
@@ -641,15 +716,24 @@ fdas_status launch_tc_bank(Plan &p, cudaStream_t s) {
     switch (p.prec) {
         case FDAS_BF16:
             tc_bank_kernel<PrecBF16><<<grid, 256, 0, s>>>((uint16_t *)p.tc_bank, p.tc_chunks, p.taps,
-                                                          p.tap_off, p.tap_m, p.m_ov);
+                                                          p.tap_off, p.tap_m, p.m_ov, false);
             tc_energy_kernel<PrecBF16><<<p.n_z, 128, 0, s>>>(p.tc_inv_energy, p.taps, p.tap_off,
-                                                             p.tap_m);
+                                                             p.tap_m, false);
             break;
         case FDAS_FP16:
             tc_bank_kernel<PrecF16><<<grid, 256, 0, s>>>((uint16_t *)p.tc_bank, p.tc_chunks, p.taps,
-                                                         p.tap_off, p.tap_m, p.m_ov);
+                                                         p.tap_off, p.tap_m, p.m_ov, false);
             tc_energy_kernel<PrecF16><<<p.n_z, 128, 0, s>>>(p.tc_inv_energy, p.taps, p.tap_off,
-                                                            p.tap_m);
+                                                            p.tap_m, false);
+            break;
+        case FDAS_FP32:   // split mode: BF16 hi and lo images
+            tc_bank_kernel<PrecBF16><<<grid, 256, 0, s>>>((uint16_t *)p.tc_bank, p.tc_chunks, p.taps,
+                                                          p.tap_off, p.tap_m, p.m_ov, false);
+            tc_bank_kernel<PrecBF16><<<grid, 256, 0, s>>>(
+                (uint16_t *)((unsigned char *)p.tc_bank + p.tc_bank_lo), p.tc_chunks, p.taps,
+                p.tap_off, p.tap_m, p.m_ov, true);
+            tc_energy_kernel<PrecBF16><<<p.n_z, 128, 0, s>>>(p.tc_inv_energy, p.taps, p.tap_off,
+                                                             p.tap_m, true);
             break;
         default:
             set_error("tensor-core correlation: 16-bit precisions only");
@@ -668,6 +752,12 @@ fdas_status launch_correlate_tc(Plan &p, const void *spec_padded, void *plane, d
         case FDAS_FP16:
             return cplx ? launch_tc_P<PrecF16, kCplx>(p, spec_padded, plane, partials, s)
                         : launch_tc_P<PrecF16, kPower>(p, spec_padded, plane, partials, s);
+        case FDAS_FP32:
+            if (cplx) {
+                set_error("the split tensor-core correlation writes power planes only");
+                return FDAS_ERR_UNSUPPORTED;
+            }
+            return launch_tc_P<PrecF32, kPower>(p, spec_padded, plane, partials, s);
         default:
             set_error("tensor-core correlation: 16-bit precisions only");
             return FDAS_ERR_UNSUPPORTED;

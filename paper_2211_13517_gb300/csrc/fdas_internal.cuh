@@ -169,6 +169,13 @@ struct Plan {
     void *tc_bank = nullptr;
     float *tc_inv_energy = nullptr;   // [n_z] 1 / energy of the 16-bit taps
     float4 *tc_edges = nullptr;       // interbinning: [n_z][n_r / 512][4] first/last F
+    // FP32 plans on the tensor cores (FDAS_CORR_TENSOR_SPLIT): operands as
+    // BF16 hi + lo parts; the lo template image sits tc_bank_lo bytes after
+    // the hi one, the spectrum parts in spec_hi / spec_lo (padded like spec_pad)
+    bool tc_split = false;
+    int64_t tc_bank_lo = 0;
+    void *spec_hi = nullptr, *spec_lo = nullptr;
+    int64_t tc_split_elems = 0;
     int tc_n_ch = 0, tc_max_ks = 0, tc_win = 0;
     // FFT split of the N/2-point complex FFT in the spectrum stage
     int fft_m1, fft_m2;     // M = m1 * m2 (m1 = 1: single pass)

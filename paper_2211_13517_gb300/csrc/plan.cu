@@ -79,6 +79,8 @@ static void free_plan_memory(Plan *p) {
     cudaFree(p->tc_bank);
     cudaFree(p->tc_inv_energy);
     cudaFree(p->tc_edges);
+    cudaFree(p->spec_hi);
+    cudaFree(p->spec_lo);
     for (int b = 0; b < 2; ++b) {
         cudaFree(p->plane[b]);
         cudaFree(p->partials[b]);
@@ -242,8 +244,12 @@ static fdas_status create(Plan *&out, int64_t n_samples, double tsamp, double z_
     if (o->autotune != 0 && o->autotune != 1) return arg_error("autotune must be 0 or 1");
     if (o->use_graph != 0 && o->use_graph != 1) return arg_error("use_graph must be 0 or 1");
     if (o->correlator != FDAS_CORR_AUTO && o->correlator != FDAS_CORR_FFT &&
-        o->correlator != FDAS_CORR_TENSOR)
+        o->correlator != FDAS_CORR_TENSOR && o->correlator != FDAS_CORR_TENSOR_SPLIT)
         return arg_error("unknown correlator");
+    if (o->correlator == FDAS_CORR_TENSOR_SPLIT && o->precision != FDAS_FP32)
+        return arg_error("correlator FDAS_CORR_TENSOR_SPLIT: FDAS_FP32 storage only");
+    if (o->correlator == FDAS_CORR_TENSOR_SPLIT && o->interbin)
+        return arg_error("correlator FDAS_CORR_TENSOR_SPLIT: no interbinning (use the FFT correlator)");
     if (o->harmonic_mode != FDAS_HARM_TOP && o->harmonic_mode != FDAS_HARM_FUNDAMENTAL)
         return arg_error("unknown harmonic_mode");
     if (o->interbin != 0 && o->interbin != 1) return arg_error("interbin must be 0 or 1");
@@ -322,16 +328,18 @@ static fdas_status create(Plan *&out, int64_t n_samples, double tsamp, double z_
     // the correlator: the tensor-core GEMM where it applies (16-bit storage,
     // template chunks that fit in shared memory), else overlap-save FFTs
     std::vector<TcChunk> tc_table;
-    if (o->correlator != FDAS_CORR_FFT && p.prec != FDAS_FP32) {
+    p.tc_split = o->correlator == FDAS_CORR_TENSOR_SPLIT;
+    if (o->correlator != FDAS_CORR_FFT && (p.prec != FDAS_FP32 || p.tc_split)) {
         tc_table = tc_chunk_table(p, m, &p.tc_win, &p.tc_max_ks);
         p.tc_n_ch = (int)tc_table.size();
     }
     {
         std::string why = "the tensor-core correlation takes 16-bit storage (FDAS_BF16/FDAS_FP16)";
         const bool tc_ok = !tc_table.empty() && tc_applicable(p, &why);
-        if (o->correlator == FDAS_CORR_TENSOR && !tc_ok) {
+        if ((o->correlator == FDAS_CORR_TENSOR || p.tc_split) && !tc_ok) {
             delete pp;
-            return arg_error("correlator FDAS_CORR_TENSOR: " + why);
+            return arg_error(std::string(p.tc_split ? "correlator FDAS_CORR_TENSOR_SPLIT: "
+                                                    : "correlator FDAS_CORR_TENSOR: ") + why);
         }
         p.correlator = (o->correlator != FDAS_CORR_FFT && tc_ok) ? FDAS_CORR_TENSOR : FDAS_CORR_FFT;
         if (p.correlator != FDAS_CORR_TENSOR) {
@@ -411,7 +419,13 @@ static fdas_status create(Plan *&out, int64_t n_samples, double tsamp, double z_
     if (p.correlator == FDAS_CORR_TENSOR) {
         const int64_t img = tc_bank_bytes(tc_table);
         PLAN_TRY(dalloc(p, &p.tc_chunks, sizeof(TcChunk) * tc_table.size()));
-        PLAN_TRY(dalloc(p, &p.tc_bank, (size_t)img));
+        if (p.tc_split) {
+            p.tc_bank_lo = img;
+            p.tc_split_elems = (int64_t)pad_elems;
+            PLAN_TRY(dalloc(p, &p.spec_hi, 4 * pad_elems));
+            PLAN_TRY(dalloc(p, &p.spec_lo, 4 * pad_elems));
+        }
+        PLAN_TRY(dalloc(p, &p.tc_bank, (size_t)img * (p.tc_split ? 2 : 1)));
         PLAN_TRY(dalloc(p, &p.tc_inv_energy, sizeof(float) * (size_t)p.n_z));
         if (p.interbin) PLAN_TRY(dalloc(p, &p.tc_edges, (size_t)tc_edge_bytes(p)));
         PLAN_CUDA(cudaMemcpyAsync(p.tc_chunks, tc_table.data(), sizeof(TcChunk) * tc_table.size(),
@@ -775,7 +789,9 @@ static fdas_status create_tuned(Plan *&out, int64_t n_samples, double tsamp, dou
                                 double z_step, int32_t seg_len, int32_t n_harm, fdas_opts o) {
     o.autotune = 0;
     std::vector<std::pair<int32_t, int32_t>> cand;   // (seg_len, correlator)
-    if (o.correlator != FDAS_CORR_TENSOR) {
+    if (o.correlator == FDAS_CORR_TENSOR_SPLIT)
+        cand.push_back({seg_len, FDAS_CORR_TENSOR_SPLIT});   // asked for explicitly
+    else if (o.correlator != FDAS_CORR_TENSOR) {
         std::vector<int32_t> lens = {2048, 4096, 8192};
         if (std::find(lens.begin(), lens.end(), seg_len) == lens.end()) lens.push_back(seg_len);
         for (int32_t L : lens) cand.push_back({L, FDAS_CORR_FFT});
@@ -911,7 +927,7 @@ fdas_status fdas_plan_get_info(const fdas_plan *plan, fdas_plan_info *info) {
     info->z_chunks = p.n_zchunk;
     info->use_graph = p.use_graph ? 1 : 0;
     info->tuned_ms = p.tuned_ms;
-    info->correlator = p.correlator;
+    info->correlator = p.tc_split ? FDAS_CORR_TENSOR_SPLIT : p.correlator;
     info->harmonic_mode = p.harm_mode;
     info->interbin = p.interbin ? 1 : 0;
     info->reserved0 = 0;

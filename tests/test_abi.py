@@ -112,6 +112,18 @@ def test_opts_validation(capi):
     with pytest.raises(capi.FdasError) as ei:
         capi.fdas_plan_create(1 << 17, 64e-6, 16.0, 2.0, 2048, 4, o)
     assert ei.value.status == capi.FDAS_ERR_ARG and "interbin" in str(ei.value)
+    # the split tensor-core correlation is for FP32 storage, without interbinning
+    o = capi.fdas_opts_default()
+    o.correlator = capi.FDAS_CORR_TENSOR_SPLIT
+    o.precision = capi.FDAS_BF16
+    with pytest.raises(capi.FdasError) as ei:
+        capi.fdas_plan_create(1 << 17, 64e-6, 16.0, 2.0, 2048, 4, o)
+    assert ei.value.status == capi.FDAS_ERR_ARG and "FP32" in str(ei.value)
+    o.precision = capi.FDAS_FP32
+    o.interbin = 1
+    with pytest.raises(capi.FdasError) as ei:
+        capi.fdas_plan_create(1 << 17, 64e-6, 16.0, 2.0, 2048, 4, o)
+    assert ei.value.status == capi.FDAS_ERR_ARG and "interbinning" in str(ei.value)
     # the half-bin plane of a 2^24-sample series has 2^24 columns: refused
     o = capi.fdas_opts_default()
     o.interbin = 1

@@ -180,6 +180,38 @@ def test_tensor_plane_matches_direct_correlation(capi, n, z_max, z_step, prec):
     plan.close()
 
 
+@pytest.mark.parametrize("n,z_max,z_step", [
+    (1 << 10, 2.0, 1.0),        # one 512-bin tile
+    (1 << 14, 7.5, 0.5),        # half-step grid, ragged last chunk
+    (1 << 16, 96.0, 1.0),       # the 193-template grid: the widest chunks that fit
+])
+def test_tensor_split_fp32_plane(capi, n, z_max, z_step):
+    """FP32 storage on the tensor cores (BF16 hi + lo operands, three
+    products per term): every cell within the FP32 bound 1e-4 * max(P, mean)
+    of the FP64 direct sum, statistics within 1e-5."""
+    plan, plane, stats, P, g = _plane_case(capi, n, z_max, z_step, 1024 if n < (1 << 16) else 8192,
+                                           prec=0, corr=capi.FDAS_CORR_TENSOR_SPLIT)
+    got = plane.cpu().numpy().astype(np.float64)
+    mean, std = O.plane_stats(P)
+    rel = np.abs(got - P) / np.maximum(P, mean)
+    assert rel.max() < 1e-4, (rel.max(), np.unravel_index(np.argmax(rel), rel.shape))
+    s = stats.cpu().numpy()
+    assert abs(s[0] / mean - 1) < 1e-5 and abs(s[1] / std - 1) < 1e-5, (s, mean, std)
+    plan.close()
+
+
+def test_tensor_split_fp32_search(capi):
+    n = 1 << 16
+    x, _ = S.pulsar_series(n, seed=21, height=1.0, z_abs=14.0)
+    ref = O.search(x, 16.0, 2.0, 16, guard=1e-4)
+    plan = _plan(capi, n, 16.0, 2.0, 2048, 16, correlator=capi.FDAS_CORR_TENSOR_SPLIT)
+    assert plan.info.correlator == capi.FDAS_CORR_TENSOR_SPLIT
+    st, cands, nf = plan.search([torch.from_numpy(x).cuda()], capacity=1 << 18)
+    assert st == capi.FDAS_OK and nf == len(cands) and nf > 0
+    _compare_cands(cands, ref["candidates"], ref["guard"], rel_power=1e-4)
+    plan.close()
+
+
 def test_tensor_correlator_is_refused_where_it_does_not_apply(capi):
     with pytest.raises(capi.FdasError) as ei:
         _plan(capi, 1 << 14, 16.0, 2.0, 2048, 4, precision=capi.FDAS_FP32,
