@@ -108,11 +108,6 @@ __host__ __device__ constexpr int src_off(int H, int o, int j) {
     return o < 0 ? -(((-o) * j + H / 2) / H) : ((o * j + H / 2) / H);
 }
 
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all_() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // element offset of the source row of every harmonic for top row iz (the
 // same for the whole CTA): threads 0..H-1 fill it, then the CTA synchronises

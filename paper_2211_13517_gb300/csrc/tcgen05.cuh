@@ -96,12 +96,7 @@ __device__ __forceinline__ void tmem_ld_wait() {
 
 // plain arrival on an mbarrier
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-    uint64_t state;
-    asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];\n"
-                 : "=l"(state)
-                 : "r"(smem_u32(bar))
-                 : "memory");
-    (void)state;
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
 }
 
 }  // namespace fdas

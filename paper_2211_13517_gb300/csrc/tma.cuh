@@ -36,12 +36,9 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
 }
 
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned bytes) {
-    uint64_t state;
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;\n"
-                 : "=l"(state)
-                 : "r"(smem_u32(bar)), "r"(bytes)
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
                  : "memory");
-    (void)state;
 }
 
 __device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, unsigned bytes,
