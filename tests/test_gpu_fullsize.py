@@ -9,6 +9,8 @@
   configuration): each GPU candidate's harmonic sum is recomputed by the
   oracle one cell at a time from the series' own spectrum, and must be
   within 3% and above the oracle threshold minus 3%.
+* FP32 storage on the tensor cores (split BF16 operands) at full size:
+  sampled plane cells within the FP32 bound, the oracle's candidates.
 * Interbinning at full size (BF16, the tensor-core epilogue that writes the
   half-bin plane): sampled cells of the 193 x 2^23-column plane, every kind of
   half bin (inside a warp's rows, at a warp edge, at a tile edge, the last
@@ -101,6 +103,41 @@ def test_fullsize_low_precision_power_error(capi, pulsar_case, prec, corr):
                                   ref["candidates"]["ir"], ref["candidates"]["power"])
             if (int(h), int(z), int(i)) in gp]
     assert len(errs) > 0 and max(errs) <= 0.03, max(errs)
+    plan.close()
+
+
+def test_fullsize_fp32_tensor_split(capi, pulsar_case):
+    """FP32 storage on the tensor cores (BF16 hi + lo operands) at full size:
+    sampled plane cells within the FP32 bound of the FP64 direct sum on the
+    spectrum as stored, and the oracle's candidates outside the 1e-4 guard."""
+    x, params, ref = pulsar_case
+    plan = capi.Plan(N, 64e-6, Z_MAX, Z_STEP, L, H, correlator=capi.FDAS_CORR_TENSOR_SPLIT)
+    assert plan.info.correlator == capi.FDAS_CORR_TENSOR_SPLIT
+    xd = torch.from_numpy(x).cuda()
+    spec = plan.spectrum(xd)
+    plane, stats = plan.power_plane(spec)
+    torch.cuda.synchronize()
+    a = spec.cpu().numpy().astype(np.float64)
+    Xs = a[0::2] + 1j * a[1::2]
+    g = O.geometry(N, Z_MAX, Z_STEP, H)
+    rng = np.random.default_rng(8)
+    iz = rng.integers(0, g.n_z, 8000)
+    r = rng.integers(0, g.n_r, 8000)
+    want = O.cell_powers(Xs, O.template_bank(g), iz, r)
+    got = plane[torch.from_numpy(iz).cuda(), torch.from_numpy(r).cuda()].cpu().numpy()
+    err = np.abs(got - want) / np.maximum(want, ref["mean"])
+    assert err.max() < 1e-4, err.max()
+    s = stats.cpu().numpy()
+    assert abs(s[0] / ref["mean"] - 1) < 1e-5 and abs(s[1] / ref["std"] - 1) < 1e-4
+    del plane
+    st, cands, nf = plan.search([xd], capacity=1 << 18)
+    assert st == capi.FDAS_OK and nf == len(cands) > 0
+    T = ref["T"]
+    guard = {(0, int(h), int(z), int(i)) for h, z, i, p in
+             zip(ref["guard"]["harm"], ref["guard"]["iz"], ref["guard"]["ir"], ref["guard"]["power"])
+             if abs(p - T[int(np.log2(h))]) <= 1e-4 * T[int(np.log2(h))]}
+    gk, rk = _keyset(cands, "trial_id"), _keyset(ref["candidates"], "trial")
+    assert not ((gk ^ rk) - guard), sorted((gk ^ rk) - guard)[:10]
     plan.close()
 
 
