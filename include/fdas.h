@@ -45,7 +45,7 @@ typedef enum {
     FDAS_ERR_CAND_OVERFLOW = 4,  /* more candidates than the caller's buffer */
     FDAS_ERR_NONFINITE = 5,      /* NaN or Inf in an input series           */
     FDAS_ERR_TIMEOUT = 6,        /* a bounded device wait gave up            */
-    FDAS_ERR_UNSUPPORTED = 7     /* valid request this build cannot serve    */
+    FDAS_ERR_UNSUPPORTED = 7     /* valid request the library does not serve */
 } fdas_status;
 
 /* storage precision of spectra, templates and the power plane; the
