@@ -376,7 +376,27 @@ def run_gpu(args, rank, world, local_rank, dist):
                            precision=capi.FDAS_FP32)
         ms_fp32, _, j_fp32, _, _ = timed(plan32, xs, args.steps, args.warmup, False, energy)
         _, prof_fp32, _, _, _ = timed(plan32, xs, 1, 1, True)
+        # BF16 against FP32 on the first 8 series (untimed): the largest
+        # relative error of S over the candidates both report, and how far
+        # the two candidate lists agree
+        nb = min(8, len(xs))
+        _, c32, _ = plan32.search(xs[:nb], trial_ids=ids[:nb], capacity=1 << 18)
         plan32.close()
+        planb = capi.Plan(N_SAMPLES, TSAMP, Z_MAX, Z_STEP, SEG_LEN, N_HARM,
+                          precision=capi.FDAS_BF16)
+        _, c16, _ = planb.search(xs[:nb], trial_ids=ids[:nb], capacity=1 << 18)
+        planb.close()
+        k32 = {(int(t), int(h), int(z), int(r)): float(pw) for t, h, z, r, pw in
+               zip(c32["trial_id"], c32["harm"], c32["iz"], c32["ir"], c32["power"])}
+        k16 = {(int(t), int(h), int(z), int(r)): float(pw) for t, h, z, r, pw in
+               zip(c16["trial_id"], c16["harm"], c16["iz"], c16["ir"], c16["power"])}
+        common = set(k32) & set(k16)
+        cmp16 = {"series": nb, "fp32_candidates": len(k32), "bf16_candidates": len(k16),
+                 "common": len(common),
+                 "max_rel_err_common": max((abs(k16[k] / k32[k] - 1) for k in common),
+                                           default=None),
+                 "note": "S_h of BF16 storage against FP32 storage on the same series; "
+                         "candidates present in one list only lie near the threshold"}
         # FP32 storage with the split (BF16 hi + lo) tensor-core correlation
         plan3 = capi.Plan(N_SAMPLES, TSAMP, Z_MAX, Z_STEP, SEG_LEN, N_HARM,
                           precision=capi.FDAS_FP32, correlator=capi.FDAS_CORR_TENSOR_SPLIT)
@@ -518,6 +538,7 @@ def run_gpu(args, rank, world, local_rank, dist):
                         "hbm_alg_frac": wm32["alg_bytes"] * args.batch * args.steps
                         / (ms_fp32 / 1000.0) / 1e9 / peak_hbm}
         line["bf16_speedup_vs_fp32"] = value / v32
+        line["bf16_vs_fp32"] = cmp16
         line["fp32_tensor_split"] = {
             "value": args.batch * args.steps * world / (ms_fp32s / 1000.0), "unit": UNIT,
             "ms_per_step": ms_fp32s / args.steps,
