@@ -107,7 +107,8 @@ class fdas_profile(Structure):
                 ("ms", c_double * 4)]
 
 
-PROFILE_GROUPS = ["spectrum", "correlate", "harmonic", "finish"]
+FDAS_PROF_SPECTRUM, FDAS_PROF_CORRELATE, FDAS_PROF_HARMONIC, FDAS_PROF_FINISH = 0, 1, 2, 3
+PROFILE_GROUPS = ["spectrum", "correlate", "harmonic", "finish"]   # index = FDAS_PROF_*
 
 
 class fdas_dedisp_info(Structure):

@@ -141,3 +141,17 @@ def test_null_arguments_rejected(capi):
     assert lib.fdas_selftest_wait_timeout(None, 1000, None) == capi.FDAS_ERR_ARG
     assert lib.fdas_refine(None, None, None, 0, 0, None, None) == capi.FDAS_ERR_ARG
     assert lib.fdas_correlation_plane(None, None, None, None) == capi.FDAS_ERR_ARG
+
+
+def test_binding_constants_match_the_header(capi):
+    """Every enumerator of include/fdas.h has the same value in the binding."""
+    import re
+    src = open(os.path.join(ROOT, "include", "fdas.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    found = 0
+    for body in re.findall(r"enum\s*\{([^}]*)\}", src):
+        for name, val in re.findall(r"(FDAS_[A-Z0-9_]+)\s*=\s*(\d+)", body):
+            assert hasattr(capi, name), name
+            assert getattr(capi, name) == int(val), (name, getattr(capi, name), val)
+            found += 1
+    assert found >= 20
