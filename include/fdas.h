@@ -45,7 +45,9 @@ typedef enum {
     FDAS_ERR_CAND_OVERFLOW = 4,  /* more candidates than the caller's buffer */
     FDAS_ERR_NONFINITE = 5,      /* NaN or Inf in an input series           */
     FDAS_ERR_TIMEOUT = 6,        /* a bounded device wait gave up            */
-    FDAS_ERR_UNSUPPORTED = 7     /* valid request the library does not serve */
+    FDAS_ERR_UNSUPPORTED = 7,    /* valid request the library does not serve */
+    FDAS_ERR_CAND_STORE_FULL = 8 /* more crossings than the plan's device
+                                    store (fdas_opts.max_candidates)         */
 } fdas_status;
 
 /* storage precision of spectra, templates and the power plane; the
@@ -207,10 +209,14 @@ fdas_status fdas_plan_get_info(const fdas_plan *plan, fdas_plan_info *info);
  * (S - h mean)/(sqrt(h) std).
  * Blocking: returns after the results are in `cands`.
  * Errors: FDAS_ERR_ARG; FDAS_ERR_NONFINITE (a series holds NaN/Inf: no
- * candidates are returned); FDAS_ERR_CAND_OVERFLOW (*n_found is the true
- * total, the first `capacity` entries in the order above are written when the
- * total fits the plan's max_candidates, otherwise an unspecified subset);
- * FDAS_ERR_CUDA.
+ * candidates are returned); FDAS_ERR_CAND_OVERFLOW (more crossings than
+ * `capacity` but no more than the plan's max_candidates: *n_found is the true
+ * total and the first `capacity` entries in the order above are written);
+ * FDAS_ERR_CAND_STORE_FULL (more crossings than the plan's max_candidates:
+ * the device store kept only some of them, in an order that depends on
+ * scheduling, so no entry is written; *n_found is the true total; search
+ * again with a larger max_candidates or a higher threshold); FDAS_ERR_CUDA.
+ * FDAS_ERR_CAND_STORE_FULL takes precedence over FDAS_ERR_CAND_OVERFLOW.
  */
 fdas_status fdas_search(fdas_plan *plan, const fdas_series *batch,
                         int32_t n_series, fdas_candidate *cands,
@@ -294,8 +300,8 @@ fdas_status fdas_refine(fdas_plan *plan, const float *spectrum,
  * white noise leaves with unit mean power.
  * series: device, N floats.  spectrum_out: device, N_r complex elements of
  * the plan's precision.  medians_out: device float[N_r / norm_block] or NULL.
- * Returns FDAS_ERR_NONFINITE after the fact only through fdas_search; this
- * call does not check.
+ * Non-finite input is not reported by this call (a NaN or Inf propagates
+ * into the spectrum); fdas_search reports it as FDAS_ERR_NONFINITE.
  */
 fdas_status fdas_spectrum(fdas_plan *plan, const float *series,
                           void *spectrum_out, float *medians_out, void *stream);
@@ -339,7 +345,8 @@ fdas_status fdas_harmonic_sums(fdas_plan *plan, const void *plane,
 /*
  * Harmonic sum + threshold of one plane with given statistics.
  * stats: device double[2] {mean, std} (e.g. from fdas_power_plane).
- * cands/capacity/n_found as in fdas_search (one trial, id `trial_id`).
+ * cands/capacity/n_found and the statuses FDAS_ERR_CAND_OVERFLOW /
+ * FDAS_ERR_CAND_STORE_FULL as in fdas_search (one trial, id `trial_id`).
  * Blocking.
  */
 fdas_status fdas_threshold(fdas_plan *plan, const void *plane,
@@ -362,9 +369,10 @@ fdas_status fdas_template_bank(fdas_plan *plan, double *taps_out,
 
 /*
  * Allocation-free spectrum (no counterpart in the paper; an addition for
- * callers that must not allocate device memory, such as code that runs while
- * a stream is being captured into a CUDA graph, or a real-time pipeline that
- * reserves all of its GPU memory up front and forbids allocation afterwards).
+ * callers that must not allocate device memory when they call in, such as a
+ * real-time pipeline that reserves all of its GPU memory up front and forbids
+ * allocation afterwards, or a host whose device memory is handed out by
+ * another allocator that must not be bypassed).
  *
  * Computes exactly what fdas_spectrum computes (R2C FFT, X_0 = 0, median
  * normalisation with blocks of norm_block bins) without a plan: the FFT
@@ -385,6 +393,8 @@ fdas_status fdas_template_bank(fdas_plan *plan, double *taps_out,
  * one array and each call overwrites what the previous left there, so calls
  * whose work may overlap on the GPU (different streams without ordering, or
  * several host threads) race with one another: order them on one stream.
+ * Like fdas_spectrum, it does not report non-finite input (a NaN or Inf in
+ * the series propagates into the spectrum; fdas_search reports it).
  */
 fdas_status fdas_spectrum_static(const float *series, int64_t n_samples,
                                  int32_t precision, int32_t norm_mode,
@@ -487,6 +497,26 @@ fdas_status fdas_dedisperse(fdas_dedisp_plan *plan, const float *filterbank, flo
  * FP32 (exact: n_chan * 255 < 2^24). */
 fdas_status fdas_dedisperse_u8(fdas_dedisp_plan *plan, const uint8_t *filterbank, float *out,
                                void *stream);
+
+/* ---------------------------------------------------------------------
+ * Host-side fault injection (no counterpart in the paper): the environment
+ * variable FDAS_FAULT, read at every call, makes the library take an error
+ * path on purpose, without any fault on the device, so that callers and
+ * tests can check how failures are reported and cleaned up:
+ *   "alloc:N"   the N-th device allocation made for a plan (counted from
+ *               fdas_plan_create, N >= 1; "alloc" means "alloc:1") fails as
+ *               if the device were out of memory: FDAS_ERR_OOM, and a failed
+ *               fdas_plan_create frees everything it had allocated;
+ *   "capacity"  fdas_search / fdas_threshold run with a device candidate
+ *               store of one record: two or more crossings give
+ *               FDAS_ERR_CAND_STORE_FULL;
+ *   "nan_input" fdas_search / fdas_threshold report FDAS_ERR_NONFINITE after
+ *               the search, as for a series holding NaN or Inf;
+ *   "bad_args"  fdas_plan_create and fdas_search return FDAS_ERR_ARG before
+ *               doing anything.
+ * Unset or empty: no fault.  Any other value: the calls above return
+ * FDAS_ERR_ARG naming the value.
+ * --------------------------------------------------------------------- */
 
 /* Thread-local message describing the last failed call ("" if none). */
 const char *fdas_last_error(void);

@@ -28,9 +28,14 @@ FDAS_ERR_CAND_OVERFLOW = 4
 FDAS_ERR_NONFINITE = 5
 FDAS_ERR_TIMEOUT = 6
 FDAS_ERR_UNSUPPORTED = 7
+FDAS_ERR_CAND_STORE_FULL = 8
 STATUS_NAMES = {0: "FDAS_OK", 1: "FDAS_ERR_ARG", 2: "FDAS_ERR_CUDA", 3: "FDAS_ERR_OOM",
                 4: "FDAS_ERR_CAND_OVERFLOW", 5: "FDAS_ERR_NONFINITE",
-                6: "FDAS_ERR_TIMEOUT", 7: "FDAS_ERR_UNSUPPORTED"}
+                6: "FDAS_ERR_TIMEOUT", 7: "FDAS_ERR_UNSUPPORTED",
+                8: "FDAS_ERR_CAND_STORE_FULL"}
+# statuses fdas_search / fdas_threshold return (not raise): the call ran and
+# *n_found holds the true number of crossings
+COUNT_STATUSES = (FDAS_ERR_CAND_OVERFLOW, FDAS_ERR_CAND_STORE_FULL)
 
 FDAS_FP32, FDAS_BF16, FDAS_FP16 = 0, 1, 2
 FDAS_THRESH_GAMMA_TAIL, FDAS_THRESH_MEAN_PLUS_KSIGMA = 0, 1
@@ -264,10 +269,11 @@ def fdas_dedisperse_u8(plan, filterbank_ptr, out_ptr, stream=None) -> None:
 
 
 def fdas_search(plan, batch, n_series, cands_ptr, capacity, stream=None):
-    """Returns (status, n_found); FDAS_ERR_CAND_OVERFLOW is returned, not raised."""
+    """Returns (status, n_found); FDAS_ERR_CAND_OVERFLOW and
+    FDAS_ERR_CAND_STORE_FULL are returned, not raised."""
     n = c_int64(0)
     st = lib().fdas_search(plan, batch, n_series, cands_ptr, capacity, ctypes.byref(n), stream)
-    _check(st, "fdas_search", allow=(FDAS_ERR_CAND_OVERFLOW,))
+    _check(st, "fdas_search", allow=COUNT_STATUSES)
     return st, n.value
 
 
@@ -293,7 +299,7 @@ def fdas_threshold(plan, plane_ptr, stats_ptr, trial_id, cands_ptr, capacity, st
     n = c_int64(0)
     st = lib().fdas_threshold(plan, plane_ptr, stats_ptr, trial_id, cands_ptr, capacity,
                               ctypes.byref(n), stream)
-    _check(st, "fdas_threshold", allow=(FDAS_ERR_CAND_OVERFLOW,))
+    _check(st, "fdas_threshold", allow=COUNT_STATUSES)
     return st, n.value
 
 
@@ -406,7 +412,7 @@ class Plan:
     def search(self, series, trial_ids=None, capacity=1 << 16, stream=None, out=None):
         """series: list of 1-D float32 tensors (device or host).  Returns
         (status, numpy structured array of the first min(n, capacity)
-        candidates, n_found)."""
+        candidates -- none with FDAS_ERR_CAND_STORE_FULL --, n_found)."""
         n = len(series)
         batch = (fdas_series * max(n, 1))()
         for i, x in enumerate(series):
@@ -418,7 +424,8 @@ class Plan:
             out = np.zeros(capacity, dtype=CANDIDATE_DTYPE)
         st, nf = fdas_search(self.handle, batch, n, out.ctypes.data_as(c_void_p), out.shape[0],
                              _stream_ptr(stream))
-        return st, out[:min(nf, out.shape[0])], nf
+        k = 0 if st == FDAS_ERR_CAND_STORE_FULL else min(nf, out.shape[0])
+        return st, out[:k], nf
 
     def profile(self, on=None):
         """Enable/disable tracing (resetting it) or, with no argument, read it
@@ -473,7 +480,8 @@ class Plan:
         st, nf = fdas_threshold(self.handle, c_void_p(plane.data_ptr()),
                                 c_void_p(stats.data_ptr()), trial_id,
                                 out.ctypes.data_as(c_void_p), capacity, _stream_ptr(stream))
-        return st, out[:min(nf, capacity)], nf
+        k = 0 if st == FDAS_ERR_CAND_STORE_FULL else min(nf, capacity)
+        return st, out[:k], nf
 
     # -- refinement (spectrum: complex64 device tensor of N_r bins) ------------
     def fourier_power(self, spectrum, rz, stream=None):

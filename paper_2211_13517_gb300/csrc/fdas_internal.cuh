@@ -153,6 +153,8 @@ struct Plan {
     double tsamp, z_max, z_step, sigma;
     double G[6];
     int64_t max_cands;
+    int64_t store_cap = 0;  // records the kernels may store this call (max_cands)
+    int64_t n_allocs = 0;   // device allocations made for the plan so far
     int device;
     int n_zchunk;           // z chunks per segment in the correlation grid
     int n_sms = 1;          // streaming multiprocessors of the device
@@ -217,7 +219,9 @@ struct Plan {
     int64_t timed[4] = {0, 0, 0, 0};
     double prof_ms[4] = {0, 0, 0, 0};
     std::vector<cudaEvent_t> events;   // pool for timed intervals
-    cudaStream_t aux = nullptr;     // second stream (harmonic sum overlap)
+    cudaStream_t aux = nullptr;     // second stream (harmonic sum overlap), lowest priority
+    cudaStream_t hi = nullptr;      // spectrum + correlation, highest priority
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;   // caller's stream <-> hi
     cudaEvent_t ev_conv[2] = {nullptr, nullptr};
     cudaEvent_t ev_hsum[2] = {nullptr, nullptr};
 };

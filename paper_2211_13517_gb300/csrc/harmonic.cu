@@ -230,22 +230,26 @@ __global__ void __launch_bounds__(kHsThreads)
 // so the thread needs only the DMAX_j + 1 consecutive bins starting at
 // j (B + 16 t)/H, and which of them each cell adds is a compile-time index.
 // A CTA (T = 128 threads, 2048 cells) walks QROWS consecutive top rows.  For
-// each row thread 0 copies, for every harmonic whose source row differs from
-// the previous row's (for the first row, every harmonic), the span of the
-// source row that the CTA needs (starting at j B / H, a multiple of 128
-// elements, so 16-byte aligned) into that harmonic's place in shared memory
-// with one bulk asynchronous copy.  From one top row to the next, source row
-// o_j changes with probability j/H, so the walk copies about 30% fewer bytes
-// than copying every span for every row.  The copies of each stage complete
-// on that stage's own mbarrier (bounded waits; one phase per row), so the
-// first stages are summed while later spans are still arriving.  With 16-bit
-// planes the top row itself (j = H, changed every row) is not staged: each
-// thread loads its 16 cells of it from global memory into registers one row
-// ahead, which leaves a smaller shared-memory footprint (7 CTAs per SM
-// instead of 6).  Each
-// thread reads its values with the widest aligned shared-memory loads, adds
-// them to its cells (16-bit planes: one mixed-precision add each), compares
-// each completed stage with its threshold and appends every crossing.
+// each row, lane j of warp 0 copies, if harmonic j_at(H, j) reads another
+// source row than for the previous row (for the first row, every harmonic),
+// the span of that source row the CTA needs (starting at j B / H, a multiple
+// of 128 elements, so 16-byte aligned) into the harmonic's place in shared
+// memory with one bulk asynchronous copy; the lanes issue their copies side
+// by side (the span constants of each lane are set once per CTA), which
+// keeps the copy issue off the critical path of the row.  From one top row
+// to the next, source row o_j changes with probability j/H, so the walk
+// copies about 30% fewer bytes than copying every span for every row.  The
+// copies of each stage complete on that stage's own mbarrier (bounded waits;
+// one phase per row), so the first stages are summed while later spans are
+// still arriving.  With 16-bit planes the top row itself (j = H, changed
+// every row) is not staged: each thread loads its 16 cells of it from global
+// memory into registers one row ahead, which leaves a smaller shared-memory
+// footprint (7 CTAs per SM instead of 6).  Each thread reads its values with
+// the widest aligned shared-memory loads (a 16-bit window that starts on an
+// odd element is read as the aligned 32-bit words around it and shifted down
+// by 16 bits), adds them to its cells (16-bit planes: one mixed-precision add
+// each), compares each completed stage with its threshold and appends every
+// crossing.
 // ---------------------------------------------------------------------------
 template <class P, int H>
 struct Dedup {
@@ -256,7 +260,12 @@ struct Dedup {
     static constexpr int EPV = 16 / (int)sizeof(real);
     static constexpr int dmax(int j) { return ((R - 1) * j + H / 2) / H; }
     static constexpr int len(int j) { return (R / H) * j * (T - 1) + dmax(j) + 1; }
-    static constexpr int padlen(int j) { return (len(j) + EPV - 1) / EPV * EPV; }
+    // (16-bit planes: + 4, because a window that starts on an odd element is
+    // read from the word below, up to two elements past its end; this is
+    // shared-memory room only: a copy never reads past the source row's last
+    // bin that a cell of the row can read)
+    static constexpr int MARGIN = sizeof(real) == 2 ? 4 : 0;
+    static constexpr int padlen(int j) { return (len(j) + MARGIN + EPV - 1) / EPV * EPV; }
     static constexpr int off(int j) { return j <= 1 ? 0 : off(j - 1) + padlen(j - 1); }
     // 16-bit planes read the top row (j = H) from global memory into
     // registers, one row ahead; FP32 planes stage it like the others
@@ -307,88 +316,62 @@ struct DedupSteps {
     using D = Dedup<P, H>;
     using real = typename P::real;
 
-    // bytes of the span of harmonic J: from j B / H (16-byte aligned) up to
-    // the last bin of the row the CTA's cells can read, rounded up to 16 bytes
-    template <int J>
-    __device__ __forceinline__ static unsigned span_bytes(int64_t n_r, int64_t B) {
-        const int64_t c0 = (int64_t)J * B / H;
-        const int64_t maxsrc = ((n_r - 1) * J + H / 2) / H;
-        if (maxsrc < c0) return 0u;
-        int64_t n = (maxsrc - c0 + 1 + D::EPV - 1) / D::EPV * D::EPV;
-        if (n > D::padlen(J)) n = D::padlen(J);
-        return (unsigned)(n * (int64_t)sizeof(real));
-    }
     // harmonics are consumed in stage order j_at(H, 0), j_at(H, 1), ...; the
     // harmonics of stage g (indices [2^(g-1), 2^g), index 0 for g = 0) are
     // copied on barrier g, so the sums of a stage start as soon as its own
     // spans have landed while the later ones are still in flight
     static constexpr int NG = ilog2h(H) + 1;
     static constexpr int group_of(int idx) { return idx == 0 ? 0 : ilog2h(idx) + 1; }
-    template <int IDX, int G>
-    __device__ __forceinline__ static unsigned group_bytes(int64_t n_r, int64_t B) {
-        if constexpr (IDX < H) {
-            const unsigned own = group_of(IDX) == G ? span_bytes<j_at(H, IDX)>(n_r, B) : 0u;
-            return own + group_bytes<IDX + 1, G>(n_r, B);
-        } else {
-            return 0u;
-        }
-    }
-    // the same for a CTA whose cells all lie inside the row: every span is
-    // the full padded length, a compile-time constant
+    // bytes of the span of harmonic J for a CTA whose cells all lie inside
+    // the row: the full padded length, a compile-time constant
     static constexpr unsigned full_bytes(int J) { return (unsigned)(D::padlen(J) * sizeof(real)); }
-    static constexpr unsigned full_group_bytes(int G) {
-        unsigned b = 0;
-        for (int i = 0; i < H; ++i)
-            if (group_of(i) == G) b += full_bytes(j_at(H, i));
-        return b;
-    }
-    // bit j - 1 set: harmonic j reads another source row for top row o than
-    // for top row o - 1 (every bit for the first row of a walk)
-    template <int J>
-    __device__ __forceinline__ static unsigned changed(int o, bool first) {
-        if constexpr (J <= H) {
-            const unsigned own =
-                (first || src_off(H, o, J) != src_off(H, o - 1, J)) ? (1u << (J - 1)) : 0u;
-            return own | changed<J + 1>(o, first);
-        } else {
-            return 0u;
-        }
-    }
-    template <int IDX, int G>
-    __device__ __forceinline__ static unsigned changed_bytes(int64_t n_r, int64_t B, bool inside,
-                                                             unsigned chg) {
-        if constexpr (IDX < H) {
-            constexpr int J = j_at(H, IDX);
-            unsigned own = 0u;
-            if constexpr (group_of(IDX) == G)
-                if ((chg >> (J - 1)) & 1u) own = inside ? full_bytes(J) : span_bytes<J>(n_r, B);
-            return own + changed_bytes<IDX + 1, G>(n_r, B, inside, chg);
-        } else {
-            return 0u;
-        }
-    }
-    // one thread, per top row: arm each stage's barrier with the bytes of its
-    // changed spans and copy them (source row iz0 + o_j of the top row
-    // iz0 + o, from bin j B / H on) over the previous row's spans
+
+    // The span a lane of warp 0 copies: lane IDX takes harmonic j_at(H, IDX),
+    // on the barrier of its stage.  Set once per CTA from compile-time values;
+    // j = 0 for lanes without a span (and for the top row when it is held in
+    // registers).
+    struct Lane {
+        int j = 0, g = 0, off = 0;
+        unsigned full = 0;
+    };
     template <int IDX>
-    __device__ __forceinline__ static void copy(const real *__restrict__ plane, int iz0, int o,
-                                                int64_t n_r, int64_t B, bool inside, unsigned chg,
-                                                real *sm, uint64_t *bars) {
+    __device__ __forceinline__ static void lane_span(int lane, Lane &L) {
         if constexpr (IDX < H) {
-            constexpr int J = j_at(H, IDX);
-            constexpr int G = group_of(IDX);
+            constexpr int J = j_at(H, IDX), G = group_of(IDX), OFF = D::off(J);
+            constexpr unsigned FULL = full_bytes(J);
             constexpr bool kSkip = IDX == 0 && D::kTopRegs;
-            if constexpr (!kSkip && (IDX == 0 || (IDX & (IDX - 1)) == 0))
-                mbar_arrive_expect_tx(&bars[G], changed_bytes<0, G>(n_r, B, inside, chg));
-            if (!kSkip && ((chg >> (J - 1)) & 1u)) {
-                const unsigned bytes = inside ? full_bytes(J) : span_bytes<J>(n_r, B);
-                const int64_t row = iz0 + src_off(H, o, J);
-                if (bytes)
-                    bulk_copy_g2s(sm + D::off(J), plane + row * n_r + (int64_t)J * B / H, bytes,
-                                  &bars[G]);
+            if (!kSkip && lane == IDX) {
+                L.j = J;
+                L.g = G;
+                L.off = OFF;
+                L.full = FULL;
             }
-            copy<IDX + 1>(plane, iz0, o, n_r, B, inside, chg, sm, bars);
+            lane_span<IDX + 1>(lane, L);
         }
+    }
+    // per top row: the lane's span if its source row differs from the
+    // previous row's (every span for the first row of a walk), copied over
+    // the previous row's span with its bytes announced on its stage's
+    // barrier; the lanes of warp 0 issue their copies side by side, and one
+    // arrival per barrier follows
+    __device__ __forceinline__ static void copy_lane(const Lane &L, const real *__restrict__ plane,
+                                                     int iz0, int o, int64_t n_r, int64_t B,
+                                                     bool first, real *sm, uint64_t *bars) {
+        if (L.j == 0) return;
+        if (!first && src_off(H, o, L.j) == src_off(H, o - 1, L.j)) return;
+        // the span, but never past the last bin of the source row that a cell
+        // of the row reads (c0 and n_r are multiples of EPV, so the rounded
+        // end stays within the row)
+        const int64_t c0 = (int64_t)L.j * B / H;
+        const int64_t maxsrc = ((n_r - 1) * L.j + H / 2) / H;
+        int64_t n = maxsrc < c0 ? 0 : (maxsrc - c0 + 1 + D::EPV - 1) / D::EPV * D::EPV;
+        if (n * (int64_t)sizeof(real) > (int64_t)L.full) n = L.full / sizeof(real);
+        const unsigned bytes = (unsigned)(n * (int64_t)sizeof(real));
+        if (bytes == 0) return;
+        const int64_t row = iz0 + src_off(H, o, L.j);
+        fence_proxy_async_smem();
+        mbar_expect_tx(&bars[L.g], bytes);
+        bulk_copy_g2s(sm + L.off, plane + row * n_r + (int64_t)L.j * B / H, bytes, &bars[L.g]);
     }
 
     // 16 consecutive 16-bit cells (32 bytes, aligned) into 8 words
@@ -423,19 +406,31 @@ struct DedupSteps {
             constexpr int NVAL = D::dmax(J) + 1;
             constexpr int W = D::width(J);
             constexpr int NLD = (NVAL + W - 1) / W;
-            const real *p = sm + D::off(J) + (D::R / H) * J * t;
+            constexpr int OFF = D::off(J);
+            const real *p = sm + OFF + (D::R / H) * J * t;
             if constexpr (sizeof(real) == 2) {
                 // 16-bit values: keep them packed as loaded and add each to
                 // its cell with one mixed-precision add (no conversions)
                 if constexpr (W == 1) {
-                    unsigned short h[NLD];
+                    // odd start (odd j, H = 16, odd t): read the aligned words
+                    // that cover the window and shift them down by 16 bits
+                    // (one funnel shift per word), half as many shared-memory
+                    // loads as one per 16-bit value
+                    constexpr int NR = (NVAL + 1) / 2;          // words after the shift
+                    const int e0 = (D::R / H) * J * t;           // first element
+                    const uint32_t *pw =
+                        reinterpret_cast<const uint32_t *>(sm + OFF) + (e0 >> 1);
+                    uint32_t w[NR + 1];
 #pragma unroll
-                    for (int k = 0; k < NLD; ++k) h[k] = reinterpret_cast<const unsigned short *>(p)[k];
+                    for (int k = 0; k <= NR; ++k) w[k] = pw[k];
+                    const unsigned sh = (unsigned)(e0 & 1) * 16u;
+#pragma unroll
+                    for (int k = 0; k < NR; ++k) w[k] = __funnelshift_r(w[k], w[k + 1], sh);
 #pragma unroll
                     for (int i = 0; i < D::R; ++i) {
                         const int d = (i * J + H / 2) / H;
                         float &s = (i & 1) ? S2[i / 2].y : S2[i / 2].x;
-                        s = P::acc16(s, h[d]);
+                        s = (d & 1) ? P::acc_hi(s, w[d / 2]) : P::acc_lo(s, w[d / 2]);
                     }
                 } else {
                     constexpr int WPL = W / 2;                 // 32-bit words per load
@@ -472,7 +467,7 @@ struct DedupSteps {
 };
 
 template <class P, int H, bool kWriteSums>
-__global__ void __launch_bounds__(Dedup<P, H>::T, 6)
+__global__ void __launch_bounds__(Dedup<P, H>::T, 7)
     harmonic_dedup_kernel(const typename P::real *__restrict__ plane, int64_t n_r, int n_z,
                           int iz0, const TrialStats *__restrict__ st, uint32_t rank,
                           CandRec *__restrict__ cand, unsigned long long *__restrict__ count,
@@ -488,13 +483,14 @@ __global__ void __launch_bounds__(Dedup<P, H>::T, 6)
     const int t = threadIdx.x;
     const int iz_begin = blockIdx.y * D::QROWS;
     const int iz_end = min(iz_begin + D::QROWS, n_z);
-    const bool inside = B + D::CELLS <= n_r;
     if (t == 0) {
         for (int g = 0; g < Steps::NG; ++g) mbar_init(&bars[g], 1);
         mbar_fence_init();
     }
     const int64_t b = B + (int64_t)D::R * t;   // first cell of this thread
     const bool active = b < n_r;   // thread 0 always is
+    typename Steps::Lane lane_sp;
+    if (t < 32) Steps::template lane_span<0>(t, lane_sp);
     const float inv = 1.0f / P::plane_scale;
     bool failed = false;
     int q = 0;
@@ -509,12 +505,14 @@ __global__ void __launch_bounds__(Dedup<P, H>::T, 6)
             failed = true;
             break;
         }
-        if (t == 0) {
+        if (t < 32) {
             // the spans whose source row changed, over the previous row's
-            // (their reads by this CTA's threads come before the copies)
-            fence_proxy_async_smem();
-            const unsigned chg = Steps::template changed<1>(iz - iz0, q == 0);
-            Steps::template copy<0>(plane, iz0, iz - iz0, n_r, B, inside, chg, sm, bars);
+            // (their reads by this CTA's threads come before the copies),
+            // then one arrival per stage barrier (none on the unused barrier
+            // of a top row held in registers)
+            Steps::copy_lane(lane_sp, plane, iz0, iz - iz0, n_r, B, q == 0, sm, bars);
+            __syncwarp();
+            if (t < Steps::NG && !(t == 0 && D::kTopRegs)) mbar_arrive(&bars[t]);
         }
         if (!active) continue;
         float2 S2[D::R / 2];
@@ -567,7 +565,8 @@ __global__ void __launch_bounds__(Dedup<P, H>::T, 6)
         // copies still in flight must land before the CTA's shared memory
         // is released (each wait bounded): those of the last row issued
         if (t == 0 && q > 0)
-            for (int g = 0; g < Steps::NG; ++g) (void)mbar_wait(&bars[g], (unsigned)((q - 1) & 1));
+            for (int g = D::kTopRegs ? 1 : 0; g < Steps::NG; ++g)
+                (void)mbar_wait(&bars[g], (unsigned)((q - 1) & 1));
     }
 }
 
@@ -709,7 +708,7 @@ fdas_status launch_dedup(Plan &p, const void *plane, const TrialStats *st, uint3
     dim3 grid((unsigned)((p.n_r + D::CELLS - 1) / D::CELLS),
               (unsigned)((p.n_z + D::QROWS - 1) / D::QROWS));
     k<<<grid, D::T, smem, s>>>((const typename P::real *)plane, p.n_r, p.n_z, p.iz0, st, rank,
-                               p.cand, p.cand_count, p.max_cands, sums_out, p.flags);
+                               p.cand, p.cand_count, p.store_cap, sums_out, p.flags);
     FDAS_CUDA_TRY(cudaGetLastError());
     return FDAS_OK;
 }
@@ -731,14 +730,14 @@ fdas_status launch_hs(Plan &p, const void *plane, const TrialStats *st, uint32_t
                 pl, p.n_r, p.n_z, p.iz0, sums_out);
         else
             harmonic_threshold_kernel<P, H, (NCMAX >= 4 ? 4 : 2)><<<grid, kHsThreads, 0, s>>>(
-                pl, p.n_r, p.iz0, st, rank, p.cand, p.cand_count, p.max_cands);
+                pl, p.n_r, p.iz0, st, rank, p.cand, p.cand_count, p.store_cap);
     } else {
         if constexpr (kWriteSums)
             harmonic_sums_kernel<P, H, 2><<<grid, kHsThreads, 0, s>>>(pl, p.n_r, p.n_z, p.iz0,
                                                                      sums_out);
         else
             harmonic_threshold_kernel<P, H, 2><<<grid, kHsThreads, 0, s>>>(
-                pl, p.n_r, p.iz0, st, rank, p.cand, p.cand_count, p.max_cands);
+                pl, p.n_r, p.iz0, st, rank, p.cand, p.cand_count, p.store_cap);
     }
     FDAS_CUDA_TRY(cudaGetLastError());
     return FDAS_OK;
@@ -902,7 +901,7 @@ fdas_status launch_fund(Plan &p, const void *plane, const TrialStats *st, uint32
     dim3 grid((unsigned)((p.n_r + per_cta - 1) / per_cta), p.n_z);
     harmonic_fund_kernel<P, H, kWriteSums><<<grid, kFundThreads, 0, s>>>(
         (const typename P::real *)plane, p.n_r, p.n_z, p.iz0, st, rank, p.cand, p.cand_count,
-        p.max_cands, sums_out);
+        p.store_cap, sums_out);
     FDAS_CUDA_TRY(cudaGetLastError());
     return FDAS_OK;
 }

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <numeric>
@@ -24,6 +25,50 @@ fdas_status cuda_status(cudaError_t e, const char *what) {
 static fdas_status arg_error(const std::string &msg) {
     set_error(msg);
     return FDAS_ERR_ARG;
+}
+
+// ---------------------------------------------------------------------------
+// host-side fault injection: FDAS_FAULT = alloc[:N] | capacity | nan_input |
+// bad_args, read at every call (semantics in include/fdas.h).  Nothing is
+// injected on the device: each fault makes the host take the error path the
+// real failure would take.
+// ---------------------------------------------------------------------------
+enum { kFaultNone = 0, kFaultAlloc, kFaultCapacity, kFaultNan, kFaultArgs, kFaultUnknown };
+
+struct Fault {
+    int kind = kFaultNone;
+    int64_t n = 0;           // alloc: which allocation fails (1-based)
+    std::string text;
+};
+
+static Fault injected_fault() {
+    Fault f;
+    const char *s = std::getenv("FDAS_FAULT");
+    if (!s || !*s) return f;
+    f.text = s;
+    if (std::strncmp(s, "alloc", 5) == 0 && (s[5] == 0 || s[5] == ':')) {
+        f.kind = kFaultAlloc;
+        f.n = s[5] == ':' ? std::atoll(s + 6) : 1;
+        if (f.n < 1) f.kind = kFaultUnknown;
+    } else if (std::strcmp(s, "capacity") == 0) {
+        f.kind = kFaultCapacity;
+    } else if (std::strcmp(s, "nan_input") == 0) {
+        f.kind = kFaultNan;
+    } else if (std::strcmp(s, "bad_args") == 0) {
+        f.kind = kFaultArgs;
+    } else {
+        f.kind = kFaultUnknown;
+    }
+    return f;
+}
+
+// FDAS_ERR_ARG for the bad_args fault and for an unknown FDAS_FAULT value
+static fdas_status fault_args_check(const Fault &f) {
+    if (f.kind == kFaultArgs) return arg_error("injected fault (FDAS_FAULT=bad_args)");
+    if (f.kind == kFaultUnknown)
+        return arg_error("FDAS_FAULT=" + f.text +
+                         ": unknown fault (alloc[:N] with N >= 1, capacity, nan_input, bad_args)");
+    return FDAS_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -107,11 +152,22 @@ static void free_plan_memory(Plan *p) {
     if (p->host_small) cudaFreeHost(p->host_small);
     for (cudaEvent_t e : p->events) cudaEventDestroy(e);
     if (p->aux) cudaStreamDestroy(p->aux);
+    if (p->hi) cudaStreamDestroy(p->hi);
+    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+    if (p->ev_join) cudaEventDestroy(p->ev_join);
     if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
 }
 
 template <class T>
 static fdas_status dalloc(Plan &p, T **ptr, size_t bytes) {
+    ++p.n_allocs;
+    const Fault f = injected_fault();
+    if (f.kind == kFaultAlloc && p.n_allocs == f.n) {
+        *ptr = nullptr;
+        set_error("cudaMalloc(" + std::to_string(bytes) + " bytes): injected fault (FDAS_FAULT=" +
+                  f.text + ")");
+        return FDAS_ERR_OOM;
+    }
     cudaError_t e = cudaMalloc((void **)ptr, bytes);
     if (e != cudaSuccess) {
         *ptr = nullptr;
@@ -215,6 +271,7 @@ static Plan plan_view(const Plan &p, int64_t n) {
 
 static fdas_status create(Plan *&out, int64_t n_samples, double tsamp, double z_max, double z_step,
                           int32_t seg_len, int32_t n_harm, const fdas_opts *o) {
+    FDAS_TRY(fault_args_check(injected_fault()));
     if (!is_pow2(n_samples) || n_samples < (1 << 10) || n_samples > (1 << 24))
         return arg_error("n_samples must be a power of two in [2^10, 2^24]");
     if (!(tsamp > 0.0) || !std::isfinite(tsamp)) return arg_error("tsamp must be > 0");
@@ -275,6 +332,7 @@ static fdas_status create(Plan *&out, int64_t n_samples, double tsamp, double z_
     p.thr_mode = o->threshold_mode;
     p.sigma = o->threshold_sigma;
     p.max_cands = o->max_candidates;
+    p.store_cap = p.max_cands;
     p.harm_mode = o->harmonic_mode;
     p.interbin = o->interbin != 0;
     for (int s = 0; s < 6; ++s) p.G[s] = s < p.n_stages ? gamma_tail_factor(1 << s, p.sigma) : 0.0;
@@ -404,7 +462,19 @@ static fdas_status create(Plan *&out, int64_t n_samples, double tsamp, double z_
         PLAN_CUDA(cudaEventCreateWithFlags(&p.ev_consumed[b], cudaEventDisableTiming));
     }
     PLAN_CUDA(cudaMallocHost((void **)&p.host_small, 4 * sizeof(unsigned long long)));
-    PLAN_CUDA(cudaStreamCreateWithFlags(&p.aux, cudaStreamNonBlocking));
+    // the harmonic sum of one series runs on the lowest-priority stream
+    // beside the spectrum and correlation of the next on the highest: as the
+    // harmonic sum's CTAs retire, the block scheduler places the correlation's
+    // persistent CTAs first, and the harmonic CTAs fill what they leave of
+    // each SM, so the two kernels share the SMs instead of running in turn
+    {
+        int least = 0, greatest = 0;
+        PLAN_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        PLAN_CUDA(cudaStreamCreateWithPriority(&p.aux, cudaStreamNonBlocking, least));
+        PLAN_CUDA(cudaStreamCreateWithPriority(&p.hi, cudaStreamNonBlocking, greatest));
+        PLAN_CUDA(cudaEventCreateWithFlags(&p.ev_fork, cudaEventDisableTiming));
+        PLAN_CUDA(cudaEventCreateWithFlags(&p.ev_join, cudaEventDisableTiming));
+    }
 
     {
         const std::vector<float2> gl = gauss_legendre_01(refine_nodes());
@@ -459,7 +529,8 @@ static fdas_status collect(Plan &p, fdas_candidate *cands, int64_t capacity, int
                                   cudaMemcpyDeviceToHost, s));
     FDAS_CUDA_TRY(cudaStreamSynchronize(s));
     const int64_t total = (int64_t)p.host_small[0];
-    const unsigned int flags = (unsigned int)(p.host_small[1] & 0xffffffffu);
+    unsigned int flags = (unsigned int)(p.host_small[1] & 0xffffffffu);
+    if (injected_fault().kind == kFaultNan) flags |= 1u;
     if (flags & 2u) {
         *n_found = 0;
         set_error("a bounded wait for an asynchronous copy gave up");
@@ -470,7 +541,16 @@ static fdas_status collect(Plan &p, fdas_candidate *cands, int64_t capacity, int
         set_error("non-finite values in an input series");
         return FDAS_ERR_NONFINITE;
     }
-    const int64_t stored = std::min(total, p.max_cands);
+    if (total > p.store_cap) {
+        // the store kept the first store_cap crossings to arrive, which
+        // depend on scheduling: no subset of them is the ordered prefix
+        *n_found = total;
+        set_error("device candidate store full: " + std::to_string(total) +
+                  " crossings, store of " + std::to_string(p.store_cap) +
+                  " (raise max_candidates or the threshold)");
+        return FDAS_ERR_CAND_STORE_FULL;
+    }
+    const int64_t stored = total;
     FDAS_TRY(launch_candidates_finish(p, stored, p.out_stage, s));
     const int64_t n_copy = std::min(stored, capacity);
     if (n_copy > 0)
@@ -552,8 +632,17 @@ static fdas_status enqueue_batch(Plan &p, const fdas_series *batch, int32_t n_se
         return e;
     };
     // while tracing, every group runs on the caller's stream, so that each
-    // event interval holds the kernels of one group and nothing else
+    // event interval holds the kernels of one group and nothing else;
+    // otherwise the spectrum and correlation run on the plan's
+    // high-priority stream (after the work already queued on the caller's)
+    // and the harmonic sums on its low-priority one
     cudaStream_t hs = p.profiling ? s : p.aux;
+    cudaStream_t caller = s;
+    if (!p.profiling) {
+        FDAS_CUDA_TRY(cudaEventRecord(p.ev_fork, caller));
+        FDAS_CUDA_TRY(cudaStreamWaitEvent(p.hi, p.ev_fork, 0));
+        s = p.hi;
+    }
     // series in host memory are copied on their own stream into two
     // alternating staging buffers, so that the copy of the next series
     // overlaps the work on this one
@@ -641,8 +730,12 @@ static fdas_status enqueue_batch(Plan &p, const fdas_series *batch, int32_t n_se
             iv.push_back({FDAS_PROF_HARMONIC, e3, e4});
         }
     }
+    if (s != caller) {
+        FDAS_CUDA_TRY(cudaEventRecord(p.ev_join, s));
+        FDAS_CUDA_TRY(cudaStreamWaitEvent(caller, p.ev_join, 0));
+    }
     for (int b = 0; b < 2 && b < n_series; ++b)
-        FDAS_CUDA_TRY(cudaStreamWaitEvent(s, p.ev_hsum[(n_series - 1 - b) & 1], 0));
+        FDAS_CUDA_TRY(cudaStreamWaitEvent(caller, p.ev_hsum[(n_series - 1 - b) & 1], 0));
     return FDAS_OK;
 }
 
@@ -687,6 +780,8 @@ static fdas_status run_as_graph(Plan &p, const fdas_series *batch, int32_t n_ser
 static fdas_status search(Plan &p, const fdas_series *batch, int32_t n_series,
                           fdas_candidate *cands, int64_t capacity, int64_t *n_found,
                           cudaStream_t s) {
+    const Fault fault = injected_fault();
+    FDAS_TRY(fault_args_check(fault));
     if (n_series < 0) return arg_error("n_series < 0");
     if (n_series > (1 << 22)) return arg_error("n_series > 2^22");
     if (n_series > 0 && batch == nullptr) return arg_error("batch is NULL");
@@ -706,6 +801,7 @@ static fdas_status search(Plan &p, const fdas_series *batch, int32_t n_series,
     }
     *n_found = 0;
     DeviceGuard guard(p.device);
+    p.store_cap = fault.kind == kFaultCapacity ? 1 : p.max_cands;
     FDAS_TRY(grow_stats(p, std::max<int64_t>(1, n_series)));
     // rank = position in trial_id order (stable), so the output order is
     // (trial_id, stage, iz, ir)
@@ -1004,6 +1100,9 @@ fdas_status fdas_threshold(fdas_plan *plan, const void *plane, const double *sta
     DeviceGuard guard(p.device);
     cudaStream_t s = (cudaStream_t)stream;
     *n_found = 0;
+    const Fault fault = injected_fault();
+    if (fault.kind == kFaultUnknown) return fault_args_check(fault);
+    p.store_cap = fault.kind == kFaultCapacity ? 1 : p.max_cands;
     FDAS_CUDA_TRY(cudaMemcpyAsync(p.rank_ids, &trial_id, sizeof(uint32_t), cudaMemcpyHostToDevice, s));
     FDAS_CUDA_TRY(cudaMemsetAsync(p.cand_count, 0, sizeof(unsigned long long), s));
     FDAS_CUDA_TRY(cudaMemsetAsync(p.flags, 0, sizeof(unsigned int), s));

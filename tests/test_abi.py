@@ -155,3 +155,35 @@ def test_binding_constants_match_the_header(capi):
             assert getattr(capi, name) == int(val), (name, getattr(capi, name), val)
             found += 1
     assert found >= 20
+
+
+def test_fault_injection_reaches_argument_checks_without_a_gpu(capi, monkeypatch):
+    """FDAS_FAULT=bad_args makes fdas_plan_create refuse valid arguments
+    before any CUDA call; an unknown FDAS_FAULT value is refused by name."""
+    good = (1 << 17, 64e-6, 16.0, 2.0, 2048, 4)
+    monkeypatch.setenv("FDAS_FAULT", "bad_args")
+    with pytest.raises(capi.FdasError) as ei:
+        capi.fdas_plan_create(*good)
+    assert ei.value.status == capi.FDAS_ERR_ARG and "injected" in str(ei.value)
+    for bad in ("alloc:0", "allocate", "nonsense"):
+        monkeypatch.setenv("FDAS_FAULT", bad)
+        with pytest.raises(capi.FdasError) as ei:
+            capi.fdas_plan_create(*good)
+        assert ei.value.status == capi.FDAS_ERR_ARG and bad in str(ei.value)
+    # a plan that passes validation then needs the device (none here)
+    monkeypatch.setenv("FDAS_FAULT", "")
+    try:
+        import torch
+        have_gpu = torch.cuda.is_available()
+    except Exception:
+        have_gpu = False
+    if not have_gpu:
+        with pytest.raises(capi.FdasError) as ei:
+            capi.fdas_plan_create(*good)
+        assert ei.value.status == capi.FDAS_ERR_CUDA
+
+
+def test_store_full_status_is_returned_not_raised(capi):
+    assert capi.FDAS_ERR_CAND_STORE_FULL == 8
+    assert capi.FDAS_ERR_CAND_STORE_FULL in capi.COUNT_STATUSES
+    assert capi.STATUS_NAMES[8] == "FDAS_ERR_CAND_STORE_FULL"

@@ -203,13 +203,14 @@ def test_fullsize_interbin_cells_and_candidates(capi):
     assert np.all(err < tol), (err.max(), iz[np.argmax(err)], col[np.argmax(err)])
     assert 0.9 < mean < 1.4
     del plane
-    # candidates of a two-series search, each recomputed from oracle cells
+    # every candidate of a two-series search, each recomputed from oracle
+    # cells: the detection strength stays within the paper's 3% (measured on
+    # this case: at most 0.54%)
     st, cands, nf = plan.search(xs, capacity=1 << 20)
     assert st == capi.FDAS_OK and nf == len(cands)
     for t, x in enumerate(xs):
         c = cands[cands["trial_id"] == t]
         assert len(c) > 0
-        c = c[np.argsort(-c["sigma"])][:300]           # the strongest ones
         Xn, _ = O.normalise(O.spectrum(x.cpu().numpy()), 2048)
         cells, owners = [], []
         for n, (h, izc, ir) in enumerate(zip(c["harm"], c["iz"], c["ir"])):
@@ -220,5 +221,5 @@ def test_fullsize_interbin_cells_and_candidates(capi):
         pw = O.half_bin_cells(Xn, bank, cells[:, 0], cells[:, 1])
         s_ora = np.bincount(np.array(owners), weights=pw, minlength=len(c))
         rel = np.abs(c["power"] / s_ora - 1)
-        assert rel.max() <= 0.06, (t, rel.max())
+        assert rel.max() <= 0.03, (t, rel.max())
     plan.close()

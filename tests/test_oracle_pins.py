@@ -406,6 +406,64 @@ def _rho0(q):
     return out
 
 
+def test_cell_powers_and_correlations_equal_the_plane_and_a_direct_sum():
+    """The one-cell routes the full-size tests check the GPU with: P at random
+    cells (every z, both edges of the spectrum) equals the whole-plane direct
+    correlation at those cells and a plain numpy sum written out here from
+    the definition F(r, z) = sum_e X'_{r-e} g_z[e] (X'_k = 0 outside
+    [0, N_r)), so an iz/r swap, a dtype slip or a tap offset in their
+    marshalling fails."""
+    g = O.geometry(1 << 12, 10.0, 1.0, 4)
+    Xn, _ = O.normalise(O.spectrum(S.white_noise(g.n_samples, 21)), 512)
+    bank = O.template_bank(g)
+    P = O.power_plane(Xn, bank)
+    F = O.correlation_plane(Xn, bank)
+    rng = np.random.default_rng(5)
+    iz = rng.integers(0, g.n_z, 400)
+    r = rng.integers(0, g.n_r, 400)
+    iz[:g.n_z] = np.arange(g.n_z)          # every template at least once
+    r[:4] = [0, 1, g.n_r - 2, g.n_r - 1]   # windows cut by both edges
+    v = O.cell_powers(Xn, bank, iz, r)
+    assert np.max(np.abs(v - P[iz, r]) / np.maximum(P[iz, r], 1e-3)) < 1e-12
+    c = O.cell_correlations(Xn, bank, iz, r)
+    assert np.max(np.abs(c - F[iz, r])) < 1e-12 * max(1.0, np.max(np.abs(F)))
+    for c in range(60):
+        a, b = int(iz[c]), int(r[c])
+        m = int(g.m[a])
+        s = 0j
+        for e in range(-m, m + 1):
+            if 0 <= b - e < g.n_r:
+                s += Xn[b - e] * bank.taps[a][e + m]
+        assert abs(abs(s) ** 2 - v[c]) < 1e-11 * max(1.0, abs(s) ** 2)
+
+
+def test_harmonic_at_equals_the_stage_planes_and_brute_force():
+    """The per-cell harmonic sums used by the full-size checks: every stage at
+    random cells (both z edges, r edges) equals the whole-plane sums and a
+    sum over harmonic_indices written out here."""
+    g = O.geometry(1 << 11, 12.0, 1.0, 16)
+    rng = np.random.default_rng(8)
+    P = rng.exponential(size=(g.n_z, g.n_r))
+    Sp = O.harmonic_planes(P, g)
+    n = 500
+    st = rng.integers(0, len(g.stages), n)
+    iz = rng.integers(0, g.n_z, n)
+    ir = rng.integers(0, g.n_r, n)
+    iz[:4] = [0, g.n_z - 1, g.iz0, g.iz0 - 1]
+    ir[:4] = [g.n_r - 1, 0, g.n_r - 1, 1]
+    st[:4] = len(g.stages) - 1
+    v = O.harmonic_at(P, g, st, iz, ir)
+    assert np.max(np.abs(v - Sp[st, iz, ir])) < 1e-12 * np.max(Sp)
+    for c in range(100):
+        h = g.stages[st[c]]
+        s = 0.0
+        for k in range(1, h + 1):
+            siz, sir = O.harmonic_indices(int(ir[c]), int(iz[c]), g.iz0, g.n_harm,
+                                          k * (g.n_harm // h))
+            s += P[siz, sir]
+        assert abs(v[c] - s) < 1e-12 * s
+
+
 def test_correlation_plane_squared_is_the_power_plane():
     g = _small_geom()
     Xn, _ = O.normalise(O.spectrum(S.white_noise(g.n_samples, 5)), 512)
