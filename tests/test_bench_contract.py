@@ -29,3 +29,10 @@ def test_reference_arm_json_line():
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+    # what a step measured: one bounded sample per step, its wall time as
+    # ms_per_step, and the fraction of a trial it stands for, consistent
+    # with the throughput
+    assert 0 < d["trials_per_step"] < 1
+    assert abs(d["trials_per_step"] / (d["ms_per_step"] / 1000.0) / d["value"] - 1) < 1e-9
+    assert d["steps"] * d["ms_per_step"] / 1000.0 <= d["wall_s"] * 1.01
+    assert "series_per_step" not in d["config"] and "precision" not in d["config"]
