@@ -18,8 +18,8 @@
 // phases p live in the template operand instead (B columns shifted by p taps),
 // so one accumulator row holds four consecutive bins of every template.
 //
-// One persistent CTA per SM takes a weighted contiguous run of (chunk, tile)
-// items.  Warp 0 (one thread) bulk-copies the chunk's template image (B, up to
+// One persistent CTA per SM takes, for every chunk in turn, every G-th tile
+// (G = the number of CTAs).  Warp 0 (one thread) bulk-copies the chunk's template image (B, up to
 // 208 KB, once per chunk) and the spectrum windows (A, a ring of 4) into shared
 // memory; warp 1 (one thread) issues the tcgen05 MMAs (M = 128, N = 224, K = 16
 // each, BF16 or FP16 operands, FP32 accumulators) into one of two TMEM
@@ -67,42 +67,32 @@ static_assert(kTcZ % (kTcEpiWarps / 4) == 0, "epilogue split");
 constexpr int kTcThreads = 32 * (2 + kTcEpiWarps);
 constexpr int kTcTmemCols = 512;
 constexpr int kTcAccStride = 256;                // TMEM column of accumulator 1
-constexpr int kTcEpiSteps = 11;                  // epilogue time of a tile, in MMA K steps
 constexpr size_t kTcMinSmem = 120 * 1024;        // keeps one CTA (and one TMEM owner) per SM
 constexpr int kTcCtasPerSm = 1;                  // persistent CTAs per SM
 
-// The (chunk, tile) items of CTA k of G: items are ordered chunk-major with
-// weight max(ks, kTcEpiSteps) each (the MMAs of a tile overlap the epilogue
-// of the previous one, so a tile costs the longer of the two), and CTA k
-// takes those whose starting weight falls in [k W / G, (k + 1) W / G).
+// The (chunk, tile) items of CTA k of G: for every chunk in turn, the tiles
+// k, k + G, k + 2G, ...  Every CTA gets the same mix of chunks (the tile
+// counts per chunk differ by at most one between CTAs), so the CTAs finish
+// together whatever a chunk's cost, and at any time the G CTAs work on G
+// adjacent tiles of one chunk (the spectrum windows and the plane rows they
+// touch are contiguous).  Producer, MMA thread and epilogue walk the same
+// sequence.
 struct TcSchedule {
-    const TcChunk *ch;
-    int n_ch;
-    int64_t n_tiles, lo, hi, base, t;
-    int c;
-    __device__ TcSchedule(const TcChunk *chunks, int n_ch_, int64_t n_tiles_, int k, int G)
-        : ch(chunks), n_ch(n_ch_), n_tiles(n_tiles_), base(0), t(-1), c(0) {
-        int64_t w = 0;
-        for (int i = 0; i < n_ch; ++i) w += max(chunks[i].ks, kTcEpiSteps);
-        const int64_t total = w * n_tiles;
-        lo = total * k / G;
-        hi = total * (k + 1) / G;
-    }
+    int n_ch, c, k, G;
+    int64_t n_tiles, t;
+    __device__ TcSchedule(const TcChunk *, int n_ch_, int64_t n_tiles_, int k_, int G_)
+        : n_ch(n_ch_), c(0), k(k_), G(G_), n_tiles(n_tiles_), t(k_) {}
     __device__ bool next(int &oc, int64_t &ot) {
         while (c < n_ch) {
-            const int64_t w = max(ch[c].ks, kTcEpiSteps);
-            if (base >= hi) break;
-            if (t < 0) t = lo > base ? (lo - base + w - 1) / w : 0;
-            if (t < n_tiles && base + t * w < hi) {
+            if (t < n_tiles) {
                 oc = c;
-                ot = t++;
+                ot = t;
+                t += G;
                 return true;
             }
-            base += n_tiles * w;
             ++c;
-            t = -1;
+            t = k;
         }
-        c = n_ch;
         return false;
     }
 };
@@ -128,16 +118,20 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         const TcChunk *__restrict__ chunks, int n_ch,
                         const float *__restrict__ inv_energy,
                         void *__restrict__ out, double2 *__restrict__ partials,
-                        int64_t n_r, int win_bytes, int b_bytes_max, unsigned int *flags,
+                        int64_t n_r, int win_bytes, int b_bytes_max, int nbuf,
+                        unsigned int *flags,
                         float4 *__restrict__ edges) {
     constexpr bool kSplit = P::id == FDAS_FP32;
     constexpr int kStages = kSplit ? 2 : kTcStages;
     constexpr int kParts = kSplit ? 2 : 1;   // hi (+ lo) operand images
     extern __shared__ __align__(128) unsigned char tc_smem[];
+    // nbuf (1 or 2) template images, then the spectrum-window ring; with two
+    // images the next chunk's is copied while the MMAs of the current one run
     unsigned char *const sB = tc_smem;
-    unsigned char *const sA = tc_smem + kParts * b_bytes_max;
+    const int b_stride = kParts * b_bytes_max;
+    unsigned char *const sA = tc_smem + nbuf * b_stride;
     __shared__ __align__(8) uint64_t a_full[kTcStages], a_empty[kTcStages];
-    __shared__ __align__(8) uint64_t b_full, b_empty, acc_full[2], acc_empty[2], drain;
+    __shared__ __align__(8) uint64_t b_full[2], b_empty[2], acc_full[2], acc_empty[2], drain;
     __shared__ uint32_t tmem_base_sh;
     __shared__ double red[2][kTcEpiWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -150,8 +144,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             mbar_init(&a_full[i], 1);
             mbar_init(&a_empty[i], 1);
         }
-        mbar_init(&b_full, 1);
-        mbar_init(&b_empty, 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&b_full[i], 1);
+            mbar_init(&b_empty[i], 1);
+        }
         for (int i = 0; i < 2; ++i) {
             mbar_init(&acc_full[i], 1);
             mbar_init(&acc_empty[i], kTcEpiWarps);
@@ -180,16 +176,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             while (sch.next(c, t)) {
                 if (c != cur) {
                     ++run;
-                    if (run > 0 && !mbar_wait(&b_empty, (run - 1) & 1)) {
+                    const int bb = run % nbuf;
+                    // the image buffer is free once the MMAs of run - nbuf completed
+                    if (run >= nbuf && !mbar_wait(&b_empty[bb], ((run / nbuf) - 1) & 1)) {
                         ok = false;
                         break;
                     }
                     const unsigned bytes = (unsigned)chunks[c].ks * kTcSlab;
-                    mbar_arrive_expect_tx(&b_full, kParts * bytes);
-                    bulk_copy_g2s(sB, bank_img + chunks[c].b_off, bytes, &b_full);
+                    unsigned char *const dstB = sB + bb * b_stride;
+                    mbar_arrive_expect_tx(&b_full[bb], kParts * bytes);
+                    bulk_copy_g2s(dstB, bank_img + chunks[c].b_off, bytes, &b_full[bb]);
                     if constexpr (kSplit)
-                        bulk_copy_g2s(sB + b_bytes_max, bank_img + b_lo + chunks[c].b_off, bytes,
-                                      &b_full);
+                        bulk_copy_g2s(dstB + b_bytes_max, bank_img + b_lo + chunks[c].b_off, bytes,
+                                      &b_full[bb]);
                     cur = c;
                 }
                 const int s = j % kStages;
@@ -211,7 +210,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 const int uses = (j - 1 - s) / kStages + 1;
                 (void)mbar_wait(&a_full[s], (uses - 1) & 1);
             }
-            if (run >= 0) (void)mbar_wait(&b_full, run & 1);
+            for (int r = run - nbuf + 1; r <= run; ++r)
+                if (r >= 0) (void)mbar_wait(&b_full[r % nbuf], (r / nbuf) & 1);
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -220,14 +220,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             int c, cur = -1, run = -1, ks = 0, kofs = 0;
             int64_t t;
             int j = 0;
-            const uint64_t bdesc0 = smem_desc(smem_u32(sB), 128, 256);
-            const uint64_t bdesc_lo = smem_desc(smem_u32(sB + (kSplit ? b_bytes_max : 0)), 128, 256);
+            uint64_t bdesc0 = 0, bdesc_lo = 0;
             while (sch.next(c, t)) {
                 if (c != cur) {
-                    if (cur >= 0) tc_commit(&b_empty);   // the old template image is free
+                    if (cur >= 0) tc_commit(&b_empty[run % nbuf]);   // the old image is free
                     ++run;
                     cur = c;
-                    if (!mbar_wait(&b_full, run & 1)) {
+                    const unsigned char *const img = sB + (run % nbuf) * b_stride;
+                    bdesc0 = smem_desc(smem_u32(img), 128, 256);
+                    bdesc_lo = smem_desc(smem_u32(img + (kSplit ? b_bytes_max : 0)), 128, 256);
+                    if (!mbar_wait(&b_full[run % nbuf], (run / nbuf) & 1)) {
                         ok = false;
                         break;
                     }
@@ -608,9 +610,9 @@ __global__ void tc_split_kernel(const float2 *__restrict__ x, __nv_bfloat162 *__
     }
 }
 
-size_t tc_smem_bytes(int max_ks, int win, bool split) {
+size_t tc_smem_bytes(int max_ks, int win, bool split, int nbuf) {
     const size_t parts = split ? 2 : 1, stages = split ? 2 : kTcStages;
-    const size_t need = parts * ((size_t)max_ks * kTcSlab + stages * (size_t)win * 4);
+    const size_t need = parts * ((size_t)nbuf * max_ks * kTcSlab + stages * (size_t)win * 4);
     return std::max(need, kTcMinSmem);
 }
 
@@ -618,7 +620,7 @@ template <class P, int kMode>
 fdas_status launch_tc_P(Plan &p, const void *spec_padded, void *plane, double2 *partials,
                         cudaStream_t s) {
     constexpr bool kSplit = P::id == FDAS_FP32;
-    const size_t smem = tc_smem_bytes(p.tc_max_ks, p.tc_win, kSplit);
+    const size_t smem = tc_smem_bytes(p.tc_max_ks, p.tc_win, kSplit, p.tc_nbuf);
     auto k = correlate_tc_kernel<P, kMode>;
     FDAS_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = correlate_tc_ctas(p);
@@ -639,7 +641,7 @@ fdas_status launch_tc_P(Plan &p, const void *spec_padded, void *plane, double2 *
                                       p.tc_n_ch,
                                       p.tc_inv_energy, plane, partials, p.n_r,
                                       p.tc_win * 4,
-                                      p.tc_max_ks * kTcSlab, p.flags, p.tc_edges);
+                                      p.tc_max_ks * kTcSlab, p.tc_nbuf, p.flags, p.tc_edges);
     FDAS_CUDA_TRY(cudaGetLastError());
     if constexpr (kMode == kInterbin) {
         tc_ib_fixup_kernel<P><<<tc_ib_fixup_ctas(p), 256, 0, s>>>(
@@ -693,11 +695,25 @@ bool tc_applicable(const Plan &p, std::string *why) {
         cudaGetLastError();
         optin = 0;
     }
-    if (tc_smem_bytes(p.tc_max_ks, p.tc_win, p.tc_split) + 1024 > (size_t)optin) {
+    if (tc_smem_bytes(p.tc_max_ks, p.tc_win, p.tc_split, 1) + 1024 > (size_t)optin) {
         if (why) *why = "the widest template chunk does not fit in shared memory (z_max too large)";
         return false;
     }
     return true;
+}
+
+// template-image buffers of the tensor-core correlation: two where both fit
+// beside the window ring (the next chunk's image then loads while the
+// current one is in use), else one
+int tc_image_buffers(const Plan &p) {
+    if (p.tc_split) return 1;
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return tc_smem_bytes(p.tc_max_ks, p.tc_win, false, 2) + 1024 <= (size_t)optin ? 2 : 1;
 }
 
 int correlate_tc_ctas(const Plan &p) {

@@ -179,6 +179,7 @@ struct Plan {
     void *spec_hi = nullptr, *spec_lo = nullptr;
     int64_t tc_split_elems = 0;
     int tc_n_ch = 0, tc_max_ks = 0, tc_win = 0;
+    int tc_nbuf = 1;                  // template-image buffers in shared memory (1 or 2)
     // FFT split of the N/2-point complex FFT in the spectrum stage
     int fft_m1, fft_m2;     // M = m1 * m2 (m1 = 1: single pass)
     // device memory
@@ -240,6 +241,7 @@ int correlate_ctas(const Plan &p);
 // tensor-core correlation: whether it applies to the plan's geometry, the
 // host-side chunk table, the operand images (from the FP64 taps) and launch
 bool tc_applicable(const Plan &p, std::string *why);
+int tc_image_buffers(const Plan &p);
 std::vector<TcChunk> tc_chunk_table(const Plan &p, const std::vector<int32_t> &m, int *win,
                                     int *max_ks);
 fdas_status launch_tc_bank(Plan &p, cudaStream_t s);

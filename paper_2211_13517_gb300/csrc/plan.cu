@@ -403,6 +403,8 @@ static fdas_status create(Plan *&out, int64_t n_samples, double tsamp, double z_
         if (p.correlator != FDAS_CORR_TENSOR) {
             tc_table.clear();
             p.tc_n_ch = 0;
+        } else {
+            p.tc_nbuf = tc_image_buffers(p);
         }
     }
 
