@@ -88,6 +88,42 @@ def test_spectrum_matches_oracle(capi, n):
     plan.close()
 
 
+@pytest.mark.parametrize("block", [16, 128, 2048, 8192])
+def test_block_medians_at_every_block_size(capi, block):
+    # exact middle order statistics of every block: odd counts (block 0 has
+    # no k = 0), crowded and sparse first-digit bins over 2048 blocks of 16
+    n = 1 << 16
+    x = S.white_noise(n, 11)
+    plan = _plan(capi, n, 4.0, 1.0, 1024, 2, norm_block=block)
+    spec, med = plan.spectrum(torch.from_numpy(x).cuda(), medians=True)
+    _, meds = O.normalise(O.spectrum(x), block)
+    assert med.shape[0] == meds.shape[0] == (n // 2) // block
+    assert np.max(np.abs(med.cpu().numpy() / meds - 1)) < 2e-5
+    plan.close()
+
+
+@pytest.mark.parametrize("shift", [0, 1])
+def test_block_medians_of_equal_powers(capi, shift):
+    # an impulse: every |X_k|^2 is 1, exactly (shift 0: Z_k = 1) or up to
+    # rounding of |W^k|^2 (shift 1: X_k = W_N^k), so each block's keys share
+    # one first-digit bin and the selection takes its radix passes
+    n = 1 << 15
+    x = np.zeros(n, np.float32)
+    x[shift] = 1.0
+    plan = _plan(capi, n, 4.0, 1.0, 1024, 2)
+    spec, med = plan.spectrum(torch.from_numpy(x).cuda(), medians=True)
+    m = med.cpu().numpy()
+    if shift == 0:
+        assert np.all(m == 1.0)
+        got = _cplx(spec)
+        ref = np.full(n // 2, math.sqrt(math.log(2.0)), np.complex128)
+        ref[0] = 0.0
+        assert np.max(np.abs(got - ref)) < 1e-6
+    else:
+        assert np.max(np.abs(m - 1.0)) < 1e-6
+    plan.close()
+
+
 def test_spectrum_without_normalisation(capi):
     n = 1 << 16
     x = S.white_noise(n, 5)
