@@ -430,6 +430,10 @@ def run_gpu(args, rank, world, local_rank, dist):
     _, prof_bf16, _, _, _ = timed(plan, xs, 1, 1, True)
     # --- e2e: the same calls with the series in pinned host memory ----------
     hosts = [x.cpu().pin_memory() for x in xs]
+    # the copy rate of these pinned buffers by themselves (torch copies, no
+    # library call): the e2e leg needs about 4 N bytes per series at the
+    # device rate, and this rate depends on how the host backs the pages
+    host_copy_gbs = pinned_copy_gbs(torch, hosts, xs[0])
     for _ in range(max(1, args.warmup // 2)):
         plan.search(hosts, trial_ids=ids, capacity=1 << 16)
     clocks_e2e = ClockSampler(local_rank)
@@ -656,6 +660,7 @@ def run_gpu(args, rank, world, local_rank, dist):
         "e2e_ms_per_step": ms_e2e / args.steps,
         "e2e_h2d_gbs": 4 * N_SAMPLES * args.batch / (ms_e2e / args.steps / 1000.0) / 1e9,
         "e2e_over_value": (trials / (ms_e2e / 1000.0)) / value,
+        "e2e_host_copy_gbs": host_copy_gbs,
         "gpu_launches": launches,
         "clocks": ck,
         "joules_per_trial": jstats(j_bf16, args.batch),
@@ -873,6 +878,20 @@ def run_uneven(args, dev, capi, S, timed_uneven):
             "note": "the paper's 5925 DM trials (3050 at full resolution, the rest decimated by "
                     "2, 4 and 8) as one fdas_search call per step, its launches captured and "
                     "replayed as one CUDA graph"}
+
+
+def pinned_copy_gbs(torch, hosts, dst):
+    """Host-to-device rate (GB/s) of one pass of plain copies of the pinned
+    host tensors `hosts` into the device tensor `dst` on a side stream."""
+    s = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(s):
+        for h in hosts:
+            dst.copy_(h, non_blocking=True)
+    s.synchronize()
+    dt = time.perf_counter() - t0
+    return sum(h.numel() * h.element_size() for h in hosts) / dt / 1e9
 
 
 def l2_copy_gbs(torch, dev, mib=32, reps=200):
