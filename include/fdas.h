@@ -207,7 +207,8 @@ fdas_status fdas_plan_get_info(const fdas_plan *plan, fdas_plan_info *info);
  * threshold_sigma*sqrt(h)*std (MEAN_PLUS_KSIGMA), with mean/std of the
  * series' own plane.  sigma = Phibar^-1(Q(h, S/mean)) or
  * (S - h mean)/(sqrt(h) std).
- * Blocking: returns after the results are in `cands`.
+ * Blocking: returns after the results are in `cands` (fdas_search_async
+ * below is the stream-ordered form).
  * Errors: FDAS_ERR_ARG; FDAS_ERR_NONFINITE (a series holds NaN/Inf: no
  * candidates are returned); FDAS_ERR_CAND_OVERFLOW (more crossings than
  * `capacity` but no more than the plan's max_candidates: *n_found is the true
@@ -221,6 +222,43 @@ fdas_status fdas_plan_get_info(const fdas_plan *plan, fdas_plan_info *info);
 fdas_status fdas_search(fdas_plan *plan, const fdas_series *batch,
                         int32_t n_series, fdas_candidate *cands,
                         int64_t capacity, int64_t *n_found, void *stream);
+
+/*
+ * The same search, stream-ordered: every step is queued on `stream` and
+ * the call returns without waiting for the device; the caller synchronises
+ * the stream (or waits on an event recorded after the call) before reading
+ * the results.  It computes what fdas_search computes (same candidates,
+ * same order, same statuses), with the count and the status decided on the
+ * device:
+ *   cands:   device memory or page-locked host memory for `capacity`
+ *            entries (written by the device directly);
+ *   n_found: device or page-locked host int64, receives the total number
+ *            of crossings (0 after a NONFINITE or TIMEOUT status);
+ *   status:  device or page-locked host int32, receives the fdas_status
+ *            fdas_search would have returned for this batch (FDAS_OK,
+ *            FDAS_ERR_CAND_OVERFLOW, FDAS_ERR_CAND_STORE_FULL,
+ *            FDAS_ERR_NONFINITE or FDAS_ERR_TIMEOUT, with the same meaning
+ *            for `cands` and `n_found`).
+ * The series may be in device or host memory as for fdas_search; a series
+ * in pageable host memory makes its copy, and so the call, wait for it.
+ * The series and the three outputs must stay valid until the stream has
+ * completed the search (`batch`, the descriptor array, is read during the
+ * call only).
+ * The return value covers only what the host can check at the call:
+ * FDAS_OK (everything queued), FDAS_ERR_ARG (also: cands, n_found or status
+ * in pageable memory, or tracing enabled with fdas_profile_enable), or
+ * FDAS_ERR_CUDA (a launch failed).
+ * The candidates are ordered on the device without knowing their number on
+ * the host, so the sort network is queued for up to the plan's
+ * max_candidates records and its unused steps return at once (about 40
+ * launches for max_candidates = 2^20).
+ * The plan's buffers are reused by the next search: calls on one plan must
+ * be ordered by the caller (one stream, or a synchronisation in between).
+ */
+fdas_status fdas_search_async(fdas_plan *plan, const fdas_series *batch,
+                              int32_t n_series, fdas_candidate *cands,
+                              int64_t capacity, int64_t *n_found,
+                              int32_t *status, void *stream);
 
 /* ---------------------------------------------------------------------
  * Candidate refinement with the Fourier-interpolated power.

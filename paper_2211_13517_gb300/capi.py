@@ -44,7 +44,8 @@ FDAS_CORR_AUTO, FDAS_CORR_FFT, FDAS_CORR_TENSOR, FDAS_CORR_TENSOR_SPLIT = 0, 1, 
 FDAS_HARM_TOP, FDAS_HARM_FUNDAMENTAL = 0, 1
 
 EXPORTED = ["fdas_opts_default", "fdas_plan_create", "fdas_plan_destroy",
-            "fdas_plan_get_info", "fdas_search", "fdas_spectrum", "fdas_power_plane",
+            "fdas_plan_get_info", "fdas_search", "fdas_search_async", "fdas_spectrum",
+            "fdas_power_plane",
             "fdas_correlation_plane",
             "fdas_harmonic_sums", "fdas_threshold", "fdas_template_bank",
             "fdas_spectrum_static", "fdas_fourier_power", "fdas_fourier_power_backward",
@@ -166,6 +167,9 @@ def lib() -> ctypes.CDLL:
         L.fdas_search.argtypes = [c_void_p, POINTER(fdas_series), c_int32, c_void_p, c_int64,
                                   POINTER(c_int64), c_void_p]
         L.fdas_search.restype = c_int32
+        L.fdas_search_async.argtypes = [c_void_p, POINTER(fdas_series), c_int32, c_void_p, c_int64,
+                                        c_void_p, c_void_p, c_void_p]
+        L.fdas_search_async.restype = c_int32
         L.fdas_spectrum.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
         L.fdas_spectrum.restype = c_int32
         L.fdas_power_plane.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
@@ -275,6 +279,14 @@ def fdas_search(plan, batch, n_series, cands_ptr, capacity, stream=None):
     st = lib().fdas_search(plan, batch, n_series, cands_ptr, capacity, ctypes.byref(n), stream)
     _check(st, "fdas_search", allow=COUNT_STATUSES)
     return st, n.value
+
+
+def fdas_search_async(plan, batch, n_series, cands_ptr, capacity, n_found_ptr, status_ptr,
+                      stream=None):
+    """Queues the search on `stream`; *n_found_ptr and *status_ptr (device or
+    page-locked host) receive the results when the stream reaches them."""
+    _check(lib().fdas_search_async(plan, batch, n_series, cands_ptr, capacity, n_found_ptr,
+                                   status_ptr, stream), "fdas_search_async")
 
 
 def fdas_spectrum(plan, series_ptr, spectrum_ptr, medians_ptr=None, stream=None):
@@ -426,6 +438,33 @@ class Plan:
                              _stream_ptr(stream))
         k = 0 if st == FDAS_ERR_CAND_STORE_FULL else min(nf, out.shape[0])
         return st, out[:k], nf
+
+    def search_async(self, series, cands, n_found, status, trial_ids=None, stream=None):
+        """Stream-ordered search.  cands: uint8 tensor of capacity x 20 bytes
+        (device or pinned host); n_found: int64 tensor of 1, status: int32
+        tensor of 1 (device or pinned host).  Returns at once; after the
+        stream is synchronised, cands holds the first min(n_found, capacity)
+        records (none with FDAS_ERR_CAND_STORE_FULL) and status the code
+        fdas_search would have returned.  The series and the output tensors
+        must stay alive until then."""
+        n = len(series)
+        batch = (fdas_series * max(n, 1))()
+        for i, x in enumerate(series):
+            batch[i].data = x.data_ptr()
+            batch[i].n_samples = x.numel()
+            batch[i].decimation = 1
+            batch[i].trial_id = i if trial_ids is None else int(trial_ids[i])
+        capacity = cands.numel() // CANDIDATE_DTYPE.itemsize
+        fdas_search_async(self.handle, batch, n, c_void_p(cands.data_ptr()), capacity,
+                          c_void_p(n_found.data_ptr()), c_void_p(status.data_ptr()),
+                          _stream_ptr(stream))
+
+    @staticmethod
+    def candidates(cands, n):
+        """The first n records of a candidate buffer (a tensor of bytes) as a
+        numpy structured array."""
+        raw = cands[:n * CANDIDATE_DTYPE.itemsize].cpu().numpy()
+        return raw.view(CANDIDATE_DTYPE)
 
     def profile(self, on=None):
         """Enable/disable tracing (resetting it) or, with no argument, read it

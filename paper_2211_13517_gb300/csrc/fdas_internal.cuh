@@ -126,6 +126,16 @@ __host__ __device__ inline unsigned long long cand_key(uint32_t rank, int stage,
            ((unsigned long long)iz << 23) | (unsigned long long)ir;
 }
 
+// outcome of a stream-ordered search, computed on the device: the status
+// and counts the blocking search derives on the host
+struct AsyncResult {
+    int64_t n_found;   // true number of crossings (0 on a non-finite or timeout error)
+    int64_t n_sort;    // records to order (0 when none are reported)
+    int64_t n_out;     // records written to the caller: min(n_sort, capacity)
+    int32_t status;    // fdas_status
+    int32_t pad;
+};
+
 // per-trial statistics and thresholds written on the device
 struct TrialStats {
     double mean, std;
@@ -201,6 +211,7 @@ struct Plan {
     unsigned int *flags = nullptr;  // [0]: non-finite input seen
     uint32_t *rank_ids = nullptr;   // [stats_cap] trial id per rank
     fdas_candidate *out_stage = nullptr;   // [max_cands] ordered output
+    AsyncResult *async_res = nullptr;      // status of the last stream-ordered search
     float *stage = nullptr;         // [n_samples] device copy of a host series
     float *stage2 = nullptr;        // second staging buffer (copies alternate)
     cudaStream_t cpy = nullptr;     // host-to-device copies of host series
@@ -273,6 +284,11 @@ fdas_status launch_harmonic_sums(Plan &p, const void *plane, float *out,
 fdas_status launch_stuck_wait(unsigned int *flags, long long limit_cycles, cudaStream_t s);
 fdas_status launch_candidates_finish(Plan &p, int64_t n, fdas_candidate *out_dev,
                                      cudaStream_t s);
+// stream-ordered end of a search: status and counts into p.async_res, the
+// records ordered and the first min(n, capacity) written to out_dev, all
+// from the count in device memory
+fdas_status launch_candidates_finish_async(Plan &p, int64_t capacity, unsigned int extra_flags,
+                                           fdas_candidate *out_dev, cudaStream_t s);
 std::vector<float2> gauss_legendre_01(int n);
 int refine_nodes();
 fdas_status launch_fourier_power(Plan &p, const float2 *X, const double2 *rz, int n, float *power,

@@ -574,65 +574,130 @@ __global__ void __launch_bounds__(Dedup<P, H>::T, 7)
 // candidate ordering and output
 // ---------------------------------------------------------------------------
 constexpr int kSortThreads = 1024;
-constexpr int kSortSmemMax = 8192;
+constexpr int kSortChunk = 8192;   // records one CTA sorts in shared memory (128 KB)
 
 __device__ __forceinline__ bool rec_less(const CandRec &a, const CandRec &b) { return a.key < b.key; }
 
-// single-CTA bitonic sort in shared memory of n <= 8192 records (padded)
-__global__ void __launch_bounds__(kSortThreads) sort_small_kernel(CandRec *rec, int n, int n_pow2) {
+// smallest power of two >= n (n >= 1)
+__host__ __device__ __forceinline__ int64_t pow2_at_least(int64_t n) {
+    int64_t p = 1;
+    while (p < n) p <<= 1;
+    return p;
+}
+
+// The record count: from device memory when n_dev is set (the count was
+// never brought to the host), else n_host.
+__device__ __forceinline__ int64_t sort_count(const int64_t *n_dev, int64_t n_host) {
+    return n_dev != nullptr ? *n_dev : n_host;
+}
+
+// Bitonic sort of the records [0, n) ascending by key, padded to
+// n2 = pow2_at_least(n) with the largest key.  The compare-exchange of
+// elements i and i ^ j in stage k sorts ascending where (i & k) == 0 (global
+// index), so that every CTA-local part of the network lines up with the
+// global one.
+//
+// sort_chunk_kernel: chunk c = records [c C, c C + C) of the padded array
+// in shared memory.  merge_k == 0: every stage k <= min(C, n2) (the whole
+// local sort; with n2 <= C this is the complete sort), on the records with
+// the padding [n, n2) filled in and written back, so that later steps see n2
+// valid entries; merge_k > 0: the steps j < C of stage merge_k, after the
+// global steps j >= C of that stage, on the chunk as it stands (records
+// and padding have moved by then).
+__global__ void __launch_bounds__(kSortThreads) sort_chunk_kernel(CandRec *rec, const int64_t *n_dev,
+                                                                  int64_t n_host, int64_t merge_k) {
     extern __shared__ CandRec sh[];
+    const int64_t n = sort_count(n_dev, n_host);
+    if (n <= 0) return;
+    const int64_t n2 = pow2_at_least(n);
+    if (merge_k > 0 && (n2 <= kSortChunk || merge_k > n2)) return;
+    const int64_t base = (int64_t)blockIdx.x * kSortChunk;
+    if (base >= n2) return;
+    const int len = (int)(n2 < kSortChunk ? n2 : kSortChunk);
     const int tid = threadIdx.x;
-    for (int i = tid; i < n_pow2; i += kSortThreads) {
-        if (i < n) sh[i] = rec[i];
-        else {
+    for (int i = tid; i < len; i += kSortThreads) {
+        if (merge_k > 0 || base + i < n) {
+            sh[i] = rec[base + i];
+        } else {
             sh[i].key = ~0ull;
             sh[i].power = 0.f;
             sh[i].pad = 0.f;
         }
     }
     __syncthreads();
-    for (int k = 2; k <= n_pow2; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = tid; i < n_pow2; i += kSortThreads) {
-                const int ixj = i ^ j;
-                if (ixj > i) {
-                    const bool up = (i & k) == 0;
-                    const CandRec a = sh[i], b = sh[ixj];
-                    if (rec_less(b, a) == up) {
-                        sh[i] = b;
-                        sh[ixj] = a;
-                    }
+    auto step = [&](int64_t k, int j) {
+        for (int i = tid; i < len; i += kSortThreads) {
+            const int ixj = i ^ j;
+            if (ixj > i) {
+                const bool up = ((base + i) & k) == 0;
+                const CandRec a = sh[i], b = sh[ixj];
+                if (rec_less(b, a) == up) {
+                    sh[i] = b;
+                    sh[ixj] = a;
                 }
             }
-            __syncthreads();
+        }
+        __syncthreads();
+    };
+    if (merge_k == 0) {
+        for (int k = 2; k <= len; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) step(k, j);
+    } else {
+        for (int j = len >> 1; j > 0; j >>= 1) step(merge_k, j);
+    }
+    for (int i = tid; i < len; i += kSortThreads) rec[base + i] = sh[i];
+}
+
+// one global compare-exchange step (k, j >= C) over the padded array
+// (grid-stride; nothing to do unless C < n2 and k <= n2)
+__global__ void bitonic_global_kernel(CandRec *rec, const int64_t *n_dev, int64_t n_host, int64_t k,
+                                      int64_t j) {
+    const int64_t n = sort_count(n_dev, n_host);
+    if (n <= 0) return;
+    const int64_t n2 = pow2_at_least(n);
+    if (n2 <= kSortChunk || k > n2) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t ixj = i ^ j;
+        if (ixj <= i) continue;
+        const bool up = (i & k) == 0;
+        const CandRec a = rec[i], b = rec[ixj];
+        if (rec_less(b, a) == up) {
+            rec[i] = b;
+            rec[ixj] = a;
         }
     }
-    for (int i = tid; i < n; i += kSortThreads) rec[i] = sh[i];
 }
 
-// pad records [n, n_pow2) with the largest key
-__global__ void pad_kernel(CandRec *rec, int64_t n, int64_t n_pow2) {
-    const int64_t i = n + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_pow2) return;
-    CandRec c;
-    c.key = ~0ull;
-    c.power = 0.f;
-    c.pad = 0.f;
-    rec[i] = c;
-}
-
-// one compare-exchange step (k, j) of a bitonic network over n_pow2 records
-__global__ void bitonic_step_kernel(CandRec *rec, int64_t n_pow2, int64_t k, int64_t j) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_pow2) return;
-    const int64_t ixj = i ^ j;
-    if (ixj <= i) return;
-    const bool up = (i & k) == 0;
-    const CandRec a = rec[i], b = rec[ixj];
-    if (rec_less(b, a) == up) {
-        rec[i] = b;
-        rec[ixj] = a;
+// the candidate status of a search, computed on the device from the count
+// and the error flags (the same rules as the host-side collection)
+__global__ void collect_status_kernel(const unsigned long long *__restrict__ count,
+                                      const unsigned int *__restrict__ flags, unsigned int extra_flags,
+                                      int64_t store_cap, int64_t capacity, AsyncResult *out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int64_t total = (int64_t)*count;
+    const unsigned int fl = *flags | extra_flags;
+    AsyncResult r;
+    if (fl & 2u) {
+        r.status = FDAS_ERR_TIMEOUT;
+        r.n_found = 0;
+        r.n_sort = 0;
+    } else if (fl & 1u) {
+        r.status = FDAS_ERR_NONFINITE;
+        r.n_found = 0;
+        r.n_sort = 0;
+    } else if (total > store_cap) {
+        r.status = FDAS_ERR_CAND_STORE_FULL;
+        r.n_found = total;
+        r.n_sort = 0;
+    } else {
+        r.status = total > capacity ? FDAS_ERR_CAND_OVERFLOW : FDAS_OK;
+        r.n_found = total;
+        r.n_sort = total;
     }
+    r.n_out = r.n_sort < capacity ? r.n_sort : capacity;
+    r.pad = 0;
+    *out = r;
 }
 
 // log Q(h, x) for integer h: Q = exp(-x) sum_{k<h} x^k / k!
@@ -671,13 +736,19 @@ __device__ double sigma_from_logp(double lp) {
     return s;
 }
 
-__global__ void finish_kernel(const CandRec *__restrict__ rec, int64_t n,
+// records [0, n) (n = *n_dev when n_dev is set) into caller records; a
+// record whose batch rank is not below n_ranks (never one the harmonic
+// kernels wrote) is not read further
+__global__ void finish_kernel(const CandRec *__restrict__ rec, int64_t n_host,
+                              const int64_t *__restrict__ n_dev,
                               const TrialStats *__restrict__ st, const uint32_t *__restrict__ ids,
-                              fdas_candidate *__restrict__ out, int mode) {
+                              int64_t n_ranks, fdas_candidate *__restrict__ out, int mode) {
+    const int64_t n = n_dev != nullptr ? *n_dev : n_host;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const CandRec c = rec[i];
     const uint32_t rank = (uint32_t)(c.key >> 42);
+    if ((int64_t)rank >= n_ranks) return;
     const int s = (int)((c.key >> 39) & 7);
     const int iz = (int)((c.key >> 23) & 0xffff);
     const uint32_t ir = (uint32_t)(c.key & 0x7fffff);
@@ -961,36 +1032,61 @@ fdas_status launch_harmonic_sums(Plan &p, const void *plane, float *out, cudaStr
 }
 
 // sort the first n stored records and convert them to fdas_candidate
-fdas_status launch_candidates_finish(Plan &p, int64_t n, fdas_candidate *out_dev, cudaStream_t s) {
-    if (n <= 0) return FDAS_OK;
-    int64_t n_pow2 = 1;
-    while (n_pow2 < n) n_pow2 <<= 1;
-    if (n_pow2 <= kSortSmemMax) {
-        const size_t smem = sizeof(CandRec) * (size_t)n_pow2;
-        FDAS_CUDA_TRY(cudaFuncSetAttribute(sort_small_kernel,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        sort_small_kernel<<<1, kSortThreads, smem, s>>>(p.cand, (int)n, (int)n_pow2);
-        FDAS_CUDA_TRY(cudaGetLastError());
-        p.launches[FDAS_PROF_FINISH] += 1;
-    } else {
-        // the record store holds a power-of-two number of entries >= max_cands
-        const unsigned nb = (unsigned)((n_pow2 + 255) / 256);
-        if (n_pow2 > n) {
-            pad_kernel<<<(unsigned)((n_pow2 - n + 255) / 256), 256, 0, s>>>(p.cand, n, n_pow2);
+// the sort network for n records (host count) or for at most cap records
+// with the count in device memory (n_dev): chunk sorts in shared memory, then
+// for each stage k > C the global steps j >= C and one chunk merge
+static fdas_status launch_sort(Plan &p, int64_t n, const int64_t *n_dev, int64_t cap,
+                               cudaStream_t s) {
+    const int64_t n2 = pow2_at_least(std::max<int64_t>(1, n_dev ? cap : n));
+    const int64_t len = std::min<int64_t>(n2, kSortChunk);
+    const unsigned chunks = (unsigned)((n2 + kSortChunk - 1) / kSortChunk);
+    const size_t smem = sizeof(CandRec) * (size_t)len;
+    FDAS_CUDA_TRY(cudaFuncSetAttribute(sort_chunk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(sizeof(CandRec) * kSortChunk)));
+    sort_chunk_kernel<<<chunks, kSortThreads, smem, s>>>(p.cand, n_dev, n, 0);
+    FDAS_CUDA_TRY(cudaGetLastError());
+    p.launches[FDAS_PROF_FINISH] += 1;
+    const unsigned gb = (unsigned)std::min<int64_t>((n2 + 255) / 256, 152 * 16);
+    for (int64_t k = 2 * (int64_t)kSortChunk; k <= n2; k <<= 1) {
+        for (int64_t j = k >> 1; j >= kSortChunk; j >>= 1) {
+            bitonic_global_kernel<<<gb, 256, 0, s>>>(p.cand, n_dev, n, k, j);
             FDAS_CUDA_TRY(cudaGetLastError());
             p.launches[FDAS_PROF_FINISH] += 1;
         }
-        for (int64_t k = 2; k <= n_pow2; k <<= 1)
-            for (int64_t j = k >> 1; j > 0; j >>= 1) {
-                bitonic_step_kernel<<<nb, 256, 0, s>>>(p.cand, n_pow2, k, j);
-                FDAS_CUDA_TRY(cudaGetLastError());
-                p.launches[FDAS_PROF_FINISH] += 1;
-            }
+        sort_chunk_kernel<<<chunks, kSortThreads, smem, s>>>(p.cand, n_dev, n, k);
+        FDAS_CUDA_TRY(cudaGetLastError());
+        p.launches[FDAS_PROF_FINISH] += 1;
     }
-    finish_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p.cand, n, p.stats, p.rank_ids,
-                                                               out_dev, p.thr_mode);
+    return FDAS_OK;
+}
+
+fdas_status launch_candidates_finish(Plan &p, int64_t n, fdas_candidate *out_dev, cudaStream_t s) {
+    if (n <= 0) return FDAS_OK;
+    FDAS_TRY(launch_sort(p, n, nullptr, 0, s));
+    finish_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p.cand, n, nullptr, p.stats, p.rank_ids,
+                                                               p.stats_cap, out_dev, p.thr_mode);
     FDAS_CUDA_TRY(cudaGetLastError());
     p.launches[FDAS_PROF_FINISH] += 1;
+    return FDAS_OK;
+}
+
+fdas_status launch_candidates_finish_async(Plan &p, int64_t capacity, unsigned int extra_flags,
+                                           fdas_candidate *out_dev, cudaStream_t s) {
+    collect_status_kernel<<<1, 32, 0, s>>>(p.cand_count, p.flags, extra_flags, p.store_cap, capacity,
+                                           p.async_res);
+    FDAS_CUDA_TRY(cudaGetLastError());
+    p.launches[FDAS_PROF_FINISH] += 1;
+    const int64_t cap = p.store_cap;   // n_sort <= store_cap
+    if (cap <= 0) return FDAS_OK;
+    FDAS_TRY(launch_sort(p, 0, &p.async_res->n_sort, cap, s));
+    const int64_t n_out_max = std::min(cap, capacity);
+    if (n_out_max > 0 && out_dev != nullptr) {
+        const unsigned gb = (unsigned)((n_out_max + 255) / 256);
+        finish_kernel<<<gb, 256, 0, s>>>(p.cand, 0, &p.async_res->n_out, p.stats, p.rank_ids,
+                                         p.stats_cap, out_dev, p.thr_mode);
+        FDAS_CUDA_TRY(cudaGetLastError());
+        p.launches[FDAS_PROF_FINISH] += 1;
+    }
     return FDAS_OK;
 }
 

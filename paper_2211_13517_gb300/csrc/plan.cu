@@ -138,6 +138,7 @@ static void free_plan_memory(Plan *p) {
     cudaFree(p->cand_count);
     cudaFree(p->flags);
     cudaFree(p->out_stage);
+    cudaFree(p->async_res);
     cudaFree(p->stage);
     cudaFree(p->stage2);
     for (int b = 0; b < 2; ++b) {
@@ -455,6 +456,7 @@ static fdas_status create(Plan *&out, int64_t n_samples, double tsamp, double z_
     PLAN_TRY(dalloc(p, &p.cand_count, sizeof(unsigned long long)));
     PLAN_TRY(dalloc(p, &p.flags, sizeof(unsigned int)));
     PLAN_TRY(dalloc(p, &p.out_stage, sizeof(fdas_candidate) * (size_t)p.max_cands));
+    PLAN_TRY(dalloc(p, &p.async_res, sizeof(AsyncResult)));
     PLAN_TRY(dalloc(p, &p.stage, sizeof(float) * (size_t)p.n_samples));
     PLAN_TRY(dalloc(p, &p.stage2, sizeof(float) * (size_t)p.n_samples));
     PLAN_CUDA(cudaStreamCreateWithFlags(&p.cpy, cudaStreamNonBlocking));
@@ -779,18 +781,13 @@ static fdas_status run_as_graph(Plan &p, const fdas_series *batch, int32_t n_ser
     return FDAS_OK;
 }
 
-static fdas_status search(Plan &p, const fdas_series *batch, int32_t n_series,
-                          fdas_candidate *cands, int64_t capacity, int64_t *n_found,
-                          cudaStream_t s) {
-    const Fault fault = injected_fault();
-    FDAS_TRY(fault_args_check(fault));
+// the series checks shared by both searches; graphable is cleared when a
+// series is in pageable host memory
+static fdas_status check_batch(const Plan &p, const fdas_series *batch, int32_t n_series,
+                               bool &graphable) {
     if (n_series < 0) return arg_error("n_series < 0");
     if (n_series > (1 << 22)) return arg_error("n_series > 2^22");
     if (n_series > 0 && batch == nullptr) return arg_error("batch is NULL");
-    if (n_found == nullptr) return arg_error("n_found is NULL");
-    if (capacity < 0 || (capacity > 0 && cands == nullptr)) return arg_error("bad cands/capacity");
-    bool graphable = p.use_graph && !p.profiling && s != nullptr && s != cudaStreamLegacy &&
-                     s != cudaStreamPerThread;
     for (int32_t i = 0; i < n_series; ++i) {
         const int64_t n = batch[i].n_samples;
         if (batch[i].data == nullptr) return arg_error("series " + std::to_string(i) + " has NULL data");
@@ -801,8 +798,15 @@ static fdas_status search(Plan &p, const fdas_series *batch, int32_t n_series,
             return arg_error("series " + std::to_string(i) + " is not 16-byte aligned");
         if (graphable && !is_pinned_or_device(batch[i].data)) graphable = false;
     }
-    *n_found = 0;
-    DeviceGuard guard(p.device);
+    return FDAS_OK;
+}
+
+// everything of a search up to the candidate collection, queued on s: trial
+// ranks, counters reset, and the batch (as a graph, or forked to the plan's
+// streams and joined back to s)
+static fdas_status enqueue_search(Plan &p, const Fault &fault, const fdas_series *batch,
+                                  int32_t n_series, bool graphable, cudaStream_t s,
+                                  std::vector<Interval> &iv, size_t &ev) {
     p.store_cap = fault.kind == kFaultCapacity ? 1 : p.max_cands;
     FDAS_TRY(grow_stats(p, std::max<int64_t>(1, n_series)));
     // rank = position in trial_id order (stable), so the output order is
@@ -816,13 +820,12 @@ static fdas_status search(Plan &p, const fdas_series *batch, int32_t n_series,
         rank[order[i]] = i;
         ids[i] = batch[order[i]].trial_id;
     }
+    // (a copy from pageable memory returns once the source has been read)
     if (n_series > 0)
         FDAS_CUDA_TRY(cudaMemcpyAsync(p.rank_ids, ids.data(), sizeof(uint32_t) * n_series,
                                       cudaMemcpyHostToDevice, s));
     FDAS_CUDA_TRY(cudaMemsetAsync(p.cand_count, 0, sizeof(unsigned long long), s));
     FDAS_CUDA_TRY(cudaMemsetAsync(p.flags, 0, sizeof(unsigned int), s));
-    std::vector<Interval> iv;
-    size_t ev = 0;
     if (p.profiling) {
         FDAS_TRY(events_reserve(p, 7 * (size_t)n_series + 2));
         iv.reserve(3 * (size_t)n_series + 1);
@@ -832,6 +835,24 @@ static fdas_status search(Plan &p, const fdas_series *batch, int32_t n_series,
     } else {
         FDAS_TRY(enqueue_batch(p, batch, n_series, rank, s, iv, ev));
     }
+    return FDAS_OK;
+}
+
+static fdas_status search(Plan &p, const fdas_series *batch, int32_t n_series,
+                          fdas_candidate *cands, int64_t capacity, int64_t *n_found,
+                          cudaStream_t s) {
+    const Fault fault = injected_fault();
+    FDAS_TRY(fault_args_check(fault));
+    if (n_found == nullptr) return arg_error("n_found is NULL");
+    if (capacity < 0 || (capacity > 0 && cands == nullptr)) return arg_error("bad cands/capacity");
+    bool graphable = p.use_graph && !p.profiling && s != nullptr && s != cudaStreamLegacy &&
+                     s != cudaStreamPerThread;
+    FDAS_TRY(check_batch(p, batch, n_series, graphable));
+    *n_found = 0;
+    DeviceGuard guard(p.device);
+    std::vector<Interval> iv;
+    size_t ev = 0;
+    FDAS_TRY(enqueue_search(p, fault, batch, n_series, graphable, s, iv, ev));
     p.prof_trials += n_series;
     cudaEvent_t f0 = nullptr;
     if (p.profiling) {
@@ -847,6 +868,54 @@ static fdas_status search(Plan &p, const fdas_series *batch, int32_t n_series,
         accumulate(p, iv);
     }
     return st;
+}
+
+// the address a kernel writes `ptr` through: device (or managed) memory as
+// it is, page-locked host memory by its mapped device address; NULL for
+// memory the device cannot reach
+static void *device_view(void *ptr) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return ptr;
+    if (a.type == cudaMemoryTypeHost) return a.devicePointer;
+    return nullptr;
+}
+
+static fdas_status search_async(Plan &p, const fdas_series *batch, int32_t n_series,
+                                fdas_candidate *cands, int64_t capacity, int64_t *n_found,
+                                int32_t *status, cudaStream_t s) {
+    const Fault fault = injected_fault();
+    FDAS_TRY(fault_args_check(fault));
+    if (n_found == nullptr || status == nullptr) return arg_error("n_found or status is NULL");
+    if (capacity < 0 || (capacity > 0 && cands == nullptr)) return arg_error("bad cands/capacity");
+    if (p.profiling)
+        return arg_error("tracing is on: the stream-ordered search is not traced (use fdas_search)");
+    // nothing below may wait for the device: the results go to memory the
+    // stream can write without the host
+    if (!is_pinned_or_device(n_found) || !is_pinned_or_device(status))
+        return arg_error("n_found and status must be device or page-locked host memory");
+    fdas_candidate *out_dev = nullptr;
+    if (capacity > 0) {
+        out_dev = (fdas_candidate *)device_view(cands);
+        if (out_dev == nullptr) return arg_error("cands must be device or page-locked host memory");
+    }
+    bool graphable = p.use_graph && s != nullptr && s != cudaStreamLegacy &&
+                     s != cudaStreamPerThread;
+    FDAS_TRY(check_batch(p, batch, n_series, graphable));
+    DeviceGuard guard(p.device);
+    std::vector<Interval> iv;
+    size_t ev = 0;
+    FDAS_TRY(enqueue_search(p, fault, batch, n_series, graphable, s, iv, ev));
+    const unsigned int extra = fault.kind == kFaultNan ? 1u : 0u;
+    FDAS_TRY(launch_candidates_finish_async(p, capacity, extra, out_dev, s));
+    FDAS_CUDA_TRY(cudaMemcpyAsync(n_found, &p.async_res->n_found, sizeof(int64_t),
+                                  cudaMemcpyDefault, s));
+    FDAS_CUDA_TRY(cudaMemcpyAsync(status, &p.async_res->status, sizeof(int32_t),
+                                  cudaMemcpyDefault, s));
+    return FDAS_OK;
 }
 
 // time the correlation of one full-length series on a plan (synthetic unit
@@ -1041,6 +1110,19 @@ fdas_status fdas_search(fdas_plan *plan, const fdas_series *batch, int32_t n_ser
                       (cudaStream_t)stream);
     } catch (...) {
         set_error("unexpected C++ exception in fdas_search");
+        return FDAS_ERR_CUDA;
+    }
+}
+
+fdas_status fdas_search_async(fdas_plan *plan, const fdas_series *batch, int32_t n_series,
+                              fdas_candidate *cands, int64_t capacity, int64_t *n_found,
+                              int32_t *status, void *stream) {
+    try {
+        if (!plan) return arg_error("plan is NULL");
+        return search_async(*reinterpret_cast<Plan *>(plan), batch, n_series, cands, capacity,
+                            n_found, status, (cudaStream_t)stream);
+    } catch (...) {
+        set_error("unexpected C++ exception in fdas_search_async");
         return FDAS_ERR_CUDA;
     }
 }
