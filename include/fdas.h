@@ -80,6 +80,14 @@ enum { FDAS_CORR_AUTO = 0, FDAS_CORR_FFT = 1, FDAS_CORR_TENSOR = 2, FDAS_CORR_TE
  *   cells where every multiple lies in the plane (h ir <= N_r - 1,
  *   |h o| <= K); fewer gathers and additions, a different candidate list. */
 enum { FDAS_HARM_TOP = 0, FDAS_HARM_FUNDAMENTAL = 1 };
+/* order of the templates in the tensor-core correlation's chunks of 28 (the
+ * same plane either way; the time differs):
+ * FDAS_TORDER_Z: consecutive z;
+ * FDAS_TORDER_PAIRED: 14 templates with z <= 0 and 14 with z > 0 of about
+ *   the same |z|, so that a chunk's templates have similar widths and less of
+ *   the K dimension is padding;
+ * FDAS_TORDER_DEFAULT: PAIRED, or with autotune the faster of the two. */
+enum { FDAS_TORDER_DEFAULT = 0, FDAS_TORDER_Z = 1, FDAS_TORDER_PAIRED = 2 };
 /* Interbinning (fdas_opts.interbin = 1; the paper does not use it, an
  * option of the search): the power plane is sampled every half bin, n_z x
  * 2 N_r cells.  With F(r, z) the complex correlation (the matched-filter
@@ -108,7 +116,8 @@ typedef struct {
     int32_t harmonic_mode;   /* FDAS_HARM_TOP (default) or FDAS_HARM_FUNDAMENTAL */
     int32_t interbin;        /* 1: the plane on the half-bin grid (see below);
                                 0 (default): whole bins.  Needs n_samples <= 2^23 */
-    int32_t reserved0;       /* set to 0 */
+    int32_t template_order;  /* tensor-core correlation: FDAS_TORDER_DEFAULT (0),
+                                _Z or _PAIRED (below); other correlators ignore it */
 } fdas_opts;
 
 /* One dedispersed time series (one DM trial).  `data` points to n_samples
@@ -151,7 +160,8 @@ typedef struct {
     int32_t correlator;       /* FDAS_CORR_FFT, _TENSOR or _TENSOR_SPLIT, as built */
     int32_t harmonic_mode;    /* FDAS_HARM_TOP or FDAS_HARM_FUNDAMENTAL         */
     int32_t interbin;         /* 1: half-bin plane                             */
-    int32_t reserved0;
+    int32_t template_order;   /* FDAS_TORDER_Z or _PAIRED as built (tensor-core
+                                 correlation), 0 for the FFT correlator          */
     int64_t plane_cols;       /* columns of the power plane: N_r or 2 N_r      */
 } fdas_plan_info;
 

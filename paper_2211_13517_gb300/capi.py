@@ -42,6 +42,7 @@ FDAS_THRESH_GAMMA_TAIL, FDAS_THRESH_MEAN_PLUS_KSIGMA = 0, 1
 FDAS_NORM_MEDIAN, FDAS_NORM_NONE = 0, 1
 FDAS_CORR_AUTO, FDAS_CORR_FFT, FDAS_CORR_TENSOR, FDAS_CORR_TENSOR_SPLIT = 0, 1, 2, 3
 FDAS_HARM_TOP, FDAS_HARM_FUNDAMENTAL = 0, 1
+FDAS_TORDER_DEFAULT, FDAS_TORDER_Z, FDAS_TORDER_PAIRED = 0, 1, 2
 
 EXPORTED = ["fdas_opts_default", "fdas_plan_create", "fdas_plan_destroy",
             "fdas_plan_get_info", "fdas_search", "fdas_search_async", "fdas_spectrum",
@@ -61,7 +62,7 @@ class fdas_opts(Structure):
                 ("norm_block", c_int32), ("max_candidates", c_int64),
                 ("autotune", c_int32), ("use_graph", c_int32),
                 ("correlator", c_int32), ("harmonic_mode", c_int32),
-                ("interbin", c_int32), ("reserved0", c_int32)]
+                ("interbin", c_int32), ("template_order", c_int32)]
 
 
 class fdas_series(Structure):
@@ -88,7 +89,7 @@ class fdas_plan_info(Structure):
                 ("threshold_sigma", c_double), ("stage_factor", c_double * 6),
                 ("workspace_bytes", c_int64), ("z_chunks", c_int32), ("use_graph", c_int32),
                 ("tuned_ms", c_double), ("correlator", c_int32), ("harmonic_mode", c_int32),
-                ("interbin", c_int32), ("reserved0", c_int32), ("plane_cols", c_int64)]
+                ("interbin", c_int32), ("template_order", c_int32), ("plane_cols", c_int64)]
 
 
 class fdas_seed(Structure):
@@ -386,7 +387,8 @@ class Plan:
                  n_harm=16, precision=FDAS_FP32, threshold_sigma=6.0,
                  threshold_mode=FDAS_THRESH_GAMMA_TAIL, norm_mode=FDAS_NORM_MEDIAN,
                  norm_block=2048, max_candidates=1 << 20, autotune=False, use_graph=False,
-                 correlator=None, harmonic_mode=FDAS_HARM_TOP, interbin=False):
+                 correlator=None, harmonic_mode=FDAS_HARM_TOP, interbin=False,
+                 template_order=FDAS_TORDER_DEFAULT):
         o = fdas_opts_default()
         o.precision = precision
         o.threshold_sigma = threshold_sigma
@@ -400,6 +402,7 @@ class Plan:
             o.correlator = correlator
         o.harmonic_mode = harmonic_mode
         o.interbin = 1 if interbin else 0
+        o.template_order = template_order
         self.handle = fdas_plan_create(n_samples, tsamp, z_max, z_step, seg_len, n_harm, o)
         self.info = fdas_plan_get_info(self.handle)
 

@@ -45,6 +45,7 @@
 // 31 record their first and last F of the tile in an edge table from which
 // the fix-up computes it (with F(N_r) = 0 after the last tile).
 #include <algorithm>
+#include <array>
 
 #include "fdas_internal.cuh"
 #include "tcgen05.cuh"
@@ -292,8 +293,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         while (sch.next(c, t)) {
             if (c != cur) {
                 cur = c;
-                const int zb = chunks[c].z_begin + kTcZpt * part;
-                zvalid = chunks[c].n_zc - kTcZpt * part;
+                const int zb = chunks[c].z_part[part];
+                zvalid = chunks[c].n_part[part];
 #pragma unroll
                 for (int k = 0; k < kTcZpt; ++k) {
                     const float ie = k < zvalid ? __ldg(inv_energy + zb + k) : 0.f;
@@ -486,9 +487,10 @@ __global__ void tc_bank_kernel(uint16_t *__restrict__ img, const TcChunk *__rest
         const int zz = nb, c = rw >> 2, p = rw & 3;
         const int kk = 8 * cb + kk8;
         const int q = 8 * k + kk / 2, comp = kk & 1;
+        const int half = zz / kTcZpt, zk = zz % kTcZpt;
         double v = 0.0;
-        if (zz < ch.n_zc) {
-            const int iz = ch.z_begin + zz;
+        if (zk < ch.n_part[half]) {
+            const int iz = ch.z_part[half] + zk;
             const int e = p + W0 - ch.kofs - q;
             const int mz = m[iz];
             if (e >= -mz && e <= mz) {
@@ -655,16 +657,41 @@ fdas_status launch_tc_P(Plan &p, const void *spec_padded, void *plane, double2 *
 
 std::vector<TcChunk> tc_chunk_table(const Plan &p, const std::vector<int32_t> &m, int *win,
                                     int *max_ks) {
+    static_assert(kTcZ == 2 * kTcZpt, "two halves of epilogue warps per chunk");
     const int W0 = p.m_ov;
     std::vector<TcChunk> out;
+    // the templates of each chunk, by half
+    std::vector<std::array<int32_t, 4>> parts;   // z_part[0], n_part[0], z_part[1], n_part[1]
+    if (p.tc_order == 0) {
+        for (int z0 = 0; z0 < p.n_z; z0 += kTcZ) {
+            const int n = std::min(kTcZ, p.n_z - z0);
+            parts.push_back({z0, std::min(kTcZpt, n), z0 + kTcZpt, std::max(0, n - kTcZpt)});
+        }
+    } else {
+        // half 0: z = 0, -1, -2, ... (rows iz0, iz0 - 1, ...), half 1: z = 1,
+        // 2, ...; chunk c takes the c-th run of 14 of each, so its templates
+        // span about 15 values of |z|
+        for (int c = 0;; ++c) {
+            const int hi0 = p.iz0 - kTcZpt * c;             // last row of half 0
+            const int lo0 = std::max(0, hi0 - kTcZpt + 1);
+            const int n0 = hi0 >= 0 ? hi0 - lo0 + 1 : 0;
+            const int lo1 = p.iz0 + 1 + kTcZpt * c;
+            const int n1 = std::max(0, std::min(kTcZpt, p.n_z - lo1));
+            if (n0 == 0 && n1 == 0) break;
+            parts.push_back({n0 > 0 ? lo0 : 0, n0, n1 > 0 ? lo1 : 0, n1});
+        }
+    }
     int64_t b_off = 0;
     int wmax = 0, kmax = 0;
-    for (int z0 = 0; z0 < p.n_z; z0 += kTcZ) {
+    for (const auto &pt : parts) {
         TcChunk c;
-        c.z_begin = z0;
-        c.n_zc = std::min(kTcZ, p.n_z - z0);
+        c.z_part[0] = pt[0];
+        c.n_part[0] = pt[1];
+        c.z_part[1] = pt[2];
+        c.n_part[1] = pt[3];
         int mc = 0;
-        for (int iz = z0; iz < z0 + c.n_zc; ++iz) mc = std::max(mc, m[iz]);
+        for (int h = 0; h < 2; ++h)
+            for (int iz = c.z_part[h]; iz < c.z_part[h] + c.n_part[h]; ++iz) mc = std::max(mc, m[iz]);
         c.kofs = (W0 - mc) & ~3;
         const int kc = (W0 - c.kofs + mc + 4 + 7) / 8 * 8;   // complex taps q in [0, kc)
         c.ks = kc / 8;

@@ -145,8 +145,11 @@ struct TrialStats {
 // one chunk of templates of the tensor-core correlation: its templates, the
 // K range it reads of each spectrum window and where its operand image lives
 struct TcChunk {
-    int32_t z_begin;   // first template index of the chunk
-    int32_t n_zc;      // templates in the chunk (the rest of the 28 columns are 0)
+    // the chunk's 28 column groups in two halves of 14, one per half of the
+    // epilogue warps: half h holds templates z_part[h] .. z_part[h] +
+    // n_part[h] - 1 (the rest of its columns are 0)
+    int32_t z_part[2];
+    int32_t n_part[2];
     int32_t kofs;      // first complex element of the window it reads (multiple of 4)
     int32_t ks;        // K steps of 8 complex taps (16 real elements)
     int64_t b_off;     // byte offset of the chunk's template image in tc_bank
@@ -190,6 +193,10 @@ struct Plan {
     int64_t tc_split_elems = 0;
     int tc_n_ch = 0, tc_max_ks = 0, tc_win = 0;
     int tc_nbuf = 1;                  // template-image buffers in shared memory (1 or 2)
+    // template order of the chunks: 0 = consecutive z, 28 per chunk; 1 =
+    // pairs of +-|z| (one half of each chunk z <= 0, the other z > 0), so
+    // that a chunk's templates have similar widths
+    int tc_order = 1;
     // FFT split of the N/2-point complex FFT in the spectrum stage
     int fft_m1, fft_m2;     // M = m1 * m2 (m1 = 1: single pass)
     // device memory

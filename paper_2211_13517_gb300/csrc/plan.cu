@@ -311,6 +311,8 @@ static fdas_status create(Plan *&out, int64_t n_samples, double tsamp, double z_
     if (o->harmonic_mode != FDAS_HARM_TOP && o->harmonic_mode != FDAS_HARM_FUNDAMENTAL)
         return arg_error("unknown harmonic_mode");
     if (o->interbin != 0 && o->interbin != 1) return arg_error("interbin must be 0 or 1");
+    if (o->template_order < FDAS_TORDER_DEFAULT || o->template_order > FDAS_TORDER_PAIRED)
+        return arg_error("template_order must be FDAS_TORDER_DEFAULT, _Z or _PAIRED");
     // candidate records keep the plane column in 23 bits
     if (o->interbin && n_samples > (1 << 23))
         return arg_error("interbinning takes n_samples <= 2^23");
@@ -388,6 +390,7 @@ static fdas_status create(Plan *&out, int64_t n_samples, double tsamp, double z_
     // template chunks that fit in shared memory), else overlap-save FFTs
     std::vector<TcChunk> tc_table;
     p.tc_split = o->correlator == FDAS_CORR_TENSOR_SPLIT;
+    p.tc_order = o->template_order == FDAS_TORDER_Z ? 0 : 1;
     if (o->correlator != FDAS_CORR_FFT && (p.prec != FDAS_FP32 || p.tc_split)) {
         tc_table = tc_chunk_table(p, m, &p.tc_win, &p.tc_max_ks);
         p.tc_n_ch = (int)tc_table.size();
@@ -948,10 +951,46 @@ static fdas_status time_correlation(Plan &p, double &ms) {
     return FDAS_OK;
 }
 
+// rebuild the tensor-core template chunks of a plan in another template
+// order (chunk table, template images, shared-memory layout)
+static fdas_status retable_tc(Plan &p, int order) {
+    if (p.correlator != FDAS_CORR_TENSOR || p.tc_order == order) return FDAS_OK;
+    std::vector<int32_t> m(p.n_z);
+    FDAS_CUDA_TRY(cudaMemcpy(m.data(), p.tap_m, sizeof(int32_t) * p.n_z, cudaMemcpyDeviceToHost));
+    const int old_order = p.tc_order, old_win = p.tc_win, old_ks = p.tc_max_ks, old_n = p.tc_n_ch;
+    p.tc_order = order;
+    std::vector<TcChunk> table = tc_chunk_table(p, m, &p.tc_win, &p.tc_max_ks);
+    if (!tc_applicable(p, nullptr)) {
+        p.tc_order = old_order;
+        p.tc_win = old_win;
+        p.tc_max_ks = old_ks;
+        p.tc_n_ch = old_n;
+        set_error("template order does not fit in shared memory");
+        return FDAS_ERR_UNSUPPORTED;
+    }
+    FDAS_CUDA_TRY(cudaDeviceSynchronize());
+    const int64_t img = tc_bank_bytes(table);
+    cudaFree(p.tc_chunks);
+    cudaFree(p.tc_bank);
+    p.tc_chunks = nullptr;
+    p.tc_bank = nullptr;
+    FDAS_TRY(dalloc(p, &p.tc_chunks, sizeof(TcChunk) * table.size()));
+    if (p.tc_split) p.tc_bank_lo = img;
+    FDAS_TRY(dalloc(p, &p.tc_bank, (size_t)img * (p.tc_split ? 2 : 1)));
+    p.tc_n_ch = (int)table.size();
+    p.tc_nbuf = tc_image_buffers(p);
+    FDAS_CUDA_TRY(cudaMemcpy(p.tc_chunks, table.data(), sizeof(TcChunk) * table.size(),
+                             cudaMemcpyHostToDevice));
+    FDAS_TRY(launch_tc_bank(p, p.aux));
+    FDAS_CUDA_TRY(cudaStreamSynchronize(p.aux));
+    return FDAS_OK;
+}
+
 // autotune: the correlator (the tensor-core GEMM, where it applies and was
 // not excluded, against overlap-save FFTs), the segment length among {2048,
 // 4096, 8192} and the one asked for, then the template chunking of the
-// fastest FFT plan, by timing the correlation
+// fastest FFT plan or the template order of the tensor-core chunks, by
+// timing the correlation
 static fdas_status create_tuned(Plan *&out, int64_t n_samples, double tsamp, double z_max,
                                 double z_step, int32_t seg_len, int32_t n_harm, fdas_opts o) {
     o.autotune = 0;
@@ -1014,6 +1053,18 @@ static fdas_status create_tuned(Plan *&out, int64_t n_samples, double tsamp, dou
         }
     }
     best->n_zchunk = best_c;
+    // template order of the tensor-core chunks, unless asked for
+    if (best->correlator == FDAS_CORR_TENSOR && o.template_order == FDAS_TORDER_DEFAULT) {
+        const int first = best->tc_order;
+        if (retable_tc(*best, 1 - first) == FDAS_OK) {
+            double ms = 0.0;
+            if (time_correlation(*best, ms) == FDAS_OK && ms < best_ms) {
+                best_ms = ms;
+            } else {
+                FDAS_TRY(retable_tc(*best, first));
+            }
+        }
+    }
     best->tuned_ms = best_ms;
     out = best;
     return FDAS_OK;
@@ -1097,7 +1148,9 @@ fdas_status fdas_plan_get_info(const fdas_plan *plan, fdas_plan_info *info) {
     info->correlator = p.tc_split ? FDAS_CORR_TENSOR_SPLIT : p.correlator;
     info->harmonic_mode = p.harm_mode;
     info->interbin = p.interbin ? 1 : 0;
-    info->reserved0 = 0;
+    info->template_order = p.correlator != FDAS_CORR_TENSOR ? 0
+                           : p.tc_order == 0                  ? FDAS_TORDER_Z
+                                                              : FDAS_TORDER_PAIRED;
     info->plane_cols = plane_cols(p);
     return FDAS_OK;
 }

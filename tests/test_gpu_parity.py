@@ -137,11 +137,11 @@ def test_spectrum_without_normalisation(capi):
 # ---------------------------------------------------------------------------
 # a3-a6: correlation / power plane / statistics
 # ---------------------------------------------------------------------------
-def _plane_case(capi, n, z_max, z_step, L, seed=7, prec=0, corr=None):
+def _plane_case(capi, n, z_max, z_step, L, seed=7, prec=0, corr=None, **kw):
     x = S.sinusoid_series(n=n, seed=seed, r0=0.3 * n / 2 + 0.4, z0=z_max * 0.45, amp=0.1)
     g = O.geometry(n, z_max, z_step, 4)
     Xn, _ = O.normalise(O.spectrum(x), 2048)
-    plan = _plan(capi, n, z_max, z_step, L, 4, precision=prec, correlator=corr)
+    plan = _plan(capi, n, z_max, z_step, L, 4, precision=prec, correlator=corr, **kw)
     if corr is not None:
         assert plan.info.correlator == corr
     il = np.empty(2 * Xn.shape[0], dtype=np.float32)
@@ -198,13 +198,16 @@ def test_power_plane_low_precision_storage(capi, prec, corr):
     (1 << 16, 96.0, 1.0),       # the 193-template grid: 7 chunks of 28
     (1 << 15, 200.0, 4.0),      # widest templates (m = 108), 101 templates
 ])
-@pytest.mark.parametrize("prec", [1, 2])
-def test_tensor_plane_matches_direct_correlation(capi, n, z_max, z_step, prec):
+@pytest.mark.parametrize("prec,order", [(1, 2), (2, 2), (1, 1), (2, 1)])
+def test_tensor_plane_matches_direct_correlation(capi, n, z_max, z_step, prec, order):
     """The tensor-core correlation against the FP64 direct sum over the whole
     plane (every tile, chunk and phase), on the spectrum exactly as stored:
-    within 3% of max(P, mean) (16-bit taps and plane, FP32 sums)."""
+    within 3% of max(P, mean) (16-bit taps and plane, FP32 sums); both
+    template orders of the chunks (paired +-|z|, consecutive z)."""
     plan, plane, stats, P, g = _plane_case(capi, n, z_max, z_step, 1024 if z_max < 100 else 2048,
-                                           prec=prec, corr=capi.FDAS_CORR_TENSOR)
+                                           prec=prec, corr=capi.FDAS_CORR_TENSOR,
+                                           template_order=order)
+    assert plan.info.template_order == order
     got = plane.float().cpu().numpy().astype(np.float64)
     if prec == 2:
         got *= 16.0
