@@ -264,6 +264,8 @@ fdas_status fdas_search(fdas_plan *plan, const fdas_series *batch,
  * launches for max_candidates = 2^20).
  * The plan's buffers are reused by the next search: calls on one plan must
  * be ordered by the caller (one stream, or a synchronisation in between).
+ * A call with more series than any earlier call on the plan first grows the
+ * plan's per-trial buffers, which waits for the device once.
  */
 fdas_status fdas_search_async(fdas_plan *plan, const fdas_series *batch,
                               int32_t n_series, fdas_candidate *cands,
