@@ -142,6 +142,8 @@ constexpr int kTopShift = 19;                    // first digit: bits 31..19 of 
 constexpr int kTopBins = 1 << (32 - kTopShift);  // 8192 (two 16-bit counters per word)
 constexpr int kListCap = 2 * kNormThreads;       // keys of the median's bin ranked directly
 static_assert(kTopBins % (16 * kNormThreads) == 0, "whole 16-byte groups of packed counters");
+static_assert(((kTopBins / (16 * kNormThreads)) & (kTopBins / (16 * kNormThreads) - 1)) == 0,
+              "a power-of-two number of 16-byte loads per thread");
 
 // CTA-wide exclusive position of rank `r` in a histogram of `nb` counters
 // (16-bit halves of `words` when `packed`, else one counter per word): the
@@ -154,10 +156,13 @@ __device__ __forceinline__ void hist_locate(const uint32_t *words, int nb, bool 
     const int per = nb / kNormThreads;   // counters per thread
     uint32_t local = 0u;
     if (packed) {
-        // per counters = per / 2 words, in 16-byte loads
-        const uint4 *w4 = reinterpret_cast<const uint4 *>(words) + tid * (per / 8);
-        for (int q = 0; q < per / 8; ++q) {
-            const uint4 a = w4[q];
+        // per counters = per / 2 words, in 16-byte loads; thread t starts at
+        // its (t / 2)-th load (mod the count), so the 8 lanes of a
+        // quarter-warp read distinct banks (the sum does not depend on order)
+        const int nq = per / 8;
+        const uint4 *w4 = reinterpret_cast<const uint4 *>(words) + tid * nq;
+        for (int q = 0; q < nq; ++q) {
+            const uint4 a = w4[(q + (tid >> 1)) & (nq - 1)];
             local += (a.x & 0xffffu) + (a.x >> 16) + (a.y & 0xffffu) + (a.y >> 16) +
                      (a.z & 0xffffu) + (a.z >> 16) + (a.w & 0xffffu) + (a.w >> 16);
         }
