@@ -158,3 +158,30 @@ def test_autotuned_plan(capi, uneven):
     st, cands, nf = plan.search([torch.from_numpy(x).cuda() for x in xs], trial_ids=ids)
     _check(cands, refs[1e-4], 1e-4, 1e-4)
     plan.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_uneven_batch_from_host_memory(capi, uneven, prec):
+    """The same uneven batch from page-locked host memory (copied by the
+    library's copy kernel), from pageable host memory (cudaMemcpyAsync) and
+    from device memory: identical records, in both search calls."""
+    lengths, xs, ids, refs = uneven
+    plan = capi.Plan(NMAX, 64e-6, ZMAX, ZSTEP, L, H, precision=prec)
+    dev = [torch.from_numpy(x).cuda() for x in xs]
+    pinned = [torch.from_numpy(x).pin_memory() for x in xs]
+    pageable = [torch.from_numpy(x).clone() for x in xs]
+    st0, c0, n0 = plan.search(dev, trial_ids=ids, capacity=1 << 15)
+    assert st0 == capi.FDAS_OK and n0 == len(c0) > 0
+    for host in (pinned, pageable):
+        st, c, n = plan.search(host, trial_ids=ids, capacity=1 << 15)
+        assert st == capi.FDAS_OK and c.tobytes() == c0.tobytes()
+        cands = torch.zeros((1 << 15) * 20, dtype=torch.uint8, device="cuda")
+        nf = torch.zeros(1, dtype=torch.int64, device="cuda")
+        sa = torch.zeros(1, dtype=torch.int32, device="cuda")
+        plan.search_async(host, cands, nf, sa, trial_ids=ids)
+        torch.cuda.synchronize()
+        assert int(sa.cpu()[0]) == capi.FDAS_OK and int(nf.cpu()[0]) == n0
+        assert capi.Plan.candidates(cands, n0).tobytes() == c0.tobytes()
+    guard, rel = (1e-4, 1e-4) if prec == 0 else (0.03, 0.03)
+    _check(c0, refs[guard], guard, rel)
+    plan.close()
