@@ -130,6 +130,13 @@ def test_opts_validation(capi):
     with pytest.raises(capi.FdasError) as ei:
         capi.fdas_plan_create(1 << 24, 64e-6, 16.0, 2.0, 2048, 4, o)
     assert ei.value.status == capi.FDAS_ERR_ARG and "2^23" in str(ei.value)
+    # the template order of the tensor-core chunks takes the three enumerators
+    for bad in (-1, 3):
+        o = capi.fdas_opts_default()
+        o.template_order = bad
+        with pytest.raises(capi.FdasError) as ei:
+            capi.fdas_plan_create(1 << 17, 64e-6, 16.0, 2.0, 2048, 4, o)
+        assert ei.value.status == capi.FDAS_ERR_ARG and "template_order" in str(ei.value)
 
 
 def test_null_arguments_rejected(capi):

@@ -182,3 +182,26 @@ def test_async_argument_checks(capi):
     torch.cuda.synchronize()
     assert int(st.cpu()[0]) == capi.FDAS_OK
     plan.close()
+
+
+def test_async_with_graph_replay_and_host_series(capi):
+    """A plan that replays each batch as a CUDA graph, series in page-locked
+    host memory (copied by the library's copy kernel inside the graph): the
+    stream-ordered call gives the blocking call's records, twice in a row
+    (the second replays the updated graph)."""
+    n = 1 << 15
+    xs = _batch(n, 4, seed=30)
+    ids = [4, 2, 8, 6]
+    plan = capi.Plan(n, 64e-6, 16.0, 2.0, 2048, 4, precision=capi.FDAS_BF16, use_graph=True)
+    host = [torch.from_numpy(x).pin_memory() for x in xs]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        st_b, c_b, nf_b = plan.search(host, trial_ids=ids, capacity=1 << 14, stream=stream)
+        assert st_b == capi.FDAS_OK and nf_b == len(c_b) > 0
+        for _ in range(2):
+            cands, nf, st = _outputs(1 << 14, False)
+            plan.search_async(host, cands, nf, st, trial_ids=ids, stream=stream)
+            stream.synchronize()
+            assert int(st.cpu()[0]) == capi.FDAS_OK and int(nf.cpu()[0]) == nf_b
+            assert capi.Plan.candidates(cands, nf_b).tobytes() == c_b.tobytes()
+    plan.close()
