@@ -105,8 +105,9 @@ typedef struct {
     int32_t norm_mode;       /* FDAS_NORM_MEDIAN (default)                          */
     int32_t norm_block;      /* bins per median block, power of 2 in [16, 8192]; 2048 */
     int64_t max_candidates;  /* device candidate store per search call; 1<<20     */
-    int32_t autotune;        /* 1: pick seg_len (among 2048, 4096, 8192 and the one
-                                asked for) and the template chunking by timing the
+    int32_t autotune;        /* 1: pick the correlator, seg_len (among 2048, 4096,
+                                8192 and the one asked for) and the template chunking,
+                                or the tensor-core template order, by timing the
                                 correlation at plan creation; 0 (default): as given */
     int32_t use_graph;       /* 1: fdas_search captures each batch's launches into
                                 one CUDA graph and replays it (device or pinned
@@ -186,10 +187,13 @@ void fdas_opts_default(fdas_opts *opts);
  * n_samples: power of 2 in [2^10, 2^24]. tsamp: sampling time in s (> 0,
  * informational). z_max >= 0, z_step > 0 with z_max/z_step an integer and
  * n_z <= 65535. seg_len: power of 2 in [1024, 16384], larger than
- * 2*m_overlap + 64 where m_overlap = m(z_max) rounded up to a multiple of 8.
+ * 2*m_overlap + 64 where m_overlap = m(z_max) rounded up to a multiple of 8;
+ * 16384 only with the tensor-core correlation, whose direct sum has no
+ * segments (FDAS_ERR_UNSUPPORTED for the overlap-save correlator).
  * n_harm in {1,2,4,8,16,32}.  opts may be NULL (defaults).
  * On success *out owns device memory until fdas_plan_destroy.
- * Errors: FDAS_ERR_ARG, FDAS_ERR_OOM, FDAS_ERR_CUDA (nothing is leaked).
+ * Errors: FDAS_ERR_ARG, FDAS_ERR_UNSUPPORTED, FDAS_ERR_OOM, FDAS_ERR_CUDA
+ * (nothing is leaked).
  * Synchronises the device before returning.
  */
 fdas_status fdas_plan_create(fdas_plan **out, int64_t n_samples, double tsamp,

@@ -360,11 +360,6 @@ static fdas_status create(Plan *&out, int64_t n_samples, double tsamp, double z_
         return arg_error("seg_len must exceed 2*m_overlap + 64 (m_overlap = " +
                          std::to_string(p.m_ov) + ")");
     }
-    if (seg_len > 8192) {
-        delete pp;
-        set_error("seg_len 16384 is accepted by the interface but not built in this version");
-        return FDAS_ERR_UNSUPPORTED;
-    }
     p.V = p.L - 2 * p.m_ov;
     set_length(p, n_samples);
     p.use_graph = o->use_graph != 0;
@@ -404,6 +399,15 @@ static fdas_status create(Plan *&out, int64_t n_samples, double tsamp, double z_
                                                     : "correlator FDAS_CORR_TENSOR: ") + why);
         }
         p.correlator = (o->correlator != FDAS_CORR_FFT && tc_ok) ? FDAS_CORR_TENSOR : FDAS_CORR_FFT;
+        // the overlap-save kernels go up to 8192-point segments; the
+        // tensor-core correlation has no segments (seg_len only sizes the
+        // frequency-domain template bank), so it takes 16384 as well
+        if (seg_len > 8192 && p.correlator != FDAS_CORR_TENSOR) {
+            delete pp;
+            set_error("seg_len 16384 needs the tensor-core correlation (FDAS_BF16 or FDAS_FP16 "
+                      "storage); the overlap-save correlator goes up to 8192");
+            return FDAS_ERR_UNSUPPORTED;
+        }
         if (p.correlator != FDAS_CORR_TENSOR) {
             tc_table.clear();
             p.tc_n_ch = 0;

@@ -219,6 +219,26 @@ def test_tensor_plane_matches_direct_correlation(capi, n, z_max, z_step, prec, o
     plan.close()
 
 
+def test_longest_segment_needs_the_tensor_cores(capi):
+    """seg_len 16384: a tensor-core plan (no segments in its direct sum)
+    searches exactly like one with 8192-bin segments; the overlap-save
+    correlator does not take it."""
+    n = 1 << 17
+    x = torch.from_numpy(S.sinusoid_series()).cuda()
+    res = []
+    for L in (8192, 16384):
+        plan = _plan(capi, n, 16.0, 2.0, L, 4, precision=capi.FDAS_BF16)
+        assert plan.info.seg_len == L and plan.info.correlator == capi.FDAS_CORR_TENSOR
+        st, c, nf = plan.search([x])
+        assert st == capi.FDAS_OK and nf > 0
+        res.append(c.tobytes())
+        plan.close()
+    assert res[0] == res[1]
+    with pytest.raises(capi.FdasError) as ei:
+        _plan(capi, n, 16.0, 2.0, 16384, 4, precision=capi.FDAS_FP32)
+    assert ei.value.status == capi.FDAS_ERR_UNSUPPORTED
+
+
 @pytest.mark.parametrize("n,z_max,z_step", [
     (1 << 10, 2.0, 1.0),        # one 512-bin tile
     (1 << 14, 7.5, 0.5),        # half-step grid, ragged last chunk
