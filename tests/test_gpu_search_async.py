@@ -205,3 +205,23 @@ def test_async_with_graph_replay_and_host_series(capi):
             assert int(st.cpu()[0]) == capi.FDAS_OK and int(nf.cpu()[0]) == nf_b
             assert capi.Plan.candidates(cands, nf_b).tobytes() == c_b.tobytes()
     plan.close()
+
+
+def test_async_under_host_fault_injection(capi, monkeypatch):
+    """FDAS_FAULT=capacity (a one-record store) and nan_input reach the
+    stream-ordered call's device-side status like the blocking call's."""
+    n = 1 << 14
+    x = torch.from_numpy(_batch(n, 1, seed=50)[0]).cuda()
+    plan = capi.Plan(n, 64e-6, 8.0, 2.0, 2048, 2)
+    st0, c0, nf0 = plan.search([x], capacity=256)
+    assert st0 == capi.FDAS_OK and nf0 > 1
+    monkeypatch.setenv("FDAS_FAULT", "capacity")
+    st, c, nf = _run_async(capi, plan, [x], None, 256)
+    assert st == capi.FDAS_ERR_CAND_STORE_FULL and nf == nf0 and len(c) == 0
+    monkeypatch.setenv("FDAS_FAULT", "nan_input")
+    st, c, nf = _run_async(capi, plan, [x], None, 256)
+    assert st == capi.FDAS_ERR_NONFINITE and nf == 0
+    monkeypatch.delenv("FDAS_FAULT")
+    st, c, nf = _run_async(capi, plan, [x], None, 256)
+    assert st == capi.FDAS_OK and c.tobytes() == c0.tobytes()
+    plan.close()
