@@ -46,8 +46,11 @@ typedef enum {
     FDAS_ERR_NONFINITE = 5,      /* NaN or Inf in an input series           */
     FDAS_ERR_TIMEOUT = 6,        /* a bounded device wait gave up            */
     FDAS_ERR_UNSUPPORTED = 7,    /* valid request the library does not serve */
-    FDAS_ERR_CAND_STORE_FULL = 8 /* more crossings than the plan's device
+    FDAS_ERR_CAND_STORE_FULL = 8, /* more crossings than the plan's device
                                     store (fdas_opts.max_candidates)         */
+    FDAS_ERR_BOUNDS = 9          /* checked build only: a device bounds check
+                                    failed or a workspace canary was
+                                    overwritten (see fdas_checked_build)     */
 } fdas_status;
 
 /* storage precision of spectra, templates and the power plane; the
@@ -567,10 +570,45 @@ fdas_status fdas_dedisperse_u8(fdas_dedisp_plan *plan, const uint8_t *filterbank
  *   "nan_input" fdas_search / fdas_threshold report FDAS_ERR_NONFINITE after
  *               the search, as for a series holding NaN or Inf;
  *   "bad_args"  fdas_plan_create and fdas_search return FDAS_ERR_ARG before
- *               doing anything.
+ *               doing anything;
+ *   "canary"    (checked build) fdas_search / fdas_search_async write one
+ *               byte of the canary guard that follows the plan's power plane,
+ *               inside its allocation, after the first correlation: the
+ *               call returns FDAS_ERR_BOUNDS naming the buffer;
+ *   "bounds"    (checked build) every device bounds limit is one element
+ *               lower during fdas_search / fdas_search_async, so that checks
+ *               fail at real sites (the accesses they skip were in bounds):
+ *               FDAS_ERR_BOUNDS naming the first site.
+ * "canary" and "bounds" in an ordinary build: FDAS_ERR_UNSUPPORTED.
  * Unset or empty: no fault.  Any other value: the calls above return
  * FDAS_ERR_ARG naming the value.
  * --------------------------------------------------------------------- */
+
+/* ---------------------------------------------------------------------
+ * Checked build (no counterpart in the paper): the same sources compiled
+ * with -DFDAS_CHECK_BOUNDS into libfdas_checked.so, the same entry points.
+ *  - Device bounds checks at the data-dependent accesses of the harmonic
+ *    sums (span copies, top-row loads, sums stores, the gathered rows of the
+ *    fundamental-indexed sum), of the tensor-core correlation (template
+ *    image and spectrum window copies, the MMA rows inside the window,
+ *    plane / F / edge stores) and of the candidate ordering.  A failed check
+ *    records itself and skips its access; nothing traps.
+ *  - Every device buffer of a search plan lies between two 256-byte guards
+ *    of canary bytes (fdas_plan_info.workspace_bytes counts the buffers
+ *    only).
+ *  - After each launch group (the spectrum, correlation and harmonic sum of
+ *    each series, the candidate ordering, plan creation and each stage
+ *    entry point) the call waits for the device and returns FDAS_ERR_BOUNDS
+ *    on the first failed check or overwritten guard byte, with
+ *    fdas_last_error() naming the launch group, the site (or buffer) and the
+ *    range.  Every call is therefore blocking, fdas_search_async included,
+ *    and graph replay is checked after the whole graph.
+ * It is a debugging build: slower, and its logs are per process (two plans
+ * used at once from two threads may see each other's failures).
+ * --------------------------------------------------------------------- */
+
+/* 1 when this library is the checked build, else 0. */
+int32_t fdas_checked_build(void);
 
 /* Thread-local message describing the last failed call ("" if none). */
 const char *fdas_last_error(void);

@@ -2,7 +2,10 @@
 
 Each .cu under csrc/ is compiled to an object in parallel, then linked into
 paper_2211_13517_gb300/_build/libfdas.so.  Objects are rebuilt when their
-source or any header is newer.
+source or any header is newer.  build(checked=True) compiles the same sources
+with -DFDAS_CHECK_BOUNDS into _build/checked/ and links
+_build/libfdas_checked.so (device bounds checks and workspace canaries; see
+include/fdas.h).
 """
 from __future__ import annotations
 
@@ -17,6 +20,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfdas.so")
+BUILD_CHECKED = os.path.join(BUILD, "checked")
+LIB_CHECKED = os.path.join(BUILD, "libfdas_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-Xptxas", "-v"]
@@ -40,8 +45,8 @@ def _stale(obj: str, src: str) -> bool:
     return any(os.path.getmtime(f) > t for f in [src] + _headers())
 
 
-def _compile(nvcc: str, src: str, obj: str, verbose: bool) -> str:
-    cmd = [nvcc, *ARCH, *FLAGS, "-c", src, "-o", obj + ".tmp"]
+def _compile(nvcc: str, src: str, obj: str, verbose: bool, extra=()) -> str:
+    cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj + ".tmp"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
@@ -49,31 +54,33 @@ def _compile(nvcc: str, src: str, obj: str, verbose: bool) -> str:
     return r.stderr if verbose else ""
 
 
-def build(verbose: bool = False, force: bool = False) -> str:
-    """Compile csrc/*.cu for sm_103a and link _build/libfdas.so; return its path."""
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose: bool = False, force: bool = False, checked: bool = False) -> str:
+    """Compile csrc/*.cu for sm_103a and link _build/libfdas.so (checked:
+    _build/libfdas_checked.so, with -DFDAS_CHECK_BOUNDS); return its path."""
+    out_dir, lib = (BUILD_CHECKED, LIB_CHECKED) if checked else (BUILD, LIB)
+    extra = ["-DFDAS_CHECK_BOUNDS"] if checked else []
+    os.makedirs(out_dir, exist_ok=True)
     nvcc = _nvcc()
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
-    objs = [os.path.join(BUILD, os.path.basename(s)[:-3] + ".o") for s in srcs]
+    objs = [os.path.join(out_dir, os.path.basename(s)[:-3] + ".o") for s in srcs]
     todo = [(s, o) for s, o in zip(srcs, objs) if force or _stale(o, s)]
     logs = []
     if todo:
         with cf.ThreadPoolExecutor(max_workers=min(len(todo), os.cpu_count() or 4)) as ex:
-            for log in ex.map(lambda so: _compile(nvcc, so[0], so[1], verbose), todo):
+            for log in ex.map(lambda so: _compile(nvcc, so[0], so[1], verbose, extra), todo):
                 logs.append(log)
-    if todo or not os.path.exists(LIB):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if todo or not os.path.exists(lib):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-        os.replace(tmp, LIB)
+        os.replace(tmp, lib)
     if verbose:
         print("".join(logs))
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":
     import sys
-    build(verbose="-v" in sys.argv, force="-f" in sys.argv)
-    print(LIB)
+    print(build(verbose="-v" in sys.argv, force="-f" in sys.argv, checked="--checked" in sys.argv))

@@ -8,6 +8,11 @@ fallback.
 
 `Plan` is a small convenience wrapper that takes torch tensors (device memory
 and streams only) and calls the same entry points.
+
+With FDAS_CHECKED=1 in the environment when the library is first loaded,
+`lib()` loads the checked build (libfdas_checked.so, built by
+build.build(checked=True)) instead: the same entry points with device bounds
+checks and workspace canaries (include/fdas.h, "Checked build").
 """
 from __future__ import annotations
 
@@ -18,7 +23,7 @@ from ctypes import (POINTER, Structure, c_char_p, c_double, c_int32, c_int64,
 
 import numpy as np
 
-from .build import LIB
+from .build import LIB, LIB_CHECKED
 
 FDAS_OK = 0
 FDAS_ERR_ARG = 1
@@ -29,10 +34,11 @@ FDAS_ERR_NONFINITE = 5
 FDAS_ERR_TIMEOUT = 6
 FDAS_ERR_UNSUPPORTED = 7
 FDAS_ERR_CAND_STORE_FULL = 8
+FDAS_ERR_BOUNDS = 9
 STATUS_NAMES = {0: "FDAS_OK", 1: "FDAS_ERR_ARG", 2: "FDAS_ERR_CUDA", 3: "FDAS_ERR_OOM",
                 4: "FDAS_ERR_CAND_OVERFLOW", 5: "FDAS_ERR_NONFINITE",
                 6: "FDAS_ERR_TIMEOUT", 7: "FDAS_ERR_UNSUPPORTED",
-                8: "FDAS_ERR_CAND_STORE_FULL"}
+                8: "FDAS_ERR_CAND_STORE_FULL", 9: "FDAS_ERR_BOUNDS"}
 # statuses fdas_search / fdas_threshold return (not raise): the call ran and
 # *n_found holds the true number of crossings
 COUNT_STATUSES = (FDAS_ERR_CAND_OVERFLOW, FDAS_ERR_CAND_STORE_FULL)
@@ -52,6 +58,7 @@ EXPORTED = ["fdas_opts_default", "fdas_plan_create", "fdas_plan_destroy",
             "fdas_spectrum_static", "fdas_fourier_power", "fdas_fourier_power_backward",
             "fdas_refine", "fdas_profile_enable", "fdas_profile_read",
             "fdas_selftest_wait_timeout", "fdas_last_error", "fdas_version",
+            "fdas_checked_build",
             "fdas_dedisp_plan_create", "fdas_dedisp_plan_destroy", "fdas_dedisp_get_info",
             "fdas_dedisp_delays", "fdas_dedisperse", "fdas_dedisperse_u8"]
 
@@ -134,14 +141,22 @@ class FdasError(RuntimeError):
 _lib = None
 
 
+def lib_path() -> str:
+    """The library lib() loads: the checked build when FDAS_CHECKED=1."""
+    return LIB_CHECKED if os.environ.get("FDAS_CHECKED") == "1" else LIB
+
+
 def lib() -> ctypes.CDLL:
-    """Load libfdas.so (built in-tree by build.build()); raise if absent."""
+    """Load libfdas.so (built in-tree by build.build()), or libfdas_checked.so
+    with FDAS_CHECKED=1; raise if absent."""
     global _lib
     if _lib is None:
-        if not os.path.exists(LIB):
-            raise RuntimeError(f"libfdas.so is not built ({LIB}); run "
-                               "paper_2211_13517_gb300.build.build() first")
-        L = ctypes.CDLL(LIB)
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"{os.path.basename(path)} is not built ({path}); run "
+                               "paper_2211_13517_gb300.build.build("
+                               f"{'checked=True' if path == LIB_CHECKED else ''}) first")
+        L = ctypes.CDLL(path)
         L.fdas_opts_default.argtypes = [POINTER(fdas_opts)]
         L.fdas_opts_default.restype = None
         L.fdas_plan_create.argtypes = [POINTER(c_void_p), c_int64, c_double, c_double,
@@ -206,6 +221,8 @@ def lib() -> ctypes.CDLL:
         L.fdas_last_error.restype = c_char_p
         L.fdas_version.argtypes = []
         L.fdas_version.restype = c_char_p
+        L.fdas_checked_build.argtypes = []
+        L.fdas_checked_build.restype = c_int32
         _lib = L
     return _lib
 
@@ -368,6 +385,10 @@ def fdas_last_error() -> str:
 
 def fdas_version() -> str:
     return lib().fdas_version().decode()
+
+
+def fdas_checked_build() -> bool:
+    return lib().fdas_checked_build() == 1
 
 
 # ----------------------------------------------------------------------------

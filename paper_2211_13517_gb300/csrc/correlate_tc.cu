@@ -50,6 +50,7 @@
 #include "fdas_internal.cuh"
 #include "tcgen05.cuh"
 #include "tma.cuh"
+#include "check.cuh"
 
 namespace fdas {
 
@@ -121,7 +122,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         void *__restrict__ out, double2 *__restrict__ partials,
                         int64_t n_r, int win_bytes, int b_bytes_max, int nbuf,
                         unsigned int *flags,
-                        float4 *__restrict__ edges) {
+                        float4 *__restrict__ edges FDAS_BC_PARAM) {
     constexpr bool kSplit = P::id == FDAS_FP32;
     constexpr int kStages = kSplit ? 2 : kTcStages;
     constexpr int kParts = kSplit ? 2 : 1;   // hi (+ lo) operand images
@@ -185,11 +186,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     }
                     const unsigned bytes = (unsigned)chunks[c].ks * kTcSlab;
                     unsigned char *const dstB = sB + bb * b_stride;
-                    mbar_arrive_expect_tx(&b_full[bb], kParts * bytes);
-                    bulk_copy_g2s(dstB, bank_img + chunks[c].b_off, bytes, &b_full[bb]);
-                    if constexpr (kSplit)
-                        bulk_copy_g2s(dstB + b_bytes_max, bank_img + b_lo + chunks[c].b_off, bytes,
-                                      &b_full[bb]);
+                    if (FDAS_IN_BOUNDS(0, bytes, b_bytes_max, kSiteTcImageSmem) &&
+                        FDAS_IN_BOUNDS(chunks[c].b_off, bytes, kSplit ? b_lo : bc.lim[0],
+                                       kSiteTcImageCopy) &&
+                        (!kSplit || FDAS_IN_BOUNDS(b_lo + chunks[c].b_off, bytes, bc.lim[0],
+                                                   kSiteTcImageCopy))) {
+                        mbar_arrive_expect_tx(&b_full[bb], kParts * bytes);
+                        bulk_copy_g2s(dstB, bank_img + chunks[c].b_off, bytes, &b_full[bb]);
+                        if constexpr (kSplit)
+                            bulk_copy_g2s(dstB + b_bytes_max, bank_img + b_lo + chunks[c].b_off,
+                                          bytes, &b_full[bb]);
+                    } else {
+                        mbar_arrive(&b_full[bb]);   // checked build: the copy is skipped
+                    }
                     cur = c;
                 }
                 const int s = j % kStages;
@@ -200,10 +209,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 // a window of 16-bit (re, im) pairs: 4 bytes per complex value
                 const int64_t a_off = t * kTcTile * 4;
                 unsigned char *const dstA = sA + s * kParts * win_bytes;
-                mbar_arrive_expect_tx(&a_full[s], (unsigned)(kParts * win_bytes));
-                bulk_copy_g2s(dstA, spec_a + a_off, (unsigned)win_bytes, &a_full[s]);
-                if constexpr (kSplit)
-                    bulk_copy_g2s(dstA + win_bytes, spec_lo + a_off, (unsigned)win_bytes, &a_full[s]);
+                if (FDAS_IN_BOUNDS(a_off, win_bytes, bc.lim[1], kSiteTcWindowCopy)) {
+                    mbar_arrive_expect_tx(&a_full[s], (unsigned)(kParts * win_bytes));
+                    bulk_copy_g2s(dstA, spec_a + a_off, (unsigned)win_bytes, &a_full[s]);
+                    if constexpr (kSplit)
+                        bulk_copy_g2s(dstA + win_bytes, spec_lo + a_off, (unsigned)win_bytes,
+                                      &a_full[s]);
+                } else {
+                    mbar_arrive(&a_full[s]);   // checked build: the copy is skipped
+                }
                 ++j;
             }
             // every copy issued lands before the CTA can exit (bounded)
@@ -253,7 +267,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 const uint32_t a_addr = smem_u32(sA + s * kParts * win_bytes) + 4u * kofs;
                 const uint64_t adesc = smem_desc(a_addr, 16, 128);
                 const uint64_t adesc_lo = smem_desc(a_addr + (kSplit ? (uint32_t)win_bytes : 0u), 16, 128);
-                for (int k = 0; k < ks; ++k) {
+                // (checked build: no MMA reads past the window or the image)
+                const int kn = FDAS_IN_BOUNDS(kofs, 4 * (kTcRows - 1) + 8 * ks, win_bytes / 4,
+                                              kSiteTcWindowRead) &&
+                                       FDAS_IN_BOUNDS(0, ks * kTcSlab, b_bytes_max, kSiteTcImageSmem)
+                                   ? ks
+                                   : 0;
+                for (int k = 0; k < kn; ++k) {
                     const uint64_t kb = (uint64_t)(kTcSlab >> 4) * k;
                     tc_mma_f16(d, adesc + 2ull * k, bdesc0 + kb, kIdesc, k > 0 ? 1u : 0u);
                     if constexpr (kSplit) {
@@ -297,7 +317,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 zvalid = chunks[c].n_part[part];
 #pragma unroll
                 for (int k = 0; k < kTcZpt; ++k) {
-                    const float ie = k < zvalid ? __ldg(inv_energy + zb + k) : 0.f;
+                    const float ie = k < zvalid && FDAS_IN_BOUNDS(zb + k, 1, bc.lim[2], kSiteTcEnergy)
+                                         ? __ldg(inv_energy + zb + k)
+                                         : 0.f;
                     sc[k] = kMode == kPower ? ie : sqrtf(ie);
                 }
                 if constexpr (kMode == kCplx)
@@ -351,11 +373,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                             // fix-up kernel writes this half bin
                             q23.y = 0.f;
                             const int64_t e = ((int64_t)(zfirst + k) * n_tiles + t) * 4 + quarter;
-                            reinterpret_cast<float2 *>(edges + e)[1] = make_float2(re23.y, im23.y);
+                            if (FDAS_IN_BOUNDS(e, 1, bc.lim[2] * n_tiles * 4, kSiteTcEdgeStore))
+                                reinterpret_cast<float2 *>(edges + e)[1] = make_float2(re23.y, im23.y);
                         }
                         if (lane == 0) {
                             const int64_t e = ((int64_t)(zfirst + k) * n_tiles + t) * 4 + quarter;
-                            reinterpret_cast<float2 *>(edges + e)[0] = make_float2(re01.x, im01.x);
+                            if (FDAS_IN_BOUNDS(e, 1, bc.lim[2] * n_tiles * 4, kSiteTcEdgeStore))
+                                reinterpret_cast<float2 *>(edges + e)[0] = make_float2(re01.x, im01.x);
                         }
                         s1 = __fadd2_rn(s1, __fadd2_rn(__fadd2_rn(p01, p23), __fadd2_rn(q01, q23)));
                         s2 = __ffma2_rn(p01, p01, s2);
@@ -372,14 +396,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         memcpy(&u.y, &w1, 4);
                         memcpy(&u.z, &w2, 4);
                         memcpy(&u.w, &w3, 4);
-                        *reinterpret_cast<uint4 *>(o + (int64_t)k * 2 * n_r) = u;
+                        if (FDAS_IN_BOUNDS((int64_t)(zfirst + k) * 2 * n_r + t * (2 * kTcTile) + 8 * row,
+                                           8, bc.lim[2] * 2 * n_r, kSiteTcPlaneStore))
+                            *reinterpret_cast<uint4 *>(o + (int64_t)k * 2 * n_r) = u;
                     }
                 }
             } else if constexpr (kMode == kCplx) {
                 typename P::cpx *oc = zcrow + t * kTcTile;
 #pragma unroll
                 for (int k = 0; k < kTcZpt; ++k) {
-                    if (k < zvalid) {
+                    if (k < zvalid &&
+                        FDAS_IN_BOUNDS((int64_t)(zfirst + k) * n_r + t * kTcTile + 4 * row, 4,
+                                       bc.lim[2] * n_r, kSiteTcPlaneStore)) {
                         uint32_t w[4];
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
@@ -406,7 +434,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 s1 = __fadd2_rn(s1, __fadd2_rn(p01, p23));
                 s2 = __ffma2_rn(p01, p01, s2);
                 s2 = __ffma2_rn(p23, p23, s2);
-                if (k < zvalid) {
+                if (k < zvalid &&
+                    FDAS_IN_BOUNDS((int64_t)(zfirst + k) * n_r + t * kTcTile + 4 * row, 4,
+                                   bc.lim[2] * n_r, kSiteTcPlaneStore)) {
                     if constexpr (kSplit) {
                         *reinterpret_cast<float4 *>(o + (int64_t)k * n_r) =
                             make_float4(p01.x, p01.y, p23.x, p23.y);
@@ -643,7 +673,8 @@ fdas_status launch_tc_P(Plan &p, const void *spec_padded, void *plane, double2 *
                                       p.tc_n_ch,
                                       p.tc_inv_energy, plane, partials, p.n_r,
                                       p.tc_win * 4,
-                                      p.tc_max_ks * kTcSlab, p.tc_nbuf, p.flags, p.tc_edges);
+                                      p.tc_max_ks * kTcSlab, p.tc_nbuf, p.flags, p.tc_edges
+                                      FDAS_BC_ARG(p.tc_img_bytes, 4 * p.spec_pad_elems, p.n_z));
     FDAS_CUDA_TRY(cudaGetLastError());
     if constexpr (kMode == kInterbin) {
         tc_ib_fixup_kernel<P><<<tc_ib_fixup_ctas(p), 256, 0, s>>>(
@@ -825,5 +856,7 @@ fdas_status launch_interbin_tc(Plan &p, const void *spec_padded, void *plane, do
 int interbin_tc_partials(const Plan &p) { return correlate_tc_ctas(p) + tc_ib_fixup_ctas(p); }
 
 int64_t tc_edge_bytes(const Plan &p) { return (int64_t)p.n_z * (p.n_r / kTcTile) * 4 * (int64_t)sizeof(float4); }
+
+FDAS_BOUNDS_LOG_TU(correlate_tc)
 
 }  // namespace fdas

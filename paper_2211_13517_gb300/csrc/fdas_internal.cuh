@@ -189,6 +189,7 @@ struct Plan {
     // the hi one, the spectrum parts in spec_hi / spec_lo (padded like spec_pad)
     bool tc_split = false;
     int64_t tc_bank_lo = 0;
+    int64_t tc_img_bytes = 0;         // bytes of tc_bank (both parts in split mode)
     void *spec_hi = nullptr, *spec_lo = nullptr;
     int64_t tc_split_elems = 0;
     int tc_n_ch = 0, tc_max_ks = 0, tc_win = 0;
@@ -208,6 +209,7 @@ struct Plan {
     int64_t n_taps = 0;
     float2 *fft_a = nullptr, *fft_b = nullptr;   // [M] scratch each
     void *spec_pad = nullptr;       // [n_seg*V + 2 m_ov] cpx, zero-padded
+    int64_t spec_pad_elems = 0;     // complex elements of spec_pad (and of spec_hi / spec_lo)
     void *plane[2] = {nullptr, nullptr};   // [n_z][plane_cols] real
     void *corr = nullptr;           // interbinning: [n_z][n_r] complex F
     double2 *partials[2] = {nullptr, nullptr};   // per correlation CTA
@@ -231,6 +233,15 @@ struct Plan {
     fdas_refined *ref_out = nullptr;       // device staging of refine results
     int64_t ref_cap = 0;
     int64_t ws_bytes = 0;
+    // checked builds: each device buffer of the plan sits between two guards
+    // of canary bytes (base .. base + guard, then after its `bytes`)
+    struct GuardedBuf {
+        char *base;
+        size_t bytes;
+        const char *name;
+    };
+    std::vector<GuardedBuf> guards;
+    bool plant_canary = false;        // FDAS_FAULT=canary for the batch being queued
     // tracing
     bool profiling = false;
     int64_t prof_trials = 0;

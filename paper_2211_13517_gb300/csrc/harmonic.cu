@@ -16,6 +16,7 @@
 #include "fdas_internal.cuh"
 #include "fft_cta.cuh"   // cadd
 #include "tma.cuh"
+#include "check.cuh"
 
 #include <cstring>
 
@@ -356,7 +357,8 @@ struct DedupSteps {
     // arrival per barrier follows
     __device__ __forceinline__ static void copy_lane(const Lane &L, const real *__restrict__ plane,
                                                      int iz0, int o, int64_t n_r, int64_t B,
-                                                     bool first, real *sm, uint64_t *bars) {
+                                                     bool first, real *sm, uint64_t *bars,
+                                                     int n_z) {
         if (L.j == 0) return;
         if (!first && src_off(H, o, L.j) == src_off(H, o - 1, L.j)) return;
         // the span, but never past the last bin of the source row that a cell
@@ -369,6 +371,9 @@ struct DedupSteps {
         const unsigned bytes = (unsigned)(n * (int64_t)sizeof(real));
         if (bytes == 0) return;
         const int64_t row = iz0 + src_off(H, o, L.j);
+        if (!FDAS_IN_BOUNDS(row, 1, n_z, kSiteHsSpanRow) ||
+            !FDAS_IN_BOUNDS((int64_t)L.j * B / H, n, n_r, kSiteHsSpanRange))
+            return;
         fence_proxy_async_smem();
         mbar_expect_tx(&bars[L.g], bytes);
         bulk_copy_g2s(sm + L.off, plane + row * n_r + (int64_t)L.j * B / H, bytes, &bars[L.g]);
@@ -496,7 +501,9 @@ __global__ void __launch_bounds__(Dedup<P, H>::T, 7)
     int q = 0;
     uint32_t tv[8];   // 16-bit planes: the thread's top-row cells, one row ahead
     if constexpr (D::kTopRegs)
-        if (active && iz_begin < iz_end) Steps::load_top(plane + (int64_t)iz_begin * n_r + b, tv);
+        if (active && iz_begin < iz_end &&
+            FDAS_IN_BOUNDS((int64_t)iz_begin * n_r + b, D::R, (int64_t)n_z * n_r, kSiteHsTopLoad))
+            Steps::load_top(plane + (int64_t)iz_begin * n_r + b, tv);
     for (int iz = iz_begin; iz < iz_end; ++iz, ++q) {
         // every thread is done with the previous row's spans (and, for the
         // first row, the barriers are initialised); stop together after a
@@ -510,7 +517,7 @@ __global__ void __launch_bounds__(Dedup<P, H>::T, 7)
             // (their reads by this CTA's threads come before the copies),
             // then one arrival per stage barrier (none on the unused barrier
             // of a top row held in registers)
-            Steps::copy_lane(lane_sp, plane, iz0, iz - iz0, n_r, B, q == 0, sm, bars);
+            Steps::copy_lane(lane_sp, plane, iz0, iz - iz0, n_r, B, q == 0, sm, bars, n_z);
             __syncwarp();
             if (t < Steps::NG && !(t == 0 && D::kTopRegs)) mbar_arrive(&bars[t]);
         }
@@ -518,10 +525,17 @@ __global__ void __launch_bounds__(Dedup<P, H>::T, 7)
         float2 S2[D::R / 2];
 #pragma unroll
         for (int c = 0; c < D::R / 2; ++c) S2[c] = make_float2(0.f, 0.f);
-        const real *next_top = iz + 1 < iz_end ? plane + (int64_t)(iz + 1) * n_r + b : nullptr;
+        const real *next_top =
+            iz + 1 < iz_end && FDAS_IN_BOUNDS((int64_t)(iz + 1) * n_r + b, D::R,
+                                              (int64_t)n_z * n_r, kSiteHsTopLoad)
+                ? plane + (int64_t)(iz + 1) * n_r + b
+                : nullptr;
         const bool ok = Steps::template sums<0>(sm, bars, (unsigned)(q & 1), t, S2,
                                                 [&](int s, float2 (&Sv)[D::R / 2]) {
             if constexpr (kWriteSums) {
+                if (!FDAS_IN_BOUNDS(((int64_t)s * n_z + iz) * n_r + b, D::R,
+                                    (int64_t)(ilog2h(H) + 1) * n_z * n_r, kSiteHsSumsStore))
+                    return;
 #pragma unroll
                 for (int c = 0; c < D::R / 2; ++c) {
                     float *o = sums_out + ((int64_t)s * n_z + iz) * n_r + b + 2 * c;
@@ -605,7 +619,8 @@ __device__ __forceinline__ int64_t sort_count(const int64_t *n_dev, int64_t n_ho
 // global steps j >= C of that stage, on the chunk as it stands (records
 // and padding have moved by then).
 __global__ void __launch_bounds__(kSortThreads) sort_chunk_kernel(CandRec *rec, const int64_t *n_dev,
-                                                                  int64_t n_host, int64_t merge_k) {
+                                                                  int64_t n_host, int64_t merge_k
+                                                                  FDAS_BC_PARAM) {
     extern __shared__ CandRec sh[];
     const int64_t n = sort_count(n_dev, n_host);
     if (n <= 0) return;
@@ -614,6 +629,7 @@ __global__ void __launch_bounds__(kSortThreads) sort_chunk_kernel(CandRec *rec, 
     const int64_t base = (int64_t)blockIdx.x * kSortChunk;
     if (base >= n2) return;
     const int len = (int)(n2 < kSortChunk ? n2 : kSortChunk);
+    if (!FDAS_IN_BOUNDS(base, len, bc.lim[0], kSiteSortRecord)) return;
     const int tid = threadIdx.x;
     for (int i = tid; i < len; i += kSortThreads) {
         if (merge_k > 0 || base + i < n) {
@@ -651,7 +667,7 @@ __global__ void __launch_bounds__(kSortThreads) sort_chunk_kernel(CandRec *rec, 
 // one global compare-exchange step (k, j >= C) over the padded array
 // (grid-stride; nothing to do unless C < n2 and k <= n2)
 __global__ void bitonic_global_kernel(CandRec *rec, const int64_t *n_dev, int64_t n_host, int64_t k,
-                                      int64_t j) {
+                                      int64_t j FDAS_BC_PARAM) {
     const int64_t n = sort_count(n_dev, n_host);
     if (n <= 0) return;
     const int64_t n2 = pow2_at_least(n);
@@ -660,6 +676,7 @@ __global__ void bitonic_global_kernel(CandRec *rec, const int64_t *n_dev, int64_
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t ixj = i ^ j;
         if (ixj <= i) continue;
+        if (!FDAS_IN_BOUNDS(ixj, 1, bc.lim[0], kSiteSortRecord)) continue;
         const bool up = (i & k) == 0;
         const CandRec a = rec[i], b = rec[ixj];
         if (rec_less(b, a) == up) {
@@ -881,17 +898,19 @@ __device__ __forceinline__ void fund_add_run(const typename P::real *row, int64_
 template <class P, int KLO, int KHI>
 __device__ __forceinline__ void fund_add_stage(const typename P::real *plane, int64_t n_r,
                                                int iz0, int o, int64_t a, bool full, int h,
-                                               float (&S)[kFundR]) {
+                                               float (&S)[kFundR], int n_z) {
     if constexpr (KLO <= KHI) {
         const typename P::real *row = plane + (int64_t)(iz0 + KLO * o) * n_r;
-        if (full) {
-            fund_add_run<P, KLO>(row, a, S);
+        if (!FDAS_IN_BOUNDS(iz0 + KLO * o, 1, n_z, kSiteFundRow)) {
+        } else if (full) {
+            if (FDAS_IN_BOUNDS((int64_t)KLO * a, KLO * kFundR, n_r, kSiteFundRun))
+                fund_add_run<P, KLO>(row, a, S);
         } else {
 #pragma unroll
             for (int i = 0; i < kFundR; ++i)
                 if ((a + i) * h <= n_r - 1) S[i] += P::ldr(row[(int64_t)KLO * (a + i)]);
         }
-        fund_add_stage<P, KLO + 1, KHI>(plane, n_r, iz0, o, a, full, h, S);
+        fund_add_stage<P, KLO + 1, KHI>(plane, n_r, iz0, o, a, full, h, S, n_z);
     }
 }
 
@@ -905,7 +924,7 @@ __device__ __forceinline__ bool fund_stages(const typename P::real *plane, int64
             const int top = iz0 + h * o;
             if (top < 0 || top >= n_z || a * h > n_r - 1) return true;
             const bool full = (a + kFundR) * h <= n_r;
-            fund_add_stage<P, h / 2 + 1, h>(plane, n_r, iz0, o, a, full, h, S);
+            fund_add_stage<P, h / 2 + 1, h>(plane, n_r, iz0, o, a, full, h, S, n_z);
         }
 #pragma unroll
         for (int i = 0; i < kFundR; ++i)
@@ -1041,19 +1060,20 @@ static fdas_status launch_sort(Plan &p, int64_t n, const int64_t *n_dev, int64_t
     const int64_t len = std::min<int64_t>(n2, kSortChunk);
     const unsigned chunks = (unsigned)((n2 + kSortChunk - 1) / kSortChunk);
     const size_t smem = sizeof(CandRec) * (size_t)len;
+    [[maybe_unused]] const int64_t rec_cap = pow2_at_least(p.max_cands);   // records p.cand holds
     FDAS_CUDA_TRY(cudaFuncSetAttribute(sort_chunk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)(sizeof(CandRec) * kSortChunk)));
-    sort_chunk_kernel<<<chunks, kSortThreads, smem, s>>>(p.cand, n_dev, n, 0);
+    sort_chunk_kernel<<<chunks, kSortThreads, smem, s>>>(p.cand, n_dev, n, 0 FDAS_BC_ARG(rec_cap));
     FDAS_CUDA_TRY(cudaGetLastError());
     p.launches[FDAS_PROF_FINISH] += 1;
     const unsigned gb = (unsigned)std::min<int64_t>((n2 + 255) / 256, 152 * 16);
     for (int64_t k = 2 * (int64_t)kSortChunk; k <= n2; k <<= 1) {
         for (int64_t j = k >> 1; j >= kSortChunk; j >>= 1) {
-            bitonic_global_kernel<<<gb, 256, 0, s>>>(p.cand, n_dev, n, k, j);
+            bitonic_global_kernel<<<gb, 256, 0, s>>>(p.cand, n_dev, n, k, j FDAS_BC_ARG(rec_cap));
             FDAS_CUDA_TRY(cudaGetLastError());
             p.launches[FDAS_PROF_FINISH] += 1;
         }
-        sort_chunk_kernel<<<chunks, kSortThreads, smem, s>>>(p.cand, n_dev, n, k);
+        sort_chunk_kernel<<<chunks, kSortThreads, smem, s>>>(p.cand, n_dev, n, k FDAS_BC_ARG(rec_cap));
         FDAS_CUDA_TRY(cudaGetLastError());
         p.launches[FDAS_PROF_FINISH] += 1;
     }
@@ -1089,5 +1109,7 @@ fdas_status launch_candidates_finish_async(Plan &p, int64_t capacity, unsigned i
     }
     return FDAS_OK;
 }
+
+FDAS_BOUNDS_LOG_TU(harmonic)
 
 }  // namespace fdas

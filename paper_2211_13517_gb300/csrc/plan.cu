@@ -1,6 +1,7 @@
 // C ABI of the FDAS library: plan construction, the search driver and the
 // stage entry points (declared in include/fdas.h).
 #include "fdas_internal.cuh"
+#include "check.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -29,11 +30,22 @@ static fdas_status arg_error(const std::string &msg) {
 
 // ---------------------------------------------------------------------------
 // host-side fault injection: FDAS_FAULT = alloc[:N] | capacity | nan_input |
-// bad_args, read at every call (semantics in include/fdas.h).  Nothing is
-// injected on the device: each fault makes the host take the error path the
-// real failure would take.
+// bad_args, and in checked builds canary | bounds, read at every call
+// (semantics in include/fdas.h).  Nothing is injected on the device: each
+// fault makes the host take the error path the real failure would take, or
+// (canary, bounds) writes one byte inside a guard or lowers the device
+// bounds limits, both inside the allocations.
 // ---------------------------------------------------------------------------
-enum { kFaultNone = 0, kFaultAlloc, kFaultCapacity, kFaultNan, kFaultArgs, kFaultUnknown };
+enum {
+    kFaultNone = 0,
+    kFaultAlloc,
+    kFaultCapacity,
+    kFaultNan,
+    kFaultArgs,
+    kFaultCanary,
+    kFaultBounds,
+    kFaultUnknown
+};
 
 struct Fault {
     int kind = kFaultNone;
@@ -56,18 +68,30 @@ static Fault injected_fault() {
         f.kind = kFaultNan;
     } else if (std::strcmp(s, "bad_args") == 0) {
         f.kind = kFaultArgs;
+    } else if (std::strcmp(s, "canary") == 0) {
+        f.kind = kFaultCanary;
+    } else if (std::strcmp(s, "bounds") == 0) {
+        f.kind = kFaultBounds;
     } else {
         f.kind = kFaultUnknown;
     }
     return f;
 }
 
-// FDAS_ERR_ARG for the bad_args fault and for an unknown FDAS_FAULT value
+// FDAS_ERR_ARG for the bad_args fault and for an unknown FDAS_FAULT value;
+// FDAS_ERR_UNSUPPORTED for the faults of checked builds in an ordinary one
 static fdas_status fault_args_check(const Fault &f) {
     if (f.kind == kFaultArgs) return arg_error("injected fault (FDAS_FAULT=bad_args)");
     if (f.kind == kFaultUnknown)
         return arg_error("FDAS_FAULT=" + f.text +
-                         ": unknown fault (alloc[:N] with N >= 1, capacity, nan_input, bad_args)");
+                         ": unknown fault (alloc[:N] with N >= 1, capacity, nan_input, bad_args, "
+                         "canary, bounds)");
+#ifndef FDAS_CHECK_BOUNDS
+    if (f.kind == kFaultCanary || f.kind == kFaultBounds) {
+        set_error("FDAS_FAULT=" + f.text + " needs the checked build (libfdas_checked.so)");
+        return FDAS_ERR_UNSUPPORTED;
+    }
+#endif
     return FDAS_OK;
 }
 
@@ -110,46 +134,96 @@ static int ilog2(int64_t v) {
     return l;
 }
 
+// ---------------------------------------------------------------------------
+// checked builds (-DFDAS_CHECK_BOUNDS): every device buffer of a plan is
+// allocated with kGuardBytes of canary bytes on each side.  After each launch
+// group the library waits for the device and reads the device bounds logs of
+// the checked kernels (check.cuh) and every guard; the first failure is
+// reported as FDAS_ERR_BOUNDS, naming the launch group, and the logs and
+// guards are reset.
+// ---------------------------------------------------------------------------
+#ifdef FDAS_CHECK_BOUNDS
+constexpr size_t kGuardBytes = 256;   // each side: the buffer keeps 256-byte alignment
+constexpr unsigned char kCanary = 0xA5;
+
+cudaError_t bounds_take_harmonic(BoundsLog *out);
+cudaError_t bounds_arm_harmonic(int64_t shrink);
+cudaError_t bounds_take_correlate_tc(BoundsLog *out);
+cudaError_t bounds_arm_correlate_tc(int64_t shrink);
+
+struct GuardDesc {
+    const unsigned char *lo, *hi;   // the kGuardBytes before and after a buffer
+};
+
+// one CTA per buffer: the smallest (buffer, guard byte) whose byte is not
+// the canary, guard bytes counted from the start of the one before the buffer
+__global__ void canary_check_kernel(const GuardDesc *g, int n, unsigned long long *first) {
+    const int b = blockIdx.x;
+    if (b >= n) return;
+    for (int i = threadIdx.x; i < 2 * (int)kGuardBytes; i += blockDim.x) {
+        const unsigned char v = i < (int)kGuardBytes ? g[b].lo[i] : g[b].hi[i - (int)kGuardBytes];
+        if (v != kCanary) atomicMin(first, ((unsigned long long)b << 32) | (unsigned)i);
+    }
+}
+#endif
+
+// cudaFree of a buffer that dalloc made (its guards included)
+static void dfree(Plan &p, void *ptr) {
+    if (ptr == nullptr) return;
+#ifdef FDAS_CHECK_BOUNDS
+    for (size_t i = 0; i < p.guards.size(); ++i) {
+        if (p.guards[i].base + kGuardBytes == (char *)ptr) {
+            cudaFree(p.guards[i].base);
+            p.guards.erase(p.guards.begin() + (std::ptrdiff_t)i);
+            return;
+        }
+    }
+#else
+    (void)p;
+#endif
+    cudaFree(ptr);
+}
+
 static void free_plan_memory(Plan *p) {
-    cudaFree(p->bank);
-    cudaFree(p->taps);
-    cudaFree(p->energy);
-    cudaFree(p->tap_off);
-    cudaFree(p->tap_m);
-    cudaFree(p->fft_a);
-    cudaFree(p->fft_b);
-    cudaFree(p->spec_pad);
-    cudaFree(p->corr);
-    cudaFree(p->tc_chunks);
-    cudaFree(p->tc_bank);
-    cudaFree(p->tc_inv_energy);
-    cudaFree(p->tc_edges);
-    cudaFree(p->spec_hi);
-    cudaFree(p->spec_lo);
+    dfree(*p, p->bank);
+    dfree(*p, p->taps);
+    dfree(*p, p->energy);
+    dfree(*p, p->tap_off);
+    dfree(*p, p->tap_m);
+    dfree(*p, p->fft_a);
+    dfree(*p, p->fft_b);
+    dfree(*p, p->spec_pad);
+    dfree(*p, p->corr);
+    dfree(*p, p->tc_chunks);
+    dfree(*p, p->tc_bank);
+    dfree(*p, p->tc_inv_energy);
+    dfree(*p, p->tc_edges);
+    dfree(*p, p->spec_hi);
+    dfree(*p, p->spec_lo);
     for (int b = 0; b < 2; ++b) {
-        cudaFree(p->plane[b]);
-        cudaFree(p->partials[b]);
+        dfree(*p, p->plane[b]);
+        dfree(*p, p->partials[b]);
         if (p->ev_conv[b]) cudaEventDestroy(p->ev_conv[b]);
         if (p->ev_hsum[b]) cudaEventDestroy(p->ev_hsum[b]);
     }
-    cudaFree(p->stats);
-    cudaFree(p->rank_ids);
-    cudaFree(p->cand);
-    cudaFree(p->cand_count);
-    cudaFree(p->flags);
-    cudaFree(p->out_stage);
-    cudaFree(p->async_res);
-    cudaFree(p->stage);
-    cudaFree(p->stage2);
+    dfree(*p, p->stats);
+    dfree(*p, p->rank_ids);
+    dfree(*p, p->cand);
+    dfree(*p, p->cand_count);
+    dfree(*p, p->flags);
+    dfree(*p, p->out_stage);
+    dfree(*p, p->async_res);
+    dfree(*p, p->stage);
+    dfree(*p, p->stage2);
     for (int b = 0; b < 2; ++b) {
         if (p->ev_copied[b]) cudaEventDestroy(p->ev_copied[b]);
         if (p->ev_consumed[b]) cudaEventDestroy(p->ev_consumed[b]);
     }
     if (p->cpy) cudaStreamDestroy(p->cpy);
     if (p->ev_start) cudaEventDestroy(p->ev_start);
-    cudaFree(p->gl_nodes);
-    cudaFree(p->ref_seeds);
-    cudaFree(p->ref_out);
+    dfree(*p, p->gl_nodes);
+    dfree(*p, p->ref_seeds);
+    dfree(*p, p->ref_out);
     if (p->host_small) cudaFreeHost(p->host_small);
     for (cudaEvent_t e : p->events) cudaEventDestroy(e);
     if (p->aux) cudaStreamDestroy(p->aux);
@@ -159,8 +233,9 @@ static void free_plan_memory(Plan *p) {
     if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
 }
 
+// a device buffer of the plan, named for the checked build's reports
 template <class T>
-static fdas_status dalloc(Plan &p, T **ptr, size_t bytes) {
+static fdas_status dalloc(Plan &p, T **ptr, size_t bytes, const char *name) {
     ++p.n_allocs;
     const Fault f = injected_fault();
     if (f.kind == kFaultAlloc && p.n_allocs == f.n) {
@@ -169,7 +244,23 @@ static fdas_status dalloc(Plan &p, T **ptr, size_t bytes) {
                   f.text + ")");
         return FDAS_ERR_OOM;
     }
+#ifdef FDAS_CHECK_BOUNDS
+    char *base = nullptr;
+    cudaError_t e = cudaMalloc((void **)&base, bytes + 2 * kGuardBytes);
+    if (e == cudaSuccess) {
+        e = cudaMemset(base, kCanary, kGuardBytes);
+        if (e == cudaSuccess) e = cudaMemset(base + kGuardBytes + bytes, kCanary, kGuardBytes);
+        if (e == cudaSuccess) {
+            *ptr = reinterpret_cast<T *>(base + kGuardBytes);
+            p.guards.push_back({base, bytes, name});
+        } else {
+            cudaFree(base);
+        }
+    }
+#else
+    (void)name;
     cudaError_t e = cudaMalloc((void **)ptr, bytes);
+#endif
     if (e != cudaSuccess) {
         *ptr = nullptr;
         cudaGetLastError();
@@ -181,18 +272,120 @@ static fdas_status dalloc(Plan &p, T **ptr, size_t bytes) {
     return FDAS_OK;
 }
 
+// Checked builds: wait for the device, then report the first failed device
+// bounds check and the first overwritten canary byte since the last check as
+// FDAS_ERR_BOUNDS (message: `after`, the launch group just queued, and what
+// failed), resetting logs and guards.  While the stream is being captured
+// into a graph nothing can be read; the check after the graph's launch covers
+// its kernels.  Ordinary builds never call it (FDAS_DEBUG_CHECK is empty).
+#ifdef FDAS_CHECK_BOUNDS
+static fdas_status debug_check(Plan &p, cudaStream_t s, const std::string &after) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    FDAS_CUDA_TRY(cudaStreamIsCapturing(s, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return FDAS_OK;
+    FDAS_CUDA_TRY(cudaDeviceSynchronize());
+    std::string msg;
+    const struct {
+        const char *unit;
+        cudaError_t (*take)(BoundsLog *);
+    } logs[] = {{"harmonic sum", bounds_take_harmonic},
+                {"tensor-core correlation", bounds_take_correlate_tc}};
+    for (const auto &l : logs) {
+        BoundsLog lg{};
+        FDAS_CUDA_TRY(l.take(&lg));
+        if (lg.failures > 0 && msg.empty())
+            msg = "after " + after + ": " + std::to_string(lg.failures) +
+                  " failed device bounds check(s) in the " + l.unit + "; the first: " +
+                  bounds_site_name(lg.site) + ", elements [" + std::to_string(lg.begin) + ", " +
+                  std::to_string(lg.begin + lg.count) + ") against a limit of " +
+                  std::to_string(lg.limit);
+    }
+    const int n = (int)p.guards.size();
+    if (n > 0) {
+        std::vector<GuardDesc> g(n);
+        for (int i = 0; i < n; ++i) {
+            g[i].lo = (const unsigned char *)p.guards[i].base;
+            g[i].hi = (const unsigned char *)p.guards[i].base + kGuardBytes + p.guards[i].bytes;
+        }
+        void *dev = nullptr;
+        const size_t tb = sizeof(GuardDesc) * (size_t)n;
+        FDAS_CUDA_TRY(cudaMalloc(&dev, tb + sizeof(unsigned long long)));
+        unsigned long long first = ~0ull;
+        auto *dfirst = (unsigned long long *)((char *)dev + tb);
+        cudaError_t e = cudaMemcpy(dev, g.data(), tb, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(dfirst, &first, sizeof(first), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) {
+            canary_check_kernel<<<n, 256>>>((const GuardDesc *)dev, n, dfirst);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaMemcpy(&first, dfirst, sizeof(first), cudaMemcpyDeviceToHost);
+        cudaFree(dev);
+        FDAS_CUDA_TRY(e);
+        if (first != ~0ull) {
+            const Plan::GuardedBuf &b = p.guards[first >> 32];
+            const int64_t i = (int64_t)(first & 0xffffffffu);
+            const int64_t off = i < (int64_t)kGuardBytes ? i - (int64_t)kGuardBytes
+                                                         : (int64_t)b.bytes + i - (int64_t)kGuardBytes;
+            if (msg.empty())
+                msg = "after " + after + ": canary of workspace buffer " + b.name + " (" +
+                      std::to_string(b.bytes) + " bytes) overwritten at byte offset " +
+                      std::to_string(off);
+            for (const Plan::GuardedBuf &r : p.guards) {
+                FDAS_CUDA_TRY(cudaMemset(r.base, kCanary, kGuardBytes));
+                FDAS_CUDA_TRY(cudaMemset(r.base + kGuardBytes + r.bytes, kCanary, kGuardBytes));
+            }
+            FDAS_CUDA_TRY(cudaDeviceSynchronize());
+        }
+    }
+    if (msg.empty()) return FDAS_OK;
+    set_error(msg);
+    return FDAS_ERR_BOUNDS;
+}
+#define FDAS_DEBUG_CHECK(p, s, after) FDAS_TRY(debug_check((p), (s), (after)))
+#else
+#define FDAS_DEBUG_CHECK(p, s, after) \
+    do {                              \
+    } while (0)
+#endif
+
+// FDAS_FAULT=bounds (checked builds): every device bounds limit is one
+// element lower for the duration of one call
+struct BoundsShrink {
+    bool on = false;
+    explicit BoundsShrink(bool want) {
+#ifdef FDAS_CHECK_BOUNDS
+        if (want) {
+            bounds_arm_harmonic(1);
+            bounds_arm_correlate_tc(1);
+            on = true;
+        }
+#else
+        (void)want;
+#endif
+    }
+    ~BoundsShrink() {
+#ifdef FDAS_CHECK_BOUNDS
+        if (on) {
+            cudaDeviceSynchronize();
+            bounds_arm_harmonic(0);
+            bounds_arm_correlate_tc(0);
+        }
+#endif
+    }
+};
+
 static fdas_status grow_stats(Plan &p, int64_t need) {
     if (need <= p.stats_cap) return FDAS_OK;
     int64_t cap = std::max<int64_t>(need, 2 * p.stats_cap);
     FDAS_CUDA_TRY(cudaDeviceSynchronize());
-    cudaFree(p.stats);
-    cudaFree(p.rank_ids);
+    dfree(p, p.stats);
+    dfree(p, p.rank_ids);
     p.stats = nullptr;
     p.rank_ids = nullptr;
     p.ws_bytes -= p.stats_cap * (int64_t)(sizeof(TrialStats) + sizeof(uint32_t));
     p.stats_cap = 0;
-    FDAS_TRY(dalloc(p, &p.stats, sizeof(TrialStats) * (size_t)cap));
-    FDAS_TRY(dalloc(p, &p.rank_ids, sizeof(uint32_t) * (size_t)cap));
+    FDAS_TRY(dalloc(p, &p.stats, sizeof(TrialStats) * (size_t)cap, "stats"));
+    FDAS_TRY(dalloc(p, &p.rank_ids, sizeof(uint32_t) * (size_t)cap, "rank_ids"));
     p.stats_cap = cap;
     return FDAS_OK;
 }
@@ -435,20 +628,23 @@ static fdas_status create(Plan *&out, int64_t n_samples, double tsamp, double z_
     } while (0)
 
     const size_t cb = cpx_bytes(p.prec), rb = real_bytes(p.prec);
-    PLAN_TRY(dalloc(p, &p.bank, cb * (size_t)p.n_z * p.L));
-    PLAN_TRY(dalloc(p, &p.taps, sizeof(double) * 2 * (size_t)p.n_taps));
-    PLAN_TRY(dalloc(p, &p.energy, sizeof(double) * p.n_z));
-    PLAN_TRY(dalloc(p, &p.tap_off, sizeof(int64_t) * p.n_z));
-    PLAN_TRY(dalloc(p, &p.tap_m, sizeof(int32_t) * p.n_z));
-    if (p.fft_m1 > 1) PLAN_TRY(dalloc(p, &p.fft_a, sizeof(float2) * (size_t)p.n_r));
-    PLAN_TRY(dalloc(p, &p.fft_b, sizeof(float2) * (size_t)p.n_r));
+    PLAN_TRY(dalloc(p, &p.bank, cb * (size_t)p.n_z * p.L, "bank"));
+    PLAN_TRY(dalloc(p, &p.taps, sizeof(double) * 2 * (size_t)p.n_taps, "taps"));
+    PLAN_TRY(dalloc(p, &p.energy, sizeof(double) * p.n_z, "energy"));
+    PLAN_TRY(dalloc(p, &p.tap_off, sizeof(int64_t) * p.n_z, "tap_off"));
+    PLAN_TRY(dalloc(p, &p.tap_m, sizeof(int32_t) * p.n_z, "tap_m"));
+    if (p.fft_m1 > 1) PLAN_TRY(dalloc(p, &p.fft_a, sizeof(float2) * (size_t)p.n_r, "fft_a"));
+    PLAN_TRY(dalloc(p, &p.fft_b, sizeof(float2) * (size_t)p.n_r, "fft_b"));
     // 64 elements past the last segment: the tensor-core windows of the last
     // tile read up to 16 elements beyond the zero tail
     const size_t pad_elems = (size_t)p.n_seg * p.V + 2 * (size_t)p.m_ov + 64;
-    PLAN_TRY(dalloc(p, &p.spec_pad, cb * pad_elems));
+    PLAN_TRY(dalloc(p, &p.spec_pad, cb * pad_elems, "spec_pad"));
+    p.spec_pad_elems = (int64_t)pad_elems;
     for (int b = 0; b < 2; ++b) {
-        PLAN_TRY(dalloc(p, &p.plane[b], rb * (size_t)p.n_z * (size_t)plane_cols(p)));
-        PLAN_TRY(dalloc(p, &p.partials[b], sizeof(double2) * (size_t)p.partials_cap));
+        PLAN_TRY(dalloc(p, &p.plane[b], rb * (size_t)p.n_z * (size_t)plane_cols(p),
+                        b == 0 ? "plane[0]" : "plane[1]"));
+        PLAN_TRY(dalloc(p, &p.partials[b], sizeof(double2) * (size_t)p.partials_cap,
+                        b == 0 ? "partials[0]" : "partials[1]"));
         PLAN_CUDA(cudaEventCreateWithFlags(&p.ev_conv[b], cudaEventDisableTiming));
         PLAN_CUDA(cudaEventCreateWithFlags(&p.ev_hsum[b], cudaEventDisableTiming));
     }
@@ -456,16 +652,16 @@ static fdas_status create(Plan *&out, int64_t n_samples, double tsamp, double z_
     // interbinning kernel; the tensor-core epilogue writes the half-bin plane
     // itself and needs only its edge table (allocated below)
     if (p.interbin && p.correlator != FDAS_CORR_TENSOR)
-        PLAN_TRY(dalloc(p, &p.corr, cb * (size_t)p.n_z * (size_t)p.n_r));
+        PLAN_TRY(dalloc(p, &p.corr, cb * (size_t)p.n_z * (size_t)p.n_r, "corr"));
     PLAN_TRY(grow_stats(p, 64));
     const int64_t rec_cap = next_pow2(p.max_cands);
-    PLAN_TRY(dalloc(p, &p.cand, sizeof(CandRec) * (size_t)rec_cap));
-    PLAN_TRY(dalloc(p, &p.cand_count, sizeof(unsigned long long)));
-    PLAN_TRY(dalloc(p, &p.flags, sizeof(unsigned int)));
-    PLAN_TRY(dalloc(p, &p.out_stage, sizeof(fdas_candidate) * (size_t)p.max_cands));
-    PLAN_TRY(dalloc(p, &p.async_res, sizeof(AsyncResult)));
-    PLAN_TRY(dalloc(p, &p.stage, sizeof(float) * (size_t)p.n_samples));
-    PLAN_TRY(dalloc(p, &p.stage2, sizeof(float) * (size_t)p.n_samples));
+    PLAN_TRY(dalloc(p, &p.cand, sizeof(CandRec) * (size_t)rec_cap, "cand"));
+    PLAN_TRY(dalloc(p, &p.cand_count, sizeof(unsigned long long), "cand_count"));
+    PLAN_TRY(dalloc(p, &p.flags, sizeof(unsigned int), "flags"));
+    PLAN_TRY(dalloc(p, &p.out_stage, sizeof(fdas_candidate) * (size_t)p.max_cands, "out_stage"));
+    PLAN_TRY(dalloc(p, &p.async_res, sizeof(AsyncResult), "async_res"));
+    PLAN_TRY(dalloc(p, &p.stage, sizeof(float) * (size_t)p.n_samples, "stage"));
+    PLAN_TRY(dalloc(p, &p.stage2, sizeof(float) * (size_t)p.n_samples, "stage2"));
     {
         // the copy stream at the highest priority: the copy kernel's CTAs
         // take the next free slots ahead of the running search's
@@ -495,7 +691,7 @@ static fdas_status create(Plan *&out, int64_t n_samples, double tsamp, double z_
 
     {
         const std::vector<float2> gl = gauss_legendre_01(refine_nodes());
-        PLAN_TRY(dalloc(p, &p.gl_nodes, sizeof(float2) * gl.size()));
+        PLAN_TRY(dalloc(p, &p.gl_nodes, sizeof(float2) * gl.size(), "gl_nodes"));
         PLAN_CUDA(cudaMemcpy(p.gl_nodes, gl.data(), sizeof(float2) * gl.size(),
                              cudaMemcpyHostToDevice));
     }
@@ -505,22 +701,26 @@ static fdas_status create(Plan *&out, int64_t n_samples, double tsamp, double z_
     PLAN_TRY(launch_template_bank(p, p.aux));
     if (p.correlator == FDAS_CORR_TENSOR) {
         const int64_t img = tc_bank_bytes(tc_table);
-        PLAN_TRY(dalloc(p, &p.tc_chunks, sizeof(TcChunk) * tc_table.size()));
+        PLAN_TRY(dalloc(p, &p.tc_chunks, sizeof(TcChunk) * tc_table.size(), "tc_chunks"));
         if (p.tc_split) {
             p.tc_bank_lo = img;
             p.tc_split_elems = (int64_t)pad_elems;
-            PLAN_TRY(dalloc(p, &p.spec_hi, 4 * pad_elems));
-            PLAN_TRY(dalloc(p, &p.spec_lo, 4 * pad_elems));
+            PLAN_TRY(dalloc(p, &p.spec_hi, 4 * pad_elems, "spec_hi"));
+            PLAN_TRY(dalloc(p, &p.spec_lo, 4 * pad_elems, "spec_lo"));
         }
-        PLAN_TRY(dalloc(p, &p.tc_bank, (size_t)img * (p.tc_split ? 2 : 1)));
-        PLAN_TRY(dalloc(p, &p.tc_inv_energy, sizeof(float) * (size_t)p.n_z));
-        if (p.interbin) PLAN_TRY(dalloc(p, &p.tc_edges, (size_t)tc_edge_bytes(p)));
+        PLAN_TRY(dalloc(p, &p.tc_bank, (size_t)img * (p.tc_split ? 2 : 1), "tc_bank"));
+        p.tc_img_bytes = img * (p.tc_split ? 2 : 1);
+        PLAN_TRY(dalloc(p, &p.tc_inv_energy, sizeof(float) * (size_t)p.n_z, "tc_inv_energy"));
+        if (p.interbin) PLAN_TRY(dalloc(p, &p.tc_edges, (size_t)tc_edge_bytes(p), "tc_edges"));
         PLAN_CUDA(cudaMemcpyAsync(p.tc_chunks, tc_table.data(), sizeof(TcChunk) * tc_table.size(),
                                   cudaMemcpyHostToDevice, p.aux));
         PLAN_TRY(launch_tc_bank(p, p.aux));
     }
     PLAN_CUDA(cudaStreamSynchronize(p.aux));
     PLAN_CUDA(cudaDeviceSynchronize());
+#ifdef FDAS_CHECK_BOUNDS
+    PLAN_TRY(debug_check(p, p.aux, "plan creation"));
+#endif
 #undef PLAN_TRY
 #undef PLAN_CUDA
     out = pp;
@@ -766,6 +966,7 @@ static fdas_status enqueue_batch(Plan &p, const fdas_series *batch, int32_t n_se
         }
         cudaEvent_t e0 = p.profiling ? mark(s) : nullptr;
         FDAS_TRY(launch_spectrum(v, x, spec, nullptr, s));
+        FDAS_DEBUG_CHECK(p, s, "the spectrum of series " + std::to_string(t));
         cudaEvent_t e1 = p.profiling ? mark(s) : nullptr;
         if (slot >= 0) {
             FDAS_CUDA_TRY(cudaEventRecord(p.ev_consumed[slot], s));
@@ -778,6 +979,15 @@ static fdas_status enqueue_batch(Plan &p, const fdas_series *batch, int32_t n_se
             if (p.profiling) e1 = mark(s);
         }
         FDAS_TRY(launch_plane(v, p.spec_pad, p.plane[b], p.partials[b], s));
+#ifdef FDAS_CHECK_BOUNDS
+        if (p.plant_canary && t == 0) {
+            // FDAS_FAULT=canary: one byte of the guard after the plane
+            for (const Plan::GuardedBuf &g : p.guards)
+                if (g.base + kGuardBytes == (char *)p.plane[b])
+                    FDAS_CUDA_TRY(cudaMemsetAsync(g.base + kGuardBytes + g.bytes, 0, 1, s));
+        }
+#endif
+        FDAS_DEBUG_CHECK(p, s, "the correlation of series " + std::to_string(t));
         cudaEvent_t e2 = p.profiling ? mark(s) : nullptr;
         FDAS_CUDA_TRY(cudaEventRecord(p.ev_conv[b], s));
         FDAS_CUDA_TRY(cudaStreamWaitEvent(hs, p.ev_conv[b], 0));
@@ -786,6 +996,7 @@ static fdas_status enqueue_batch(Plan &p, const fdas_series *batch, int32_t n_se
         Plan hv = harm_view(v);
         FDAS_TRY(launch_finalize_stats(hv, p.partials[b], plane_partials(v), nullptr, ts, hs));
         FDAS_TRY(launch_harmonic_threshold(hv, p.plane[b], ts, (uint32_t)rank[t], hs));
+        FDAS_DEBUG_CHECK(p, hs, "the harmonic sum of series " + std::to_string(t));
         cudaEvent_t e4 = p.profiling ? mark(hs) : nullptr;
         FDAS_CUDA_TRY(cudaEventRecord(p.ev_hsum[b], hs));
         p.launches[FDAS_PROF_SPECTRUM] += (v.fft_m1 == 1 ? 1 : 2) + 1;
@@ -893,12 +1104,12 @@ static fdas_status enqueue_search(Plan &p, const Fault &fault, const fdas_series
         FDAS_TRY(events_reserve(p, 7 * (size_t)n_series + 2));
         iv.reserve(3 * (size_t)n_series + 1);
     }
-    if (graphable && n_series > 0) {
-        FDAS_TRY(run_as_graph(p, batch, n_series, rank, s));
-    } else {
-        FDAS_TRY(enqueue_batch(p, batch, n_series, rank, s, iv, ev));
-    }
-    return FDAS_OK;
+    p.plant_canary = fault.kind == kFaultCanary;
+    fdas_status st = graphable && n_series > 0
+                         ? run_as_graph(p, batch, n_series, rank, s)
+                         : enqueue_batch(p, batch, n_series, rank, s, iv, ev);
+    p.plant_canary = false;
+    return st;
 }
 
 static fdas_status search(Plan &p, const fdas_series *batch, int32_t n_series,
@@ -913,6 +1124,7 @@ static fdas_status search(Plan &p, const fdas_series *batch, int32_t n_series,
     FDAS_TRY(check_batch(p, batch, n_series, graphable));
     *n_found = 0;
     DeviceGuard guard(p.device);
+    BoundsShrink shrink(fault.kind == kFaultBounds);
     std::vector<Interval> iv;
     size_t ev = 0;
     FDAS_TRY(enqueue_search(p, fault, batch, n_series, graphable, s, iv, ev));
@@ -930,6 +1142,7 @@ static fdas_status search(Plan &p, const fdas_series *batch, int32_t n_series,
         iv.push_back({FDAS_PROF_FINISH, f0, f1});
         accumulate(p, iv);
     }
+    FDAS_DEBUG_CHECK(p, s, "the candidate ordering");
     return st;
 }
 
@@ -956,6 +1169,7 @@ static fdas_status search_async(Plan &p, const fdas_series *batch, int32_t n_ser
                      s != cudaStreamPerThread;
     FDAS_TRY(check_batch(p, batch, n_series, graphable));
     DeviceGuard guard(p.device);
+    BoundsShrink shrink(fault.kind == kFaultBounds);
     std::vector<Interval> iv;
     size_t ev = 0;
     FDAS_TRY(enqueue_search(p, fault, batch, n_series, graphable, s, iv, ev));
@@ -965,6 +1179,7 @@ static fdas_status search_async(Plan &p, const fdas_series *batch, int32_t n_ser
                                   cudaMemcpyDefault, s));
     FDAS_CUDA_TRY(cudaMemcpyAsync(status, &p.async_res->status, sizeof(int32_t),
                                   cudaMemcpyDefault, s));
+    FDAS_DEBUG_CHECK(p, s, "the candidate ordering");
     return FDAS_OK;
 }
 
@@ -1017,13 +1232,15 @@ static fdas_status retable_tc(Plan &p, int order) {
     }
     FDAS_CUDA_TRY(cudaDeviceSynchronize());
     const int64_t img = tc_bank_bytes(table);
-    cudaFree(p.tc_chunks);
-    cudaFree(p.tc_bank);
+    p.ws_bytes -= p.tc_img_bytes + (int64_t)sizeof(TcChunk) * old_n;
+    dfree(p, p.tc_chunks);
+    dfree(p, p.tc_bank);
     p.tc_chunks = nullptr;
     p.tc_bank = nullptr;
-    FDAS_TRY(dalloc(p, &p.tc_chunks, sizeof(TcChunk) * table.size()));
+    FDAS_TRY(dalloc(p, &p.tc_chunks, sizeof(TcChunk) * table.size(), "tc_chunks"));
     if (p.tc_split) p.tc_bank_lo = img;
-    FDAS_TRY(dalloc(p, &p.tc_bank, (size_t)img * (p.tc_split ? 2 : 1)));
+    FDAS_TRY(dalloc(p, &p.tc_bank, (size_t)img * (p.tc_split ? 2 : 1), "tc_bank"));
+    p.tc_img_bytes = img * (p.tc_split ? 2 : 1);
     p.tc_n_ch = (int)table.size();
     p.tc_nbuf = tc_image_buffers(p);
     FDAS_CUDA_TRY(cudaMemcpy(p.tc_chunks, table.data(), sizeof(TcChunk) * table.size(),
@@ -1233,7 +1450,9 @@ fdas_status fdas_spectrum(fdas_plan *plan, const float *series, void *spectrum_o
     if (((uintptr_t)series & 15u) != 0) return arg_error("series is not 16-byte aligned");
     Plan &p = *reinterpret_cast<Plan *>(plan);
     DeviceGuard guard(p.device);
-    return launch_spectrum(p, series, spectrum_out, medians_out, (cudaStream_t)stream);
+    FDAS_TRY(launch_spectrum(p, series, spectrum_out, medians_out, (cudaStream_t)stream));
+    FDAS_DEBUG_CHECK(p, (cudaStream_t)stream, "fdas_spectrum");
+    return FDAS_OK;
 }
 
 fdas_status fdas_power_plane(fdas_plan *plan, const void *spectrum, void *plane_out,
@@ -1252,6 +1471,7 @@ fdas_status fdas_power_plane(fdas_plan *plan, const void *spectrum, void *plane_
         FDAS_CUDA_TRY(cudaMemcpyAsync(stats_out, p.stats, 2 * sizeof(double),
                                       cudaMemcpyDeviceToDevice, s));
     }
+    FDAS_DEBUG_CHECK(p, s, "fdas_power_plane");
     return FDAS_OK;
 }
 
@@ -1264,7 +1484,9 @@ fdas_status fdas_correlation_plane(fdas_plan *plan, const void *spectrum, void *
     const size_t cb = cpx_bytes(p.prec);
     FDAS_CUDA_TRY(cudaMemcpyAsync((char *)p.spec_pad + cb * (size_t)p.m_ov, spectrum,
                                   cb * (size_t)p.n_r, cudaMemcpyDeviceToDevice, s));
-    return launch_correlate(p, p.spec_pad, corr_out, p.partials[0], s, true);
+    FDAS_TRY(launch_correlate(p, p.spec_pad, corr_out, p.partials[0], s, true));
+    FDAS_DEBUG_CHECK(p, s, "fdas_correlation_plane");
+    return FDAS_OK;
 }
 
 fdas_status fdas_harmonic_sums(fdas_plan *plan, const void *plane, float *sums_out, void *stream) {
@@ -1272,7 +1494,9 @@ fdas_status fdas_harmonic_sums(fdas_plan *plan, const void *plane, float *sums_o
     Plan &p = *reinterpret_cast<Plan *>(plan);
     DeviceGuard guard(p.device);
     Plan hv = harm_view(p);
-    return launch_harmonic_sums(hv, plane, sums_out, (cudaStream_t)stream);
+    FDAS_TRY(launch_harmonic_sums(hv, plane, sums_out, (cudaStream_t)stream));
+    FDAS_DEBUG_CHECK(p, (cudaStream_t)stream, "fdas_harmonic_sums");
+    return FDAS_OK;
 }
 
 fdas_status fdas_threshold(fdas_plan *plan, const void *plane, const double *stats,
@@ -1293,7 +1517,9 @@ fdas_status fdas_threshold(fdas_plan *plan, const void *plane, const double *sta
     Plan hv = harm_view(p);
     FDAS_TRY(launch_finalize_stats(hv, nullptr, 0, stats, p.stats, s));
     FDAS_TRY(launch_harmonic_threshold(hv, plane, p.stats, 0, s));
-    return collect(p, cands, capacity, n_found, s);
+    const fdas_status st = collect(p, cands, capacity, n_found, s);
+    FDAS_DEBUG_CHECK(p, s, "fdas_threshold");
+    return st;
 }
 
 fdas_status fdas_selftest_wait_timeout(fdas_plan *plan, int64_t limit_cycles, void *stream) {
@@ -1360,18 +1586,20 @@ fdas_status fdas_refine(fdas_plan *plan, const float *spectrum, const fdas_seed 
     if (n == 0) return FDAS_OK;
     if (n > p.ref_cap) {
         FDAS_CUDA_TRY(cudaStreamSynchronize(s));
-        cudaFree(p.ref_seeds);
-        cudaFree(p.ref_out);
+        p.ws_bytes -= (int64_t)(sizeof(fdas_seed) + sizeof(fdas_refined)) * p.ref_cap;
+        dfree(p, p.ref_seeds);
+        dfree(p, p.ref_out);
         p.ref_seeds = nullptr;
         p.ref_out = nullptr;
         p.ref_cap = 0;
-        FDAS_TRY(dalloc(p, &p.ref_seeds, sizeof(fdas_seed) * (size_t)n));
-        FDAS_TRY(dalloc(p, &p.ref_out, sizeof(fdas_refined) * (size_t)n));
+        FDAS_TRY(dalloc(p, &p.ref_seeds, sizeof(fdas_seed) * (size_t)n, "ref_seeds"));
+        FDAS_TRY(dalloc(p, &p.ref_out, sizeof(fdas_refined) * (size_t)n, "ref_out"));
         p.ref_cap = n;
     }
     FDAS_CUDA_TRY(cudaMemcpyAsync(p.ref_seeds, seeds, sizeof(fdas_seed) * (size_t)n,
                                   cudaMemcpyDefault, s));
     FDAS_TRY(launch_refine(p, (const float2 *)spectrum, p.ref_seeds, n, n_steps, p.ref_out, s));
+    FDAS_DEBUG_CHECK(p, s, "fdas_refine");
     FDAS_CUDA_TRY(cudaMemcpyAsync(out, p.ref_out, sizeof(fdas_refined) * (size_t)n,
                                   cudaMemcpyDefault, s));
     FDAS_CUDA_TRY(cudaStreamSynchronize(s));
@@ -1405,6 +1633,12 @@ fdas_status fdas_profile_read(const fdas_plan *plan, fdas_profile *out) {
 
 const char *fdas_last_error(void) { return g_last_error.c_str(); }
 
+#ifdef FDAS_CHECK_BOUNDS
+const char *fdas_version(void) { return "fdas-gb300 0.1 (sm_103a, checked)"; }
+int32_t fdas_checked_build(void) { return 1; }
+#else
 const char *fdas_version(void) { return "fdas-gb300 0.1 (sm_103a)"; }
+int32_t fdas_checked_build(void) { return 0; }
+#endif
 
 }  // extern "C"

@@ -13,6 +13,14 @@ def pytest_configure(config):
     config.addinivalue_line("markers", "slow: full-size case (minutes of CPU)")
 
 
+def pytest_sessionstart(session):
+    # FDAS_CHECKED=1: the binding loads the checked build of the library
+    # (device bounds checks, workspace canaries) for every test
+    if os.environ.get("FDAS_CHECKED") == "1":
+        import importlib
+        importlib.import_module("paper_2211_13517_gb300.build").build(checked=True)
+
+
 def pytest_collection_modifyitems(config, items):
     try:
         import torch

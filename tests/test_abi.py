@@ -5,6 +5,7 @@ struct layouts the binding relies on, and the argument validation that every
 entry point performs before touching CUDA.
 """
 import ctypes
+import importlib
 import os
 import re
 
@@ -194,3 +195,34 @@ def test_store_full_status_is_returned_not_raised(capi):
     assert capi.FDAS_ERR_CAND_STORE_FULL == 8
     assert capi.FDAS_ERR_CAND_STORE_FULL in capi.COUNT_STATUSES
     assert capi.STATUS_NAMES[8] == "FDAS_ERR_CAND_STORE_FULL"
+
+
+def test_checked_build_exports_the_same_symbols(capi):
+    """The checked build (-DFDAS_CHECK_BOUNDS) links, exports every declared
+    symbol and says so; the ordinary build says it is not."""
+    path = importlib.import_module("paper_2211_13517_gb300.build").build(checked=True)
+    assert os.path.basename(path) == "libfdas_checked.so" and path != capi.LIB
+    chk = ctypes.CDLL(path)
+    missing = [n for n in sorted(_declared_symbols()) if not hasattr(chk, n)]
+    assert not missing, missing
+    chk.fdas_checked_build.restype = ctypes.c_int32
+    chk.fdas_version.restype = ctypes.c_char_p
+    assert chk.fdas_checked_build() == 1 and b"checked" in chk.fdas_version()
+    plain = ctypes.CDLL(capi.LIB)
+    plain.fdas_checked_build.restype = ctypes.c_int32
+    assert plain.fdas_checked_build() == 0
+    assert capi.STATUS_NAMES[capi.FDAS_ERR_BOUNDS] == "FDAS_ERR_BOUNDS"
+
+
+def test_checked_faults_need_the_checked_build(capi, monkeypatch):
+    """FDAS_FAULT=canary / bounds are refused by the ordinary build before any
+    CUDA call (FDAS_ERR_UNSUPPORTED, naming the checked build)."""
+    if capi.fdas_checked_build():
+        pytest.skip("the checked build takes these faults")
+    good = (1 << 17, 64e-6, 16.0, 2.0, 2048, 4)
+    for fault in ("canary", "bounds"):
+        monkeypatch.setenv("FDAS_FAULT", fault)
+        with pytest.raises(capi.FdasError) as ei:
+            capi.fdas_plan_create(*good)
+        assert ei.value.status == capi.FDAS_ERR_UNSUPPORTED
+        assert "checked build" in str(ei.value) and fault in str(ei.value)

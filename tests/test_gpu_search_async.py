@@ -148,6 +148,8 @@ def test_ordering_of_many_candidates_matches_oracle(capi):
 
 
 def test_async_returns_before_the_work_is_done(capi):
+    if capi.fdas_checked_build():
+        pytest.skip("the checked build waits for the device after each launch group")
     n = 1 << 23
     plan = capi.Plan(n, 64e-6, 96.0, 1.0, 8192, 16, precision=capi.FDAS_BF16)
     xs = [torch.randn(n, device="cuda") for _ in range(24)]
