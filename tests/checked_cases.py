@@ -64,7 +64,8 @@ def _rec(capi, st, c, nf):
 
 
 def _u8(t):
-    return np.frombuffer(t.contiguous().cpu().numpy().tobytes(), dtype=np.uint8)
+    import torch
+    return t.contiguous().reshape(-1).view(torch.uint8).cpu().numpy().copy()
 
 
 def run_cases(capi, torch):
