@@ -9,6 +9,7 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -240,7 +241,13 @@ struct Plan {
         size_t bytes;
         const char *name;
     };
-    std::vector<GuardedBuf> guards;
+    // the plan's pools, shared with its views (the copies of a Plan made
+    // for one series or one stage), so that a view copies no vector
+    struct Pools {
+        std::vector<cudaEvent_t> events;   // timed intervals of tracing
+        std::vector<GuardedBuf> guards;    // checked builds
+    };
+    std::shared_ptr<Pools> pools = std::make_shared<Pools>();
     bool plant_canary = false;        // FDAS_FAULT=canary for the batch being queued
     // tracing
     bool profiling = false;
@@ -248,7 +255,6 @@ struct Plan {
     int64_t launches[4] = {0, 0, 0, 0};
     int64_t timed[4] = {0, 0, 0, 0};
     double prof_ms[4] = {0, 0, 0, 0};
-    std::vector<cudaEvent_t> events;   // pool for timed intervals
     cudaStream_t aux = nullptr;     // second stream (harmonic sum overlap), lowest priority
     cudaStream_t hi = nullptr;      // spectrum + correlation, highest priority
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;   // caller's stream <-> hi

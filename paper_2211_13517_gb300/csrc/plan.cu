@@ -171,10 +171,10 @@ __global__ void canary_check_kernel(const GuardDesc *g, int n, unsigned long lon
 static void dfree(Plan &p, void *ptr) {
     if (ptr == nullptr) return;
 #ifdef FDAS_CHECK_BOUNDS
-    for (size_t i = 0; i < p.guards.size(); ++i) {
-        if (p.guards[i].base + kGuardBytes == (char *)ptr) {
-            cudaFree(p.guards[i].base);
-            p.guards.erase(p.guards.begin() + (std::ptrdiff_t)i);
+    for (size_t i = 0; i < p.pools->guards.size(); ++i) {
+        if (p.pools->guards[i].base + kGuardBytes == (char *)ptr) {
+            cudaFree(p.pools->guards[i].base);
+            p.pools->guards.erase(p.pools->guards.begin() + (std::ptrdiff_t)i);
             return;
         }
     }
@@ -225,7 +225,7 @@ static void free_plan_memory(Plan *p) {
     dfree(*p, p->ref_seeds);
     dfree(*p, p->ref_out);
     if (p->host_small) cudaFreeHost(p->host_small);
-    for (cudaEvent_t e : p->events) cudaEventDestroy(e);
+    for (cudaEvent_t e : p->pools->events) cudaEventDestroy(e);
     if (p->aux) cudaStreamDestroy(p->aux);
     if (p->hi) cudaStreamDestroy(p->hi);
     if (p->ev_fork) cudaEventDestroy(p->ev_fork);
@@ -252,7 +252,7 @@ static fdas_status dalloc(Plan &p, T **ptr, size_t bytes, const char *name) {
         if (e == cudaSuccess) e = cudaMemset(base + kGuardBytes + bytes, kCanary, kGuardBytes);
         if (e == cudaSuccess) {
             *ptr = reinterpret_cast<T *>(base + kGuardBytes);
-            p.guards.push_back({base, bytes, name});
+            p.pools->guards.push_back({base, bytes, name});
         } else {
             cudaFree(base);
         }
@@ -300,12 +300,13 @@ static fdas_status debug_check(Plan &p, cudaStream_t s, const std::string &after
                   std::to_string(lg.begin + lg.count) + ") against a limit of " +
                   std::to_string(lg.limit);
     }
-    const int n = (int)p.guards.size();
+    const int n = (int)p.pools->guards.size();
     if (n > 0) {
         std::vector<GuardDesc> g(n);
         for (int i = 0; i < n; ++i) {
-            g[i].lo = (const unsigned char *)p.guards[i].base;
-            g[i].hi = (const unsigned char *)p.guards[i].base + kGuardBytes + p.guards[i].bytes;
+            const Plan::GuardedBuf &b = p.pools->guards[i];
+            g[i].lo = (const unsigned char *)b.base;
+            g[i].hi = (const unsigned char *)b.base + kGuardBytes + b.bytes;
         }
         void *dev = nullptr;
         const size_t tb = sizeof(GuardDesc) * (size_t)n;
@@ -322,7 +323,7 @@ static fdas_status debug_check(Plan &p, cudaStream_t s, const std::string &after
         cudaFree(dev);
         FDAS_CUDA_TRY(e);
         if (first != ~0ull) {
-            const Plan::GuardedBuf &b = p.guards[first >> 32];
+            const Plan::GuardedBuf &b = p.pools->guards[first >> 32];
             const int64_t i = (int64_t)(first & 0xffffffffu);
             const int64_t off = i < (int64_t)kGuardBytes ? i - (int64_t)kGuardBytes
                                                          : (int64_t)b.bytes + i - (int64_t)kGuardBytes;
@@ -330,7 +331,7 @@ static fdas_status debug_check(Plan &p, cudaStream_t s, const std::string &after
                 msg = "after " + after + ": canary of workspace buffer " + b.name + " (" +
                       std::to_string(b.bytes) + " bytes) overwritten at byte offset " +
                       std::to_string(off);
-            for (const Plan::GuardedBuf &r : p.guards) {
+            for (const Plan::GuardedBuf &r : p.pools->guards) {
                 FDAS_CUDA_TRY(cudaMemset(r.base, kCanary, kGuardBytes));
                 FDAS_CUDA_TRY(cudaMemset(r.base + kGuardBytes + r.bytes, kCanary, kGuardBytes));
             }
@@ -815,10 +816,10 @@ class DeviceGuard {
 
 // event pool for the tracing intervals
 static fdas_status events_reserve(Plan &p, size_t n) {
-    while (p.events.size() < n) {
+    while (p.pools->events.size() < n) {
         cudaEvent_t e;
         FDAS_CUDA_TRY(cudaEventCreate(&e));
-        p.events.push_back(e);
+        p.pools->events.push_back(e);
     }
     return FDAS_OK;
 }
@@ -884,7 +885,7 @@ static fdas_status enqueue_batch(Plan &p, const fdas_series *batch, int32_t n_se
     const size_t cb = cpx_bytes(p.prec);
     void *spec = (char *)p.spec_pad + cb * (size_t)p.m_ov;
     auto mark = [&](cudaStream_t st) -> cudaEvent_t {
-        cudaEvent_t e = p.events[ev++];
+        cudaEvent_t e = p.pools->events[ev++];
         cudaEventRecord(e, st);
         return e;
     };
@@ -982,7 +983,7 @@ static fdas_status enqueue_batch(Plan &p, const fdas_series *batch, int32_t n_se
 #ifdef FDAS_CHECK_BOUNDS
         if (p.plant_canary && t == 0) {
             // FDAS_FAULT=canary: one byte of the guard after the plane
-            for (const Plan::GuardedBuf &g : p.guards)
+            for (const Plan::GuardedBuf &g : p.pools->guards)
                 if (g.base + kGuardBytes == (char *)p.plane[b])
                     FDAS_CUDA_TRY(cudaMemsetAsync(g.base + kGuardBytes + g.bytes, 0, 1, s));
         }
@@ -1131,12 +1132,12 @@ static fdas_status search(Plan &p, const fdas_series *batch, int32_t n_series,
     p.prof_trials += n_series;
     cudaEvent_t f0 = nullptr;
     if (p.profiling) {
-        f0 = p.events[ev++];
+        f0 = p.pools->events[ev++];
         cudaEventRecord(f0, s);
     }
     fdas_status st = collect(p, cands, capacity, n_found, s);
     if (p.profiling) {
-        cudaEvent_t f1 = p.events[ev++];
+        cudaEvent_t f1 = p.pools->events[ev++];
         cudaEventRecord(f1, s);
         cudaEventSynchronize(f1);
         iv.push_back({FDAS_PROF_FINISH, f0, f1});
