@@ -454,6 +454,51 @@ def test_empty_batch_and_overflow(capi):
     plan.close()
 
 
+@pytest.mark.parametrize("prec,corr", [(0, 1), (1, 2)])
+def test_silent_series_in_a_batch(capi, prec, corr):
+    """A degenerate input: an all-zero series (every block median 0, factor 0)
+    between two ordinary ones.  Its spectrum and plane are exactly 0 and it
+    gives no candidate in either threshold mode; the other series' lists are
+    the oracle's (FP32: 1e-4 guard band; BF16: 3%)."""
+    n = 1 << 14
+    zero = np.zeros(n, np.float32)
+    xs = [S.sinusoid_series(n=n, seed=31, r0=2000.3, z0=3.0, amp=0.3), zero,
+          S.sinusoid_series(n=n, seed=32, r0=3100.6, z0=-5.0, amp=0.3)]
+    guard = 1e-4 if prec == 0 else 0.03
+    for mode in (capi.FDAS_THRESH_GAMMA_TAIL, capi.FDAS_THRESH_MEAN_PLUS_KSIGMA):
+        plan = _plan(capi, n, 16.0, 2.0, 2048, 4, precision=prec, correlator=corr,
+                     threshold_mode=mode)
+        spec = plan.spectrum(torch.from_numpy(zero).cuda())
+        assert not torch.any(spec.float() != 0)
+        plane, stats = plan.power_plane(spec)
+        assert not torch.any(plane.float() != 0) and not torch.any(stats != 0)
+        st, cands, nf = plan.search([torch.from_numpy(x).cuda() for x in xs], trial_ids=[0, 1, 2])
+        assert st == capi.FDAS_OK and nf == len(cands) > 0
+        assert not np.any(cands["trial_id"] == 1)
+        for t in (0, 2):
+            ref = O.search(xs[t], 16.0, 2.0, 4, mode=mode, trial=t, guard=guard)
+            _compare_cands(cands[cands["trial_id"] == t], ref["candidates"], ref["guard"],
+                           rel_power=guard)
+        plan.close()
+
+
+@pytest.mark.parametrize("prec,corr", [(0, 1), (1, 2)])
+def test_single_template_search(capi, prec, corr):
+    """z_max = 0: one template (a plain Fourier search with harmonic sums
+    along the z = 0 row), against the oracle."""
+    n = 1 << 15
+    x, _ = S.pulsar_series(n, seed=23, height=1.0, z_abs=0.0)
+    guard = 1e-4 if prec == 0 else 0.03
+    ref = O.search(x, 0.0, 1.0, 8, guard=guard)
+    plan = _plan(capi, n, 0.0, 1.0, 1024, 8, precision=prec, correlator=corr)
+    assert plan.info.n_z == 1
+    st, cands, nf = plan.search([torch.from_numpy(x).cuda()], capacity=1 << 16)
+    assert st == capi.FDAS_OK and nf == len(cands) > 0
+    assert np.all(cands["iz"] == 0)
+    _compare_cands(cands, ref["candidates"], ref["guard"], rel_power=guard)
+    plan.close()
+
+
 def test_nonfinite_input_reported(capi):
     n = 1 << 14
     x = S.white_noise(n, 2)

@@ -665,3 +665,17 @@ def test_fourier_power_peak_of_an_injection(r0, z0):
     assert 0.99 < E < 1.0
     for dr, dz in ((0.03, 0), (-0.03, 0), (0, 0.3), (0, -0.3)):
         assert O.fourier_power(X, r0 + dr, z0 + dz)[0] < P
+
+
+def test_silent_series_gives_no_candidates():
+    """An all-zero series: every block median is 0, so every block gets the
+    factor 0 (the reading for a block without power); the plane, its
+    statistics and both kinds of threshold are 0, nothing crosses, and no NaN
+    appears anywhere."""
+    x = np.zeros(1 << 12, np.float32)
+    for mode in (O.GAMMA_TAIL, O.MEAN_PLUS_KSIGMA):
+        r = O.search(x, 4.0, 1.0, 4, mode=mode)
+        assert np.all(r["medians"] == 0.0) and np.all(r["Xn"] == 0.0)
+        assert np.all(r["P"] == 0.0) and r["mean"] == 0.0 and r["std"] == 0.0
+        assert np.all(r["T"] == 0.0) and len(r["candidates"]) == 0
+
