@@ -43,7 +43,8 @@ typedef enum {
     FDAS_ERR_CUDA = 2,           /* a CUDA runtime call failed               */
     FDAS_ERR_OOM = 3,            /* device allocation failed                 */
     FDAS_ERR_CAND_OVERFLOW = 4,  /* more candidates than the caller's buffer */
-    FDAS_ERR_NONFINITE = 5,      /* NaN or Inf in an input series           */
+    FDAS_ERR_NONFINITE = 5,      /* NaN or Inf in an input series, or a
+                                    spectral power beyond the FP32 range    */
     FDAS_ERR_TIMEOUT = 6,        /* a bounded device wait gave up            */
     FDAS_ERR_UNSUPPORTED = 7,    /* valid request the library does not serve */
     FDAS_ERR_CAND_STORE_FULL = 8, /* more crossings than the plan's device
@@ -226,8 +227,9 @@ fdas_status fdas_plan_get_info(const fdas_plan *plan, fdas_plan_info *info);
  * (S - h mean)/(sqrt(h) std).
  * Blocking: returns after the results are in `cands` (fdas_search_async
  * below is the stream-ordered form).
- * Errors: FDAS_ERR_ARG; FDAS_ERR_NONFINITE (a series holds NaN/Inf: no
- * candidates are returned); FDAS_ERR_CAND_OVERFLOW (more crossings than
+ * Errors: FDAS_ERR_ARG; FDAS_ERR_NONFINITE (a series holds NaN/Inf, or
+ * a power |X_k|^2 of its spectrum exceeds the FP32 range, about 3.4e38, as
+ * for samples of about 1e20 at N = 2^23: no candidates are returned); FDAS_ERR_CAND_OVERFLOW (more crossings than
  * `capacity` but no more than the plan's max_candidates: *n_found is the true
  * total and the first `capacity` entries in the order above are written);
  * FDAS_ERR_CAND_STORE_FULL (more crossings than the plan's max_candidates:

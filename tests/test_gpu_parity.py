@@ -499,6 +499,26 @@ def test_single_template_search(capi, prec, corr):
     plan.close()
 
 
+def test_power_beyond_fp32_range_reported_as_nonfinite(capi):
+    """A finite series whose spectral power does not fit in FP32 (one sample
+    of 1e21: |X_k|^2 = 1e42) is reported like a non-finite series; one of
+    1e15 (|X_k|^2 = 1e30) is searched.  The plan stays usable."""
+    n = 1 << 14
+    plan = _plan(capi, n, 16.0, 2.0, 2048, 4)
+    x = S.white_noise(n, 3)
+    x[5] = 1e21
+    with pytest.raises(capi.FdasError) as ei:
+        plan.search([torch.from_numpy(x).cuda()])
+    assert ei.value.status == capi.FDAS_ERR_NONFINITE
+    x[5] = 1e15
+    st, _, _ = plan.search([torch.from_numpy(x).cuda()], capacity=1 << 10)
+    assert st in (capi.FDAS_OK, capi.FDAS_ERR_CAND_OVERFLOW, capi.FDAS_ERR_CAND_STORE_FULL)
+    x[5] = 0.0
+    st, _, _ = plan.search([torch.from_numpy(x).cuda()])
+    assert st == capi.FDAS_OK
+    plan.close()
+
+
 def test_nonfinite_input_reported(capi):
     n = 1 << 14
     x = S.white_noise(n, 2)
